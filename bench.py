@@ -1,0 +1,393 @@
+"""Benchmark of the LBVH search path on B300.
+
+One step = the whole hot path over one batch of synthetic input: build the
+tree over n points (scene box, Morton codes, radix sort, hierarchy, fit),
+Morton-sort the queries, spatial query in two passes (count, scan, read the
+total, fill) and k-nearest query.  Default workload: n = 1e7 points uniform in
+the unit cube, m = 1e6 queries from the same distribution, radius for a mean
+of 10 neighbours, k = 10.
+
+Prints one JSON line (rank 0).  `value` is the query throughput of the whole
+step in Mqueries/s (radius + nearest queries per second of build+query time),
+with inputs resident in HBM; `e2e` is the same metric with the points and
+queries copied from pinned host memory and all results copied back inside the
+timed region.  L2 is flushed (256 MB write) between timed steps.
+
+--impl reference times the CPU oracle (median-split CPU BVH, OpenMP) on the
+host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import datagen  # noqa: E402
+
+METRIC = "kNN k=10 & radius Mqueries/s + build Mpts/s at 1e7 pts; learned vs plain"
+UNIT = "Mqueries/s"
+
+WORKLOADS = {
+    # name: (distribution, n, m, k)
+    "cube_1e7": ("cube", 10_000_000, 1_000_000, 10),
+    "hollow_sphere_1e7": ("hollow_sphere", 10_000_000, 1_000_000, 10),
+    "cube_1e6": ("cube", 1_000_000, 1_000_000, 10),
+}
+
+
+# ---------------------------------------------------------------- helpers
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+# algorithmic bytes per unit of each kernel (the design doc states the derivation)
+def kernel_bytes(name, n, m, k, nnz, nodes):
+    """Algorithmic DRAM bytes of all launches of `name` in one step."""
+    passes = 4  # 30-bit keys, 8-bit digits
+    sort_b = lambda u: u * (12 + 16 * (passes - 1))  # first pass reads keys only, writes pairs
+    table = {
+        "bounds": 12 * n,
+        "morton": 16 * n + 16 * m,                  # points -> codes, queries -> codes
+        "onesweep_pass": sort_b(n) + sort_b(m),
+        "hierarchy": 12 * n,                        # codes read, parent links written
+        "fit": 52 * n + 76 * max(n - 1, 0),         # gather + leaf record, then per internal node
+        "scan": 12 * m + 8,                         # counts read twice, offsets written
+        "spatial_count": 20 * m + 64 * nodes.get("spatial", 0),
+        "spatial_fill": 28 * m + 4 * nnz + 64 * nodes.get("spatial", 0),
+        "nearest": m * (16 + 8 * k + 8) + 64 * nodes.get("nearest", 0),
+    }
+    return table.get(name)
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1908_11807_b300 as ab
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist_name, n, m, k = WORKLOADS[args.workload]
+    seed = datagen.SEED0 + 2
+    p_h, q_h = datagen.workload(dist_name, n, m, seed)
+    r = datagen.radius_for_mean(n, dist_name)
+    p = torch.from_numpy(p_h).to(dev)
+    q = torch.from_numpy(q_h).to(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(points, queries, out=None):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
+        bvh = ab.BVH(points)
+        ev[1].record(stream)
+        off, idx = bvh.query_spatial(queries, r)
+        ev[2].record(stream)
+        kidx, kd2 = bvh.query_nearest(queries, k)
+        ev[3].record(stream)
+        bvh.destroy()
+        return ev, (off, idx, kidx, kd2)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step(p, q)
+    barrier()
+
+    # nodes visited per query (instrumented untimed run)
+    nodes = {}
+
+    ab.profile_enable(True)
+    ab.profile_report()  # reset
+    phase = np.zeros(3)
+    total_ms = 0.0
+    nnz = 0
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1.0)  # evict L2 between steps (outside the timed interval)
+            barrier()
+            ev, res = step(p, q)
+            torch.cuda.synchronize()
+            t = [ev[0].elapsed_time(e) for e in ev[1:]]
+            phase += np.array([t[0], t[1] - t[0], t[2] - t[1]])
+            total_ms += t[2]
+            nnz = int(res[1].numel())
+    prof = ab.profile_report()
+    ab.profile_enable(False)
+    clocks = clk.summary()
+
+    step_ms = total_ms / args.steps
+    if ws > 1:
+        tt = torch.tensor([step_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        step_ms = float(tt.item())
+    value = ws * 2 * m / (step_ms * 1e-3) / 1e6
+    build_ms, spatial_ms, knn_ms = phase / args.steps
+
+    # ---- end to end: pinned host buffers in, results back to host, every step
+    p_pin = torch.from_numpy(p_h).pin_memory()
+    q_pin = torch.from_numpy(q_h).pin_memory()
+    kk = min(k, n)
+    outs = dict(off=torch.empty(m + 1, dtype=torch.int64).pin_memory(),
+                kidx=torch.empty((m, kk), dtype=torch.int32).pin_memory(),
+                kd2=torch.empty((m, kk), dtype=torch.float32).pin_memory())
+    idx_pin = torch.empty(max(nnz, 1) * 2, dtype=torch.int32).pin_memory()
+    pd = torch.empty_like(p)
+    qd = torch.empty_like(q)
+
+    def e2e_step():
+        pd.copy_(p_pin, non_blocking=True)
+        qd.copy_(q_pin, non_blocking=True)
+        ev, (off, idx, kidx, kd2) = step(pd, qd)
+        outs["off"].copy_(off, non_blocking=True)
+        idx_pin[: idx.numel()].copy_(idx, non_blocking=True)
+        outs["kidx"].copy_(kidx, non_blocking=True)
+        outs["kd2"].copy_(kd2, non_blocking=True)
+        return idx.numel()
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_ms = 0.0
+    d2h = 0
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        got = e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
+        d2h = (m + 1) * 8 + got * 4 + m * kk * 8
+    e2e_ms /= args.steps
+    if ws > 1:
+        tt = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+    e2e_value = ws * 2 * m / (e2e_ms * 1e-3) / 1e6
+
+    # ---- roofline of the dominant kernel
+    peak, peak_kind = measured_peaks()
+    kernels = {}
+    dom = None
+    for name, (cnt, ms) in prof.items():
+        per_step_ms = ms / args.steps
+        kernels[name] = {"launches_per_step": cnt / args.steps, "ms_per_step": round(per_step_ms, 4)}
+        if dom is None or ms > prof[dom][1]:
+            dom = name
+    tot_k = sum(ms for _, ms in prof.values())
+    for name in kernels:
+        kernels[name]["share"] = round(prof[name][1] / tot_k, 4) if tot_k else None
+    launches = int(sum(c for c, _ in prof.values()) / args.steps)
+    roofline = None
+    if dom is not None:
+        b = kernel_bytes(dom, n, m, k, nnz, nodes)
+        dom_ms = prof[dom][1] / args.steps
+        if b is not None and dom_ms > 0:
+            achieved = b / (dom_ms * 1e-3) / 1e9
+            roofline = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                        "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                        "traffic": None, "algorithmic_bytes_per_step": int(b)}
+
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(step_ms, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: n={n} {dist_name} points, m={m} same-distribution queries, "
+                               f"radius {r:.7g} (mean 10 neighbours), k={k}",
+                   "n": n, "m": m, "k": k, "radius": r, "key_bits": 30, "parallelism": f"replicas{ws}",
+                   "l2": "flushed between steps (256 MB write)"},
+        "components": {"build_mpts_s": round(n / (build_ms * 1e-3) / 1e6, 2),
+                       "radius_mq_s": round(m / (spatial_ms * 1e-3) / 1e6, 2),
+                       "knn_mq_s": round(m / (knn_ms * 1e-3) / 1e6, 2),
+                       "build_ms": round(build_ms, 4), "radius_ms": round(spatial_ms, 4),
+                       "knn_ms": round(knn_ms, 4), "nnz": nnz},
+        "kernels": kernels,
+        "roofline": roofline,
+        "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "ms_per_step": round(e2e_ms, 4),
+                "h2d_bytes_per_step": int(p_h.nbytes + q_h.nbytes), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args, p_h, q_h, r, k, n, m, budget_s=args.cpu_budget)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------- CPU oracle arm
+
+def cpu_sample_step(p_h, q_h, r, k, n, m, sample):
+    import oracle
+    t0 = time.perf_counter()
+    tree = oracle.CpuBVH(p_h)
+    t1 = time.perf_counter()
+    qs = q_h[:sample]
+    tree.spatial(qs, r)
+    t2 = time.perf_counter()
+    tree.nearest(qs, k)
+    t3 = time.perf_counter()
+    del tree
+    est = (t1 - t0) + (m / sample) * ((t2 - t1) + (t3 - t2))
+    return est, (t1 - t0), (t2 - t1), (t3 - t2)
+
+
+def cpu_baseline(args, p_h, q_h, r, k, n, m, budget_s=20.0):
+    import oracle
+    cores = oracle.threads()
+    sample = min(m, 50_000)
+    ests = []
+    t_start = time.perf_counter()
+    while True:
+        est, tb, ts, tk = cpu_sample_step(p_h, q_h, r, k, n, m, sample)
+        ests.append(est)
+        if time.perf_counter() - t_start > budget_s * 0.5 or len(ests) >= 3:
+            break
+    est = float(np.median(ests))
+    return {"value": round(2 * m / est / 1e6, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"CPU BVH (median split, leaf 4, OpenMP) built over all {n} points; {sample} radius and "
+                      f"{sample} k={k} queries timed and scaled to m={m}; median of {len(ests)} samples",
+            "build_s": round(tb, 3), "spatial_sample_s": round(ts, 4), "knn_sample_s": round(tk, 4)}
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    dist_name, n, m, k = WORKLOADS[args.workload]
+    seed = datagen.SEED0 + 2
+    p_h, q_h = datagen.workload(dist_name, n, m, seed)
+    r = datagen.radius_for_mean(n, dist_name)
+    sample = min(m, 20_000)
+    for _ in range(args.warmup):
+        cpu_sample_step(p_h, q_h, r, k, n, m, sample)
+    ests = [cpu_sample_step(p_h, q_h, r, k, n, m, sample)[0] for _ in range(args.steps)]
+    est = float(np.mean(ests))
+    value = 2 * m / est / 1e6
+    cores = oracle.threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(est * 1e3, 2), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: n={n} {dist_name} points, m={m} same-distribution queries, "
+                               f"radius {r:.7g} (mean 10 neighbours), k={k}", "n": n, "m": m, "k": k},
+        "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"per step: CPU BVH built over all {n} points, {sample} radius + {sample} "
+                                   f"k={k} queries, scaled to m={m}"},
+        "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
+    ap.add_argument("--workload", default="cube_1e7", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "b300":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,208 @@
+/*
+ * arborx_b300.h -- C ABI of a B300 (sm_103a) linear-BVH geometric search
+ * library following ArborX (Lebrun-Grandie, Prokopenko, Turcksin, Slattery,
+ * arXiv 1908.11807).
+ *
+ * Every call takes plain pointers and sizes.  Unless stated otherwise:
+ *   - pointers named d_* are DEVICE memory of the current CUDA device, owned by
+ *     the caller and only read (inputs) or written (outputs) during the call's
+ *     stream-ordered work;
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream); all device work is enqueued on it, and calls return before it
+ *     finishes unless they say they synchronise;
+ *   - coordinates are float32, 3 per point (x, y, z) or 6 per box
+ *     (lo.x, lo.y, lo.z, hi.x, hi.y, hi.z), rows packed back to back;
+ *   - the return value is an arborx_status code; no call throws, aborts or
+ *     prints.  On a non-zero return no output is guaranteed and, for
+ *     arborx_build, no handle is created.
+ *
+ * Results are exact: a spatial query returns exactly the primitives whose box
+ * is within distance r of the query point, d^2 <= fl32(r*r) with
+ * d^2 = ((gx*gx) + (gy*gy)) + (gz*gz) evaluated in FP32 round-to-nearest
+ * without fused multiply-add (g = per-axis gap between point and box); a
+ * nearest query returns the min(k, n) primitives first in (d^2, index) order.
+ * A query with a non-finite coordinate has no neighbours.
+ */
+#ifndef ARBORX_B300_H
+#define ARBORX_B300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define ARBORX_API __attribute__((visibility("default")))
+#else
+#define ARBORX_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+typedef enum {
+  ARBORX_OK = 0,
+  ARBORX_EINVAL = 1,    /* bad argument: NULL pointer, size out of range, r < 0 or NaN, k < 1,
+                           non-finite primitive coordinate (found by the scene-box reduction) */
+  ARBORX_ENOMEM = 2,    /* a device allocation failed */
+  ARBORX_ECUDA = 3,     /* a CUDA runtime call or kernel launch failed */
+  ARBORX_ETIMEOUT = 4,  /* a bounded inter-block wait (radix-sort look-back) gave up;
+                           results of that call are invalid, the context stays usable */
+  ARBORX_EOVERFLOW = 5, /* a result would not fit: traversal stack or CSR capacity exceeded */
+  ARBORX_ESTATE = 6     /* call out of order (e.g. spatial fill without a matching count) */
+} arborx_status;
+
+/* primitive kinds */
+#define ARBORX_POINTS 0 /* d_prims is float[n][3] */
+#define ARBORX_BOXES 1  /* d_prims is float[n][6] = lo.xyz, hi.xyz (lo <= hi per axis) */
+
+/* limits */
+#define ARBORX_MAX_PRIMS ((int64_t)1 << 30) /* n must be < this */
+#define ARBORX_MAX_QUERIES ((int64_t)1 << 30) /* m must be < this */
+#define ARBORX_MAX_K 512
+
+/* Tree record layout, as exported by arborx_export_tree: float32 [2 + 2(n-1)][8].
+ * A record is (lo.x, lo.y, lo.z, enc, hi.x, hi.y, hi.z, aux), 32 bytes, with enc
+ * the bit pattern of an int32: enc >= 0 names internal node enc, enc < 0 a leaf
+ * holding primitive ~enc.  Record 0 describes the root (its box is the scene
+ * box); record 1 is reserved; the two children of internal node p are records
+ * 2 + 2p (left) and 3 + 2p (right), adjacent, so one 64-byte load tests both.
+ * Leaves are not stored separately: a child record of a leaf is its primitive's
+ * box.  aux is unspecified. */
+#define ARBORX_RECORD_FLOATS 8
+
+/* Caller-supplied device allocator (e.g. a framework's caching allocator).
+ * alloc returns device memory of at least `bytes` bytes usable on `stream`,
+ * or NULL on failure; free releases it (stream-ordered). */
+typedef void *(*arborx_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*arborx_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
+
+typedef struct arborx_opts {
+  int32_t key_bits;     /* Morton code length: 30 (default, 10 bits per axis) or 63 (21 bits per axis) */
+  int32_t sort_queries; /* 1 (default): traverse queries in Morton order (Sec. 2.2, "Query ordering");
+                           0: in input order.  Results are the same either way. */
+  int32_t validate;     /* 1 (default): arborx_build synchronises once after the scene-box reduction and
+                           returns ARBORX_EINVAL on a non-finite coordinate; 0: fully asynchronous, the
+                           error is reported by arborx_check instead */
+  int32_t keep_order;   /* 1: keep the sorted Morton codes and the leaf permutation for arborx_export_tree;
+                           0 (default): freed at the end of the build */
+  int32_t block_size;   /* traversal threads per block: 0 = default (128); 32..256, multiple of 32 */
+  int32_t stack_smem;   /* per-thread traversal-stack entries held in shared memory (0 = default 16);
+                           deeper entries spill to local memory, never dropped */
+  arborx_alloc_fn alloc; /* NULL: stream-ordered cudaMallocAsync / cudaFreeAsync */
+  arborx_free_fn free;
+  void *alloc_ctx;
+} arborx_opts;
+
+typedef struct arborx_bvh_s *arborx_handle;
+
+/* Library version string (static storage). */
+ARBORX_API const char *arborx_version(void);
+
+/* Human-readable text of a status code (static storage; unknown codes give "unknown"). */
+ARBORX_API const char *arborx_error_string(int status);
+
+/* Fill *opts with the defaults listed above.  EINVAL if opts is NULL. */
+ARBORX_API int arborx_default_opts(arborx_opts *opts);
+
+/* Build the LBVH over n primitives (Sec. 2.1, "BVH construction"): scene-box
+ * reduction, Morton codes of the box centroids scaled by the scene box, a
+ * stable radix sort of (code, index) pairs, the binary radix-tree hierarchy
+ * split at the highest differing bit of the index-augmented codes (Karras
+ * 2012), and the bottom-up box fit in which the second thread to reach a node
+ * continues (Sec. 2.1, "Calculate internal nodes bounding boxes").
+ *   d_prims  device float[n][3] (ARBORX_POINTS) or float[n][6] (ARBORX_BOXES); read only during the
+ *            build's stream work; may be freed once that work completes (the tree keeps its own copy
+ *            of every primitive box)
+ *   n        0 <= n < ARBORX_MAX_PRIMS; n = 0 gives an empty tree, n = 1 a tree whose root is the leaf
+ *   opts     NULL for defaults; copied, need not outlive the call
+ *   out      receives the handle, owned by the caller until arborx_destroy
+ * Synchronises `stream` once when opts->validate is 1 (the default). */
+ARBORX_API int arborx_build(const float *d_prims, int64_t n, int32_t kind, const arborx_opts *opts, void *stream,
+                 arborx_handle *out);
+
+/* Release every allocation of the handle, stream-ordered on the stream of the handle's last call
+ * (a handle is used from one stream at a time).  NULL is a no-op. */
+ARBORX_API int arborx_destroy(arborx_handle h);
+
+/* Number of primitives and their kind. */
+ARBORX_API int arborx_size(arborx_handle h, int64_t *n, int32_t *kind);
+
+/* Synchronise `stream` and report errors raised on the device by earlier calls on this handle
+ * (non-finite input when validate was 0, a timed-out look-back, a stack or CSR overflow);
+ * clears them. */
+ARBORX_API int arborx_check(arborx_handle h, void *stream);
+
+/* Spatial query, pass 1 of the count-and-fill scheme (Sec. 2.2, "2P"): traverse the tree for
+ * each of the m query points, count the primitives within distance `radius`, and write the
+ * exclusive prefix sum of the counts to d_offsets[0..m] (d_offsets[m] = total, int64).
+ *   d_queries  device float[m][3]; radius >= 0 and not NaN (+inf selects everything)
+ *   d_offsets  device int64[m + 1], written
+ * Keeps the query permutation in the handle for the matching arborx_query_spatial_fill.
+ * Does not synchronise. */
+ARBORX_API int arborx_query_spatial_count(arborx_handle h, const float *d_queries, int64_t m, float radius, void *stream,
+                               int64_t *d_offsets);
+
+/* Spatial query, pass 2: traverse again and write row j (the primitives within `radius` of
+ * query j) to d_indices[d_offsets[j] .. d_offsets[j+1]).  Must follow
+ * arborx_query_spatial_count on the same handle with the same d_queries, m, radius and
+ * d_offsets.  Row order within a row is the traversal order (rows are sets).
+ *   d_indices  device int32[capacity], capacity >= d_offsets[m]; writes beyond capacity are
+ *              skipped and reported as ARBORX_EOVERFLOW by arborx_check.
+ * Does not synchronise. */
+ARBORX_API int arborx_query_spatial_fill(arborx_handle h, const float *d_queries, int64_t m, float radius, void *stream,
+                              const int64_t *d_offsets, int32_t *d_indices, int64_t capacity);
+
+/* Spatial query, both passes: count, read the total back to the host (synchronises `stream`),
+ * allocate the indices with the handle's allocator, fill.
+ *   d_offsets   device int64[m + 1], written (CSR offsets, original query order)
+ *   d_indices   receives a device int32[*nnz] array allocated with the handle's allocator
+ *               (opts.alloc, else cudaMallocAsync); release it with arborx_free
+ *   nnz         receives the total number of results */
+ARBORX_API int arborx_query_spatial(arborx_handle h, const float *d_queries, int64_t m, float radius, void *stream,
+                         int64_t *d_offsets, int32_t **d_indices, int64_t *nnz);
+
+/* Release memory returned by arborx_query_spatial (stream-ordered on `stream`). */
+ARBORX_API int arborx_free(arborx_handle h, void *d_ptr, size_t bytes, void *stream);
+
+/* Nearest query (Sec. 2.2, "Traversal for nearest queries"): for each query, the kk = min(k, n)
+ * primitives first in (d^2, index) order, found by a stack traversal that visits the closer
+ * child first and skips a node whose box distance exceeds the current k-th candidate.
+ *   k           1 <= k <= ARBORX_MAX_K
+ *   d_offsets   NULL or device int64[m + 1]: written with j * kk (CSR view of the rows)
+ *   d_indices   device int32[m * kk]: row j holds query j's neighbours in (d^2, index) order;
+ *               -1 where a query has fewer (non-finite query)
+ *   d_dist2     NULL or device float[m * kk]: the matching squared distances (+inf for -1)
+ * Does not synchronise. */
+ARBORX_API int arborx_query_nearest(arborx_handle h, const float *d_queries, int64_t m, int32_t k, void *stream,
+                         int64_t *d_offsets, int32_t *d_indices, float *d_dist2);
+
+/* Copy the tree out for inspection (device to device, stream-ordered):
+ *   d_records  NULL or device float[(2 + 2(n-1)) * 8] in the record layout above (n >= 1)
+ *   d_scene    NULL or device float[6]: the scene box lo.xyz, hi.xyz
+ *   d_codes    NULL or device uint64[n]: sorted Morton codes (needs opts.keep_order = 1)
+ *   d_perm     NULL or device uint32[n]: primitive index of each sorted leaf (needs keep_order)
+ * ESTATE if codes / perm are requested but were not kept. */
+ARBORX_API int arborx_export_tree(arborx_handle h, void *stream, float *d_records, float *d_scene, uint64_t *d_codes,
+                       uint32_t *d_perm);
+
+/* Stable ascending radix sort of n keys of key_bits significant bits (the sort step of the
+ * build, Sec. 2.1, exposed on its own): keys are uint32 when key_bits <= 32, else uint64;
+ * d_keys is sorted in place and d_perm receives, for each output position, the input position
+ * of its key (ties keep input order).  Needs temporary memory from cudaMallocAsync.
+ *   1 <= key_bits <= 64; 0 <= n < ARBORX_MAX_PRIMS */
+ARBORX_API int arborx_sort_pairs(void *d_keys, uint32_t *d_perm, int64_t n, int32_t key_bits, void *stream);
+
+/* Process-wide kernel timing.  With on = 1, every kernel launch of the library is bracketed by a
+ * pair of CUDA events on its stream (a few microseconds of host overhead per launch). */
+ARBORX_API int arborx_profile_enable(int on);
+
+/* Wait for the recorded events, then write one line per kernel name, "name launches total_ms\n",
+ * into buf (NUL-terminated, at most cap bytes) and reset the counters.  EOVERFLOW if truncated. */
+ARBORX_API int arborx_profile_report(char *buf, size_t cap);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ARBORX_B300_H */

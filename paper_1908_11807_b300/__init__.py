@@ -1,0 +1,24 @@
+"""B300-native linear-BVH geometric search (ArborX, arXiv 1908.11807).
+
+The compute path is the CUDA library ``libarborx_b300.so`` (sm_103a), reached
+through its C ABI (``include/arborx_b300.h``); this package is the thin Python
+binding over it.  PyTorch supplies device memory and streams only.
+"""
+from ._binding import (  # noqa: F401
+    ARBORX_BOXES,
+    ARBORX_MAX_K,
+    ARBORX_POINTS,
+    ArborXError,
+    BVH,
+    arborx_build,
+    arborx_query_nearest,
+    arborx_query_spatial,
+    arborx_sort_pairs,
+    default_opts,
+    profile_enable,
+    profile_report,
+    error_string,
+    lib,
+    version,
+    LIB_PATH,
+)

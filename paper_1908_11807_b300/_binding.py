@@ -1,0 +1,267 @@
+"""Thin ctypes binding of ``libarborx_b300.so`` (argument marshalling only).
+
+Every step of the search runs in the library's CUDA kernels; this module only
+passes device pointers, sizes and the current torch stream.  Tensors must be
+contiguous CUDA tensors on the current device.  If the library has not been
+built the import fails loudly: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Tuple
+
+import torch
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libarborx_b300.so")
+
+ARBORX_OK = 0
+ARBORX_EINVAL = 1
+ARBORX_ENOMEM = 2
+ARBORX_ECUDA = 3
+ARBORX_ETIMEOUT = 4
+ARBORX_EOVERFLOW = 5
+ARBORX_ESTATE = 6
+ARBORX_POINTS = 0
+ARBORX_BOXES = 1
+ARBORX_MAX_K = 512
+
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class arborx_opts(ctypes.Structure):
+    _fields_ = [
+        ("key_bits", ctypes.c_int32),
+        ("sort_queries", ctypes.c_int32),
+        ("validate", ctypes.c_int32),
+        ("keep_order", ctypes.c_int32),
+        ("block_size", ctypes.c_int32),
+        ("stack_smem", ctypes.c_int32),
+        ("alloc", _ALLOC_FN),
+        ("free", _FREE_FN),
+        ("alloc_ctx", ctypes.c_void_p),
+    ]
+
+
+class ArborXError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {error_string(code)} (status {code})")
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load the CUDA library (fails loudly if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_1908_11807_b300.build_ext` "
+                              "(or __graft_entry__.build()); there is no CPU fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+        L.arborx_version.restype = ctypes.c_char_p
+        L.arborx_error_string.restype = ctypes.c_char_p
+        L.arborx_error_string.argtypes = [ctypes.c_int]
+        L.arborx_default_opts.argtypes = [ctypes.POINTER(arborx_opts)]
+        L.arborx_build.argtypes = [vp, i64, i32, ctypes.POINTER(arborx_opts), vp, ctypes.POINTER(vp)]
+        L.arborx_destroy.argtypes = [vp]
+        L.arborx_size.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i32)]
+        L.arborx_check.argtypes = [vp, vp]
+        L.arborx_query_spatial_count.argtypes = [vp, vp, i64, ctypes.c_float, vp, vp]
+        L.arborx_query_spatial_fill.argtypes = [vp, vp, i64, ctypes.c_float, vp, vp, vp, i64]
+        L.arborx_query_spatial.argtypes = [vp, vp, i64, ctypes.c_float, vp, vp, ctypes.POINTER(vp),
+                                           ctypes.POINTER(i64)]
+        L.arborx_free.argtypes = [vp, vp, ctypes.c_size_t, vp]
+        L.arborx_query_nearest.argtypes = [vp, vp, i64, i32, vp, vp, vp, vp]
+        L.arborx_export_tree.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.arborx_sort_pairs.argtypes = [vp, vp, i64, i32, vp]
+        L.arborx_profile_enable.argtypes = [ctypes.c_int]
+        L.arborx_profile_report.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
+        _lib = L
+    return _lib
+
+
+def error_string(code: int) -> str:
+    return lib().arborx_error_string(int(code)).decode()
+
+
+def version() -> str:
+    return lib().arborx_version().decode()
+
+
+def _check(code: int, where: str) -> None:
+    if code != ARBORX_OK:
+        raise ArborXError(code, where)
+
+
+def _stream() -> int:
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _as_f32_cuda(x: torch.Tensor, width: int, name: str) -> torch.Tensor:
+    if not isinstance(x, torch.Tensor) or not x.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if x.dtype != torch.float32:
+        raise TypeError(f"{name} must be float32")
+    if x.dim() != 2 or x.shape[1] != width:
+        raise ValueError(f"{name} must have shape [n][{width}]")
+    return x.contiguous()
+
+
+def default_opts(**kw) -> arborx_opts:
+    o = arborx_opts()
+    _check(lib().arborx_default_opts(ctypes.byref(o)), "arborx_default_opts")
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+class BVH:
+    """A linear BVH on the current CUDA device (wraps an ``arborx_handle``)."""
+
+    def __init__(self, prims: torch.Tensor, kind: Optional[int] = None, **opts):
+        if kind is None:
+            kind = ARBORX_POINTS if prims.dim() == 2 and prims.shape[1] == 3 else ARBORX_BOXES
+        width = 3 if kind == ARBORX_POINTS else 6
+        self.prims = _as_f32_cuda(prims, width, "prims")
+        self.kind = int(kind)
+        self.n = int(self.prims.shape[0])
+        self.opts = default_opts(**opts)
+        h = ctypes.c_void_p()
+        _check(lib().arborx_build(_ptr(self.prims), self.n, self.kind, ctypes.byref(self.opts), _stream(),
+                                  ctypes.byref(h)), "arborx_build")
+        self._h = h
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        if self._h is None:
+            raise RuntimeError("BVH destroyed")
+        return self._h
+
+    def destroy(self) -> None:
+        if getattr(self, "_h", None) is not None:
+            lib().arborx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def check(self) -> None:
+        """Synchronise and raise if a kernel reported an error on this tree."""
+        _check(lib().arborx_check(self.handle, _stream()), "arborx_check")
+
+    # -- spatial (2P)
+    def query_spatial_count(self, queries: torch.Tensor, radius: float,
+                            offsets: Optional[torch.Tensor] = None) -> torch.Tensor:
+        q = _as_f32_cuda(queries, 3, "queries")
+        m = q.shape[0]
+        if offsets is None:
+            offsets = torch.empty(m + 1, dtype=torch.int64, device=q.device)
+        _check(lib().arborx_query_spatial_count(self.handle, _ptr(q), m, ctypes.c_float(radius), _stream(),
+                                                _ptr(offsets)), "arborx_query_spatial_count")
+        self._count_q = q
+        return offsets
+
+    def query_spatial_fill(self, queries: torch.Tensor, radius: float, offsets: torch.Tensor,
+                           indices: torch.Tensor) -> torch.Tensor:
+        q = getattr(self, "_count_q", None)  # the exact buffer the count pass traversed
+        if q is None:
+            raise ArborXError(ARBORX_ESTATE, "arborx_query_spatial_fill")
+        _check(lib().arborx_query_spatial_fill(self.handle, _ptr(q), q.shape[0], ctypes.c_float(radius),
+                                               _stream(), _ptr(offsets), _ptr(indices), indices.numel()),
+               "arborx_query_spatial_fill")
+        return indices
+
+    def query_spatial(self, queries: torch.Tensor, radius: float) -> Tuple[torch.Tensor, torch.Tensor]:
+        """CSR (offsets int64 [m+1], indices int32 [nnz]) of the primitives within
+        ``radius`` of each query (count, read the total back, fill)."""
+        offsets = self.query_spatial_count(queries, radius)
+        nnz = int(offsets[-1].item())
+        self.check()
+        indices = torch.empty(nnz, dtype=torch.int32, device=offsets.device)
+        self.query_spatial_fill(queries, radius, offsets, indices)
+        return offsets, indices
+
+    # -- nearest
+    def query_nearest(self, queries: torch.Tensor, k: int, return_dist2: bool = True,
+                      with_offsets: bool = False):
+        """Rows [m][min(k, n)] of neighbour indices (int32) in (d2, index) order,
+        and their squared distances (float32) if requested."""
+        q = _as_f32_cuda(queries, 3, "queries")
+        m = q.shape[0]
+        kk = min(int(k), self.n)
+        idx = torch.empty((m, kk), dtype=torch.int32, device=q.device)
+        d2 = torch.empty((m, kk), dtype=torch.float32, device=q.device) if return_dist2 else None
+        off = torch.empty(m + 1, dtype=torch.int64, device=q.device) if with_offsets else None
+        _check(lib().arborx_query_nearest(self.handle, _ptr(q), m, int(k), _stream(), _ptr(off), _ptr(idx),
+                                          _ptr(d2)), "arborx_query_nearest")
+        out = (idx, d2) if return_dist2 else (idx,)
+        if with_offsets:
+            out = out + (off,)
+        return out if len(out) > 1 else out[0]
+
+    # -- inspection
+    def export_tree(self, order: bool = False):
+        """(records float32 [2+2(n-1)][8], scene float32 [6], codes uint64 [n] | None, perm int32 [n] | None)."""
+        dev = self.prims.device
+        n = self.n
+        rec = torch.empty((2 + 2 * max(n - 1, 0), 8), dtype=torch.float32, device=dev) if n > 0 else None
+        scene = torch.empty(6, dtype=torch.float32, device=dev)
+        codes = torch.empty(n, dtype=torch.int64, device=dev) if order else None
+        perm = torch.empty(n, dtype=torch.int32, device=dev) if order else None
+        _check(lib().arborx_export_tree(self.handle, _stream(), _ptr(rec), _ptr(scene), _ptr(codes), _ptr(perm)),
+               "arborx_export_tree")
+        return rec, scene, codes, perm
+
+
+def arborx_build(prims: torch.Tensor, kind: Optional[int] = None, **opts) -> BVH:
+    return BVH(prims, kind, **opts)
+
+
+def arborx_query_spatial(bvh: BVH, queries: torch.Tensor, radius: float):
+    return bvh.query_spatial(queries, radius)
+
+
+def arborx_query_nearest(bvh: BVH, queries: torch.Tensor, k: int, return_dist2: bool = True):
+    return bvh.query_nearest(queries, k, return_dist2)
+
+
+def arborx_sort_pairs(keys: torch.Tensor, key_bits: int) -> Tuple[torch.Tensor, torch.Tensor]:
+    """Stable radix sort of int32/int64 keys (treated as unsigned, key_bits significant
+    bits) on the GPU: (sorted keys, permutation int32)."""
+    if keys.dtype not in (torch.int32, torch.int64) or not keys.is_cuda:
+        raise TypeError("keys must be an int32 or int64 CUDA tensor")
+    if (keys.dtype == torch.int32) != (key_bits <= 32):
+        raise ValueError("int32 keys need key_bits <= 32, int64 keys key_bits > 32")
+    k = keys.contiguous().clone()
+    perm = torch.empty(k.numel(), dtype=torch.int32, device=k.device)
+    _check(lib().arborx_sort_pairs(_ptr(k), _ptr(perm), k.numel(), int(key_bits), _stream()), "arborx_sort_pairs")
+    return k, perm
+
+
+def profile_enable(on: bool = True) -> None:
+    """Bracket every library kernel launch with CUDA events (process-wide)."""
+    _check(lib().arborx_profile_enable(1 if on else 0), "arborx_profile_enable")
+
+
+def profile_report() -> dict:
+    """{kernel name: (launches, total device ms)} since the last report; resets."""
+    buf = ctypes.create_string_buffer(1 << 16)
+    _check(lib().arborx_profile_report(buf, len(buf)), "arborx_profile_report")
+    out = {}
+    for line in buf.value.decode().splitlines():
+        name, cnt, ms = line.split()
+        out[name] = (int(cnt), float(ms))
+    return out

@@ -1,0 +1,373 @@
+// LBVH construction kernels (ArborX Sec. 2.1): scene box, Morton codes with
+// fused radix histograms, binary radix-tree hierarchy, bottom-up box fit.
+#include <algorithm>
+
+#include "kernels.cuh"
+#include "prof.cuh"
+#include "radix_sort.cuh"
+
+namespace abx {
+
+namespace {
+
+__device__ __forceinline__ void acc_axis(float v, float &mn, float &mx, uint32_t &bad) {
+  const bool ok = is_finite_bits(v);
+  bad += ok ? 0u : 1u;
+  mn = fminf(mn, ok ? v : __int_as_float(0x7f800000));
+  mx = fmaxf(mx, ok ? v : __int_as_float(0xff800000));
+}
+
+// Scene box: per-axis min / max over every coordinate of every box corner.
+// The coordinate array is nf floats, coordinate i belonging to axis i % 3 for
+// both points (3 per row) and boxes (6 per row).
+__global__ void __launch_bounds__(256) k_bounds(const float *__restrict__ f, uint64_t nf, bool vec,
+                                               DevMeta *__restrict__ meta) {
+  float mn[3], mx[3];
+  uint32_t bad = 0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    mn[a] = __int_as_float(0x7f800000);
+    mx[a] = __int_as_float(0xff800000);
+  }
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t groups = vec ? nf / 12 : 0;  // 12 floats = 3 float4 = axes x y z x | y z x y | z x y z
+  const float4 *f4 = reinterpret_cast<const float4 *>(f);
+  for (uint64_t g = tid; g < groups; g += stride) {
+    const float4 a = __ldg(f4 + 3 * g), b = __ldg(f4 + 3 * g + 1), c = __ldg(f4 + 3 * g + 2);
+    acc_axis(a.x, mn[0], mx[0], bad); acc_axis(a.y, mn[1], mx[1], bad); acc_axis(a.z, mn[2], mx[2], bad);
+    acc_axis(a.w, mn[0], mx[0], bad); acc_axis(b.x, mn[1], mx[1], bad); acc_axis(b.y, mn[2], mx[2], bad);
+    acc_axis(b.z, mn[0], mx[0], bad); acc_axis(b.w, mn[1], mx[1], bad); acc_axis(c.x, mn[2], mx[2], bad);
+    acc_axis(c.y, mn[0], mx[0], bad); acc_axis(c.z, mn[1], mx[1], bad); acc_axis(c.w, mn[2], mx[2], bad);
+  }
+  for (uint64_t i = groups * 12 + tid; i < nf; i += stride) {
+    const int a = (int)(i % 3);
+    acc_axis(f[i], mn[a], mx[a], bad);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      mn[a] = fminf(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], o));
+      mx[a] = fmaxf(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
+    }
+    bad += __shfl_xor_sync(0xffffffffu, bad, o);
+  }
+  __shared__ float s_v[8][6];
+  __shared__ uint32_t s_bad[8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      s_v[warp][a] = mn[a];
+      s_v[warp][3 + a] = mx[a];
+    }
+    s_bad[warp] = bad;
+  }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    const int a = threadIdx.x;
+    float v = s_v[0][a];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v = a < 3 ? fminf(v, s_v[w][a]) : fmaxf(v, s_v[w][a]);
+    if (a < 3) atomicMin(&meta->bounds_ord[a], f2ord(v));
+    else atomicMax(&meta->bounds_ord[a], f2ord(v));
+  } else if (threadIdx.x == 32) {
+    uint32_t b = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += s_bad[w];
+    if (b) {
+      atomicAdd(&meta->nonfinite, b);
+      atomicOr(&meta->err, ERR_NONFINITE);
+    }
+  }
+}
+
+__global__ void k_init_meta(DevMeta *meta) {
+  const int t = threadIdx.x;
+  if (t < 3) meta->bounds_ord[t] = 0xffffffffu;
+  else if (t < 6) meta->bounds_ord[t] = 0u;
+  else if (t == 6) meta->nonfinite = 0;
+  else if (t == 7) meta->err = 0;
+  else if (t >= 8 && t < 11) meta->scene[t - 8] = __int_as_float(0x7f800000);   // empty box: +inf
+  else if (t >= 11 && t < 14) meta->scene[t - 8] = __int_as_float(0xff800000);  // -inf
+}
+
+// ------------------------------------------------------------ Morton codes
+
+template <int BITS>
+__device__ __forceinline__ uint32_t quantise(float c, float L, float H) {
+  const float ext = __fsub_rn(H, L);
+  float u = 0.0f;
+  if (ext > 0.0f) u = __fdiv_rn(__fsub_rn(c, L), ext);
+  if (!(u >= 0.0f)) u = 0.0f;  // also NaN
+  if (u > 1.0f) u = 1.0f;
+  const uint32_t q = (uint32_t)floorf(__fmul_rn(u, (float)(1u << BITS)));
+  return min(q, (1u << BITS) - 1u);
+}
+
+__device__ __forceinline__ uint32_t spread10(uint32_t x) {
+  x &= 0x3ffu;
+  x = (x | (x << 16)) & 0x030000FFu;
+  x = (x | (x << 8)) & 0x0300F00Fu;
+  x = (x | (x << 4)) & 0x030C30C3u;
+  x = (x | (x << 2)) & 0x09249249u;
+  return x;
+}
+
+__device__ __forceinline__ uint64_t spread21(uint64_t x) {
+  x &= 0x1fffffull;
+  x = (x | (x << 32)) & 0x1f00000000ffffull;
+  x = (x | (x << 16)) & 0x1f0000ff0000ffull;
+  x = (x | (x << 8)) & 0x100f00f00f00f00full;
+  x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+  x = (x | (x << 2)) & 0x1249249249249249ull;
+  return x;
+}
+
+template <typename K>
+__device__ __forceinline__ K morton(float cx, float cy, float cz, const float *sc);
+
+template <>
+__device__ __forceinline__ uint32_t morton<uint32_t>(float cx, float cy, float cz, const float *sc) {
+  return (spread10(quantise<10>(cx, sc[0], sc[3])) << 2) | (spread10(quantise<10>(cy, sc[1], sc[4])) << 1) |
+         spread10(quantise<10>(cz, sc[2], sc[5]));
+}
+template <>
+__device__ __forceinline__ uint64_t morton<uint64_t>(float cx, float cy, float cz, const float *sc) {
+  return (spread21(quantise<21>(cx, sc[0], sc[3])) << 2) | (spread21(quantise<21>(cy, sc[1], sc[4])) << 1) |
+         spread21(quantise<21>(cz, sc[2], sc[5]));
+}
+
+template <typename K>
+__device__ __forceinline__ void hist_add(uint32_t (*s_h)[kRadix], int passes, K code) {
+  for (int p = 0; p < passes; ++p) atomicAdd(&s_h[p][(uint32_t)(code >> (p * kRadixBits)) & (kRadix - 1)], 1u);
+}
+
+// Morton code of each primitive's centroid (points: the point; boxes: the box
+// centre), scaled by the scene box in `meta`; histograms of every radix pass.
+template <typename K, int KIND>
+__global__ void __launch_bounds__(256) k_morton(const float *__restrict__ prims, uint32_t n, bool vec,
+                                               DevMeta *__restrict__ meta, K *__restrict__ codes,
+                                               uint32_t *__restrict__ hist, int passes, bool write_scene) {
+  __shared__ uint32_t s_h[8][kRadix];
+  __shared__ float s_sc[6];
+  for (int i = threadIdx.x; i < passes * kRadix; i += blockDim.x) (&s_h[0][0])[i] = 0;
+  if (threadIdx.x < 6) s_sc[threadIdx.x] = ord2f(meta->bounds_ord[threadIdx.x]);
+  __syncthreads();
+  if (write_scene && blockIdx.x == 0 && threadIdx.x < 6) meta->scene[threadIdx.x] = s_sc[threadIdx.x];
+  float sc[6];
+#pragma unroll
+  for (int a = 0; a < 6; ++a) sc[a] = s_sc[a];
+
+  constexpr int PER = KIND == 0 ? 3 : 6;  // floats per primitive
+  constexpr int GP = 12 / PER;            // primitives per 3-float4 group
+  const uint32_t stride = gridDim.x * blockDim.x;
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t groups = vec ? n / GP : 0;
+  const float4 *f4 = reinterpret_cast<const float4 *>(prims);
+  for (uint32_t g = tid; g < groups; g += stride) {
+    const float4 a = __ldg(f4 + 3 * (uint64_t)g), b = __ldg(f4 + 3 * (uint64_t)g + 1),
+                 c = __ldg(f4 + 3 * (uint64_t)g + 2);
+    const float v[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
+    K out[GP];
+#pragma unroll
+    for (int j = 0; j < GP; ++j) {
+      float cx, cy, cz;
+      if (KIND == 0) {
+        cx = v[3 * j]; cy = v[3 * j + 1]; cz = v[3 * j + 2];
+      } else {
+        cx = __fmul_rn(__fadd_rn(v[6 * j], v[6 * j + 3]), 0.5f);
+        cy = __fmul_rn(__fadd_rn(v[6 * j + 1], v[6 * j + 4]), 0.5f);
+        cz = __fmul_rn(__fadd_rn(v[6 * j + 2], v[6 * j + 5]), 0.5f);
+      }
+      out[j] = morton<K>(cx, cy, cz, sc);
+      hist_add<K>(s_h, passes, out[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < GP; ++j) codes[(uint64_t)g * GP + j] = out[j];
+  }
+  for (uint32_t i = groups * GP + tid; i < n; i += stride) {
+    const float *p = prims + (uint64_t)i * PER;
+    float cx, cy, cz;
+    if (KIND == 0) {
+      cx = p[0]; cy = p[1]; cz = p[2];
+    } else {
+      cx = __fmul_rn(__fadd_rn(p[0], p[3]), 0.5f);
+      cy = __fmul_rn(__fadd_rn(p[1], p[4]), 0.5f);
+      cz = __fmul_rn(__fadd_rn(p[2], p[5]), 0.5f);
+    }
+    const K code = morton<K>(cx, cy, cz, sc);
+    codes[i] = code;
+    hist_add<K>(s_h, passes, code);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < passes * kRadix; i += blockDim.x) {
+    const uint32_t c = (&s_h[0][0])[i];
+    if (c) atomicAdd(&hist[i], c);
+  }
+}
+
+// ------------------------------------------------------------ hierarchy
+
+template <typename K>
+__device__ __forceinline__ int clz_key(K x);
+template <>
+__device__ __forceinline__ int clz_key<uint32_t>(uint32_t x) { return __clz(x); }
+template <>
+__device__ __forceinline__ int clz_key<uint64_t>(uint64_t x) { return __clzll(x); }
+
+// Length of the common prefix of the index-augmented keys (code_i, i) and
+// (code_j, j); -1 outside [0, n).
+template <typename K>
+__device__ __forceinline__ int delta(const K *__restrict__ codes, K ci, int i, int j, int n) {
+  if (j < 0 || j >= n) return -1;
+  const K cj = codes[j];
+  if (cj != ci) return clz_key<K>(ci ^ cj);
+  return (int)(8 * sizeof(K)) + __clz((uint32_t)(i ^ j));
+}
+
+// Internal node i (of n - 1) finds the range of sorted leaves it covers and the
+// split inside it where the highest differing bit of the augmented keys flips
+// (binary radix tree, Karras 2012); records parent links (p << 1 | side) of its
+// two children.  Node ids: internal 0 .. n-2 (root 0), leaf t is n - 1 + t.
+template <typename K>
+__global__ void __launch_bounds__(256) k_hierarchy(const K *__restrict__ codes, uint32_t n,
+                                                  int32_t *__restrict__ parent) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int N = (int)n;
+  if (i >= N - 1) return;
+  const K ci = codes[i];
+  const int dl = delta<K>(codes, ci, i, i - 1, N);
+  const int dr = delta<K>(codes, ci, i, i + 1, N);
+  const int d = dr > dl ? 1 : -1;
+  const int dmin = min(dl, dr);
+  int lmax = 2;
+  while (delta<K>(codes, ci, i, i + lmax * d, N) > dmin) lmax <<= 1;
+  int l = 0;
+  for (int t = lmax >> 1; t >= 1; t >>= 1)
+    if (delta<K>(codes, ci, i, i + (l + t) * d, N) > dmin) l += t;
+  const int j = i + l * d;
+  const int dnode = delta<K>(codes, ci, i, j, N);
+  int s = 0, t = l;
+  do {
+    t = (t + 1) >> 1;
+    if (delta<K>(codes, ci, i, i + (s + t) * d, N) > dnode) s += t;
+  } while (t > 1);
+  const int gamma = i + s * d + min(d, 0);
+  const int left = (min(i, j) == gamma) ? (N - 1 + gamma) : gamma;
+  const int right = (max(i, j) == gamma + 1) ? (N - 1 + gamma + 1) : gamma + 1;
+  parent[left] = (i << 1);
+  parent[right] = (i << 1) | 1;
+}
+
+// Bottom-up fit: one thread per sorted leaf writes its primitive's box into its
+// parent's child slot, then climbs; at each internal node the first arriving
+// thread stops and the second merges both child boxes and continues.
+template <int KIND>
+__global__ void __launch_bounds__(256) k_fit(const float *__restrict__ prims, uint32_t n,
+                                            const uint32_t *__restrict__ perm, const int32_t *__restrict__ parent,
+                                            uint32_t *__restrict__ arrival, float4 *__restrict__ rec,
+                                            uint32_t *__restrict__ err) {
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const uint32_t prim = perm[t];
+  float lx, ly, lz, hx, hy, hz;
+  if (KIND == 0) {
+    const float *p = prims + 3 * (uint64_t)prim;
+    lx = hx = p[0]; ly = hy = p[1]; lz = hz = p[2];
+  } else {
+    const float *p = prims + 6 * (uint64_t)prim;
+    lx = p[0]; ly = p[1]; lz = p[2]; hx = p[3]; hy = p[4]; hz = p[5];
+  }
+  int enc = ~(int)prim;
+  if (n == 1) {
+    rec[0] = make_float4(lx, ly, lz, __int_as_float(enc));
+    rec[1] = make_float4(hx, hy, hz, 0.0f);
+    return;
+  }
+  int c = (int)n - 1 + (int)t;
+  for (int level = 0;; ++level) {
+    const int pp = __ldg(parent + c);
+    const int p = pp >> 1, side = pp & 1;
+    if (pp < 0 || p >= (int)n - 1 || level > 128) {  // broken hierarchy: report, never write outside
+      set_err(err, ERR_STACK);
+      return;
+    }
+    float4 *slot = rec + 4 + 4 * (uint64_t)p + 2 * side;
+    slot[0] = make_float4(lx, ly, lz, __int_as_float(enc));
+    slot[1] = make_float4(hx, hy, hz, 0.0f);
+    if (atom_add_acq_rel_gpu(arrival + p, 1u) == 0u) return;  // sibling not done yet
+    const float4 *sib = rec + 4 + 4 * (uint64_t)p + 2 * (1 - side);
+    const float4 slo = ld_cg_f4(sib), shi = ld_cg_f4(sib + 1);
+    lx = fminf(lx, slo.x); ly = fminf(ly, slo.y); lz = fminf(lz, slo.z);
+    hx = fmaxf(hx, shi.x); hy = fmaxf(hy, shi.y); hz = fmaxf(hz, shi.z);
+    enc = p;
+    c = p;
+    if (p == 0) {
+      rec[0] = make_float4(lx, ly, lz, __int_as_float(0));
+      rec[1] = make_float4(hx, hy, hz, 0.0f);
+      return;
+    }
+  }
+}
+
+int sm_count() {
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms;
+}
+
+}  // namespace
+
+void launch_init_meta(DevMeta *meta, cudaStream_t s) { k_init_meta<<<1, 32, 0, s>>>(meta); }
+
+void launch_bounds(const float *prims, int64_t n, int kind, DevMeta *meta, cudaStream_t s) {
+  const uint64_t nf = (uint64_t)n * (kind == 0 ? 3 : 6);
+  if (nf == 0) return;
+  const bool vec = (reinterpret_cast<uintptr_t>(prims) & 15u) == 0;
+  const uint64_t work = vec ? nf / 12 + 1 : nf;
+  const uint32_t blocks = (uint32_t)std::min<uint64_t>(ceil_div<uint64_t>(work, 256), (uint64_t)sm_count() * 8);
+  prof::Scope ps(s, "bounds");
+  k_bounds<<<blocks, 256, 0, s>>>(prims, nf, vec, meta);
+}
+
+template <typename K>
+void launch_morton(const float *prims, uint32_t n, int kind, DevMeta *meta, K *codes, uint32_t *hist, int passes,
+                   bool write_scene, cudaStream_t s) {
+  if (n == 0) return;
+  const bool vec = (reinterpret_cast<uintptr_t>(prims) & 15u) == 0;
+  const uint32_t per_thread = kind == 0 ? 4 : 2;
+  const uint32_t blocks = std::min<uint32_t>(ceil_div<uint32_t>(ceil_div<uint32_t>(n, per_thread), 256u),
+                                        (uint32_t)sm_count() * 8u);
+  prof::Scope ps(s, "morton");
+  if (kind == 0)
+    k_morton<K, 0><<<blocks, 256, 0, s>>>(prims, n, vec, meta, codes, hist, passes, write_scene);
+  else
+    k_morton<K, 1><<<blocks, 256, 0, s>>>(prims, n, vec, meta, codes, hist, passes, write_scene);
+}
+
+template <typename K>
+void launch_hierarchy(const K *codes, uint32_t n, int32_t *parent, cudaStream_t s) {
+  if (n < 2) return;
+  prof::Scope ps(s, "hierarchy");
+  k_hierarchy<K><<<ceil_div<uint32_t>(n - 1, 256u), 256, 0, s>>>(codes, n, parent);
+}
+
+void launch_fit(const float *prims, uint32_t n, int kind, const uint32_t *perm, const int32_t *parent,
+                uint32_t *arrival, float4 *rec, uint32_t *err, cudaStream_t s) {
+  if (n == 0) return;
+  prof::Scope ps(s, "fit");
+  if (kind == 0)
+    k_fit<0><<<ceil_div<uint32_t>(n, 256u), 256, 0, s>>>(prims, n, perm, parent, arrival, rec, err);
+  else
+    k_fit<1><<<ceil_div<uint32_t>(n, 256u), 256, 0, s>>>(prims, n, perm, parent, arrival, rec, err);
+}
+
+template void launch_morton<uint32_t>(const float *, uint32_t, int, DevMeta *, uint32_t *, uint32_t *, int, bool,
+                                      cudaStream_t);
+template void launch_morton<uint64_t>(const float *, uint32_t, int, DevMeta *, uint64_t *, uint32_t *, int, bool,
+                                      cudaStream_t);
+template void launch_hierarchy<uint32_t>(const uint32_t *, uint32_t, int32_t *, cudaStream_t);
+template void launch_hierarchy<uint64_t>(const uint64_t *, uint32_t, int32_t *, cudaStream_t);
+
+}  // namespace abx

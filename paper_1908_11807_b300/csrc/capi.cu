@@ -1,0 +1,514 @@
+// C ABI of the LBVH library: handles, memory, argument checks and the launch
+// sequences of the build and the queries (ArborX Sec. 2.1 - 2.3).
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "../../include/arborx_b300.h"
+#include "kernels.cuh"
+#include "radix_sort.cuh"
+
+using namespace abx;
+
+struct arborx_bvh_s {
+  int device;
+  int64_t n;
+  int32_t kind;
+  arborx_opts opts;
+  cudaStream_t stream;  // build stream (used to release memory)
+  // persistent: DevMeta followed by the records
+  void *persist;
+  size_t persist_bytes;
+  DevMeta *meta;
+  float4 *rec;
+  // sorted codes + permutation (keep_order)
+  void *order;
+  size_t order_bytes;
+  // query workspace, grown on demand
+  void *qws;
+  size_t qws_bytes;
+  // state handed from spatial count to spatial fill
+  const uint32_t *qperm;
+  const float *count_queries;
+  int64_t count_m;
+  float count_radius;
+  bool count_valid;
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+struct Carver {
+  char *base;
+  size_t off = 0;
+  explicit Carver(void *b) : base((char *)b) {}
+  template <typename T>
+  T *take(size_t count) {
+    T *p = (T *)(base + off);
+    off += align_up(count * sizeof(T));
+    return p;
+  }
+};
+
+void *dev_alloc(const arborx_opts &o, size_t bytes, cudaStream_t s) {
+  if (bytes == 0) bytes = kAlign;
+  if (o.alloc) return o.alloc(bytes, (void *)s, o.alloc_ctx);
+  void *p = nullptr;
+  if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+void dev_free(const arborx_opts &o, void *p, size_t bytes, cudaStream_t s) {
+  if (!p) return;
+  if (bytes == 0) bytes = kAlign;
+  if (o.free) {
+    o.free(p, bytes, (void *)s, o.alloc_ctx);
+    return;
+  }
+  cudaFreeAsync(p, s);
+}
+
+int launch_status() {
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? ARBORX_OK : ARBORX_ECUDA;
+}
+
+int err_bits_to_status(uint32_t bits) {
+  if (bits & ERR_NONFINITE) return ARBORX_EINVAL;
+  if (bits & ERR_TIMEOUT) return ARBORX_ETIMEOUT;
+  if (bits & (ERR_STACK | ERR_CSR)) return ARBORX_EOVERFLOW;
+  return ARBORX_OK;
+}
+
+TravCfg trav_cfg(const arborx_opts &o) {
+  TravCfg c;
+  c.block = o.block_size > 0 ? o.block_size : 128;
+  c.stack_smem = o.stack_smem > 0 ? o.stack_smem : 16;
+  return c;
+}
+
+bool opts_ok(const arborx_opts &o) {
+  if (o.key_bits != 30 && o.key_bits != 63) return false;
+  if (o.block_size != 0 && (o.block_size < 32 || o.block_size > 256 || o.block_size % 32)) return false;
+  if (o.stack_smem < 0 || o.stack_smem > 64) return false;
+  if ((o.alloc == nullptr) != (o.free == nullptr)) return false;
+  return true;
+}
+
+// Sort (keys, iota) with the onesweep passes; keys already in kA, histogram
+// already in ws.hist.  Returns pointers to the sorted keys / permutation.
+template <typename K>
+void sort_pairs(K *kA, K *kB, uint32_t *vA, uint32_t *vB, uint32_t n, const SortWs &ws, uint32_t *err,
+                cudaStream_t s, K **sorted_keys, uint32_t **perm) {
+  const bool inA = launch_onesweep<K>(kA, kB, vA, vB, n, ws, err, s);
+  *sorted_keys = inA ? kA : kB;
+  *perm = inA ? vA : vB;
+}
+
+template <typename K>
+int build_impl(arborx_bvh_s *h, const float *d_prims, cudaStream_t s) {
+  const int64_t n = h->n;
+  const uint32_t un = (uint32_t)n;
+  const int key_bits = h->opts.key_bits;
+  const int passes = sort_passes(key_bits);
+  const int64_t n_int = n > 0 ? n - 1 : 0;
+
+  // persistent block: meta + records (root, reserved, 2 per internal node)
+  const size_t rec_floats = (size_t)(2 + 2 * n_int) * 8;
+  h->persist_bytes = align_up(sizeof(DevMeta)) + align_up(rec_floats * sizeof(float));
+  h->persist = dev_alloc(h->opts, h->persist_bytes, s);
+  if (!h->persist) return ARBORX_ENOMEM;
+  {
+    Carver c(h->persist);
+    h->meta = c.take<DevMeta>(1);
+    h->rec = c.take<float4>(rec_floats / 4);
+  }
+  launch_init_meta(h->meta, s);
+  if (n == 0) {
+    // empty tree: the root record must still be readable; mark it empty by n == 0
+    cudaMemsetAsync(h->rec, 0, 2 * sizeof(float4), s);
+    return launch_status();
+  }
+  launch_bounds(d_prims, n, h->kind, h->meta, s);
+  int st = launch_status();
+  if (st) return st;
+  if (h->opts.validate) {
+    uint32_t nonfinite = 0;
+    if (cudaMemcpyAsync(&nonfinite, &h->meta->nonfinite, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return ARBORX_ECUDA;
+    if (nonfinite) return ARBORX_EINVAL;
+  }
+
+  // scratch: keys A/B, vals A/B, parent, then the zero-initialised region
+  const size_t ws_words = sort_ws_words<K>(n, key_bits);
+  const size_t zero_bytes = align_up((size_t)n_int * sizeof(uint32_t)) + align_up(ws_words * sizeof(uint32_t));
+  const size_t scratch_bytes = 2 * align_up((size_t)n * sizeof(K)) + 2 * align_up((size_t)n * sizeof(uint32_t)) +
+                               align_up((size_t)(2 * n - 1) * sizeof(int32_t)) + zero_bytes;
+  void *scratch = dev_alloc(h->opts, scratch_bytes, s);
+  if (!scratch) return ARBORX_ENOMEM;
+  Carver c(scratch);
+  K *kA = c.take<K>(n);
+  K *kB = c.take<K>(n);
+  uint32_t *vA = c.take<uint32_t>(n);
+  uint32_t *vB = c.take<uint32_t>(n);
+  int32_t *parent = c.take<int32_t>(2 * n - 1);
+  char *zero_base = c.base + c.off;
+  uint32_t *arrival = c.take<uint32_t>(n_int);
+  uint32_t *wsbase = c.take<uint32_t>(ws_words);
+  cudaMemsetAsync(zero_base, 0, zero_bytes, s);
+  cudaMemsetAsync(parent, 0xff, (size_t)(2 * n - 1) * sizeof(int32_t), s);  // unset links read as -1
+  const SortWs ws = sort_ws_carve<K>(wsbase, n, key_bits);
+
+  launch_morton<K>(d_prims, un, h->kind, h->meta, kA, ws.hist, passes, true, s);
+  K *skeys;
+  uint32_t *perm;
+  sort_pairs<K>(kA, kB, vA, vB, un, ws, &h->meta->err, s, &skeys, &perm);
+  launch_hierarchy<K>(skeys, un, parent, s);
+  launch_fit(d_prims, un, h->kind, perm, parent, arrival, h->rec, &h->meta->err, s);
+  st = launch_status();
+  if (st == ARBORX_OK && h->opts.keep_order) {
+    h->order_bytes = align_up((size_t)n * sizeof(uint64_t)) + align_up((size_t)n * sizeof(uint32_t));
+    h->order = dev_alloc(h->opts, h->order_bytes, s);
+    if (!h->order) {
+      st = ARBORX_ENOMEM;
+    } else {
+      // keep codes widened to uint64 so the export format does not depend on key_bits
+      Carver oc(h->order);
+      uint64_t *codes64 = oc.take<uint64_t>(n);
+      uint32_t *perm_keep = oc.take<uint32_t>(n);
+      if (sizeof(K) == 8) {
+        cudaMemcpyAsync(codes64, skeys, n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s);
+      } else {
+        // widen with a strided copy: low words = codes, high words = 0
+        cudaMemsetAsync(codes64, 0, n * sizeof(uint64_t), s);
+        cudaMemcpy2DAsync(codes64, sizeof(uint64_t), skeys, sizeof(uint32_t), sizeof(uint32_t), n,
+                          cudaMemcpyDeviceToDevice, s);
+      }
+      cudaMemcpyAsync(perm_keep, perm, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
+      st = launch_status();
+    }
+  }
+  dev_free(h->opts, scratch, scratch_bytes, s);
+  return st;
+}
+
+void release(arborx_bvh_s *h) {
+  if (!h) return;
+  dev_free(h->opts, h->qws, h->qws_bytes, h->stream);
+  dev_free(h->opts, h->order, h->order_bytes, h->stream);
+  dev_free(h->opts, h->persist, h->persist_bytes, h->stream);
+  h->qws = h->order = h->persist = nullptr;
+}
+
+// Query workspace: codes A/B, perm A/B, sort workspace, counts, scan tiles.
+struct QueryWs {
+  uint32_t *cA, *cB, *pA, *pB;
+  uint32_t *sortws;
+  size_t sort_words;
+  int32_t *counts;
+  int64_t *scan_tmp;
+  uint32_t *miss;  // miss list + counter (learned bound fallback)
+};
+
+size_t query_ws_bytes(int64_t m, size_t *sort_words) {
+  *sort_words = sort_ws_words<uint32_t>(m, 30);
+  return 4 * align_up((size_t)m * sizeof(uint32_t)) + align_up(*sort_words * sizeof(uint32_t)) +
+         align_up((size_t)m * sizeof(int32_t)) + align_up(scan_tmp_words((uint32_t)m) * sizeof(int64_t)) +
+         align_up(((size_t)m + 32) * sizeof(uint32_t));
+}
+
+int get_query_ws(arborx_bvh_s *h, int64_t m, cudaStream_t s, QueryWs *q) {
+  size_t sort_words;
+  const size_t need = query_ws_bytes(m, &sort_words);
+  if (need > h->qws_bytes) {
+    dev_free(h->opts, h->qws, h->qws_bytes, s);
+    h->qws = dev_alloc(h->opts, need, s);
+    h->qws_bytes = h->qws ? need : 0;
+    if (!h->qws) return ARBORX_ENOMEM;
+  }
+  Carver c(h->qws);
+  q->cA = c.take<uint32_t>(m);
+  q->cB = c.take<uint32_t>(m);
+  q->pA = c.take<uint32_t>(m);
+  q->pB = c.take<uint32_t>(m);
+  q->sortws = c.take<uint32_t>(sort_words);
+  q->sort_words = sort_words;
+  q->counts = c.take<int32_t>(m);
+  q->scan_tmp = c.take<int64_t>(scan_tmp_words((uint32_t)m));
+  q->miss = c.take<uint32_t>(m + 32);
+  return ARBORX_OK;
+}
+
+// Morton-sort the queries against the tree's scene box; returns the
+// permutation (sorted position -> query index), or NULL for input order.
+int order_queries(arborx_bvh_s *h, const float *d_q, int64_t m, cudaStream_t s, QueryWs &q, const uint32_t **perm) {
+  *perm = nullptr;
+  if (!h->opts.sort_queries || m < 2 || h->n == 0) return ARBORX_OK;
+  cudaMemsetAsync(q.sortws, 0, q.sort_words * sizeof(uint32_t), s);
+  const SortWs ws = sort_ws_carve<uint32_t>(q.sortws, m, 30);
+  launch_morton<uint32_t>(d_q, (uint32_t)m, ARBORX_POINTS, h->meta, q.cA, ws.hist, ws.passes, false, s);
+  uint32_t *sk, *pm;
+  sort_pairs<uint32_t>(q.cA, q.cB, q.pA, q.pB, (uint32_t)m, ws, &h->meta->err, s, &sk, &pm);
+  *perm = pm;
+  return launch_status();
+}
+
+bool finite_radius(float r) { return !std::isnan(r) && r >= 0.0f; }
+
+}  // namespace
+
+extern "C" {
+
+const char *arborx_version(void) { return "arborx-b300 0.1 (sm_103a)"; }
+
+const char *arborx_error_string(int status) {
+  switch (status) {
+    case ARBORX_OK: return "ok";
+    case ARBORX_EINVAL: return "invalid argument";
+    case ARBORX_ENOMEM: return "out of device memory";
+    case ARBORX_ECUDA: return "CUDA error";
+    case ARBORX_ETIMEOUT: return "bounded device wait timed out";
+    case ARBORX_EOVERFLOW: return "result capacity exceeded";
+    case ARBORX_ESTATE: return "call out of order";
+    default: return "unknown";
+  }
+}
+
+int arborx_default_opts(arborx_opts *o) {
+  if (!o) return ARBORX_EINVAL;
+  std::memset(o, 0, sizeof(*o));
+  o->key_bits = 30;
+  o->sort_queries = 1;
+  o->validate = 1;
+  o->keep_order = 0;
+  o->block_size = 0;
+  o->stack_smem = 0;
+  return ARBORX_OK;
+}
+
+int arborx_build(const float *d_prims, int64_t n, int32_t kind, const arborx_opts *opts, void *stream,
+                 arborx_handle *out) {
+  if (!out) return ARBORX_EINVAL;
+  *out = nullptr;
+  if (n < 0 || n >= ARBORX_MAX_PRIMS || (kind != ARBORX_POINTS && kind != ARBORX_BOXES)) return ARBORX_EINVAL;
+  if (n > 0 && !d_prims) return ARBORX_EINVAL;
+  arborx_opts o;
+  if (opts) o = *opts;
+  else arborx_default_opts(&o);
+  if (!opts_ok(o)) return ARBORX_EINVAL;
+  arborx_bvh_s *h = new (std::nothrow) arborx_bvh_s();
+  if (!h) return ARBORX_ENOMEM;
+  cudaGetDevice(&h->device);
+  h->n = n;
+  h->kind = kind;
+  h->opts = o;
+  h->stream = (cudaStream_t)stream;
+  const cudaStream_t s = (cudaStream_t)stream;
+  const int st = o.key_bits == 30 ? build_impl<uint32_t>(h, d_prims, s) : build_impl<uint64_t>(h, d_prims, s);
+  if (st != ARBORX_OK) {
+    release(h);
+    delete h;
+    return st;
+  }
+  *out = h;
+  return ARBORX_OK;
+}
+
+int arborx_destroy(arborx_handle h) {
+  if (!h) return ARBORX_OK;
+  // memory is released stream-ordered on the stream of the handle's last call
+  release(h);
+  delete h;
+  return launch_status();
+}
+
+int arborx_size(arborx_handle h, int64_t *n, int32_t *kind) {
+  if (!h) return ARBORX_EINVAL;
+  if (n) *n = h->n;
+  if (kind) *kind = h->kind;
+  return ARBORX_OK;
+}
+
+int arborx_check(arborx_handle h, void *stream) {
+  if (!h) return ARBORX_EINVAL;
+  const cudaStream_t s = (cudaStream_t)stream;
+  uint32_t bits = 0;
+  if (cudaMemcpyAsync(&bits, &h->meta->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return ARBORX_ECUDA;
+  // non-finite input is a property of the tree: keep reporting it
+  const uint32_t keep = bits & ERR_NONFINITE;
+  if (bits & ~keep) cudaMemcpyAsync(&h->meta->err, &keep, sizeof(uint32_t), cudaMemcpyHostToDevice, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return ARBORX_ECUDA;
+  return err_bits_to_status(bits);
+}
+
+int arborx_query_spatial_count(arborx_handle h, const float *d_queries, int64_t m, float radius, void *stream,
+                               int64_t *d_offsets) {
+  if (!h || m < 0 || m >= ARBORX_MAX_QUERIES || !d_offsets || (m > 0 && !d_queries) || !finite_radius(radius))
+    return ARBORX_EINVAL;
+  const cudaStream_t s = (cudaStream_t)stream;
+  h->stream = s;
+  h->count_valid = false;
+  QueryWs q;
+  int st = get_query_ws(h, m, s, &q);
+  if (st) return st;
+  const uint32_t *perm;
+  st = order_queries(h, d_queries, m, s, q, &perm);
+  if (st) return st;
+  const float r2 = radius * radius;  // one IEEE single rounding
+  launch_spatial_count(h->rec, (uint32_t)h->n, d_queries, perm, (uint32_t)m, r2, q.counts, &h->meta->err,
+                       trav_cfg(h->opts), s);
+  launch_scan(q.counts, (uint32_t)m, d_offsets, q.scan_tmp, s);
+  st = launch_status();
+  if (st) return st;
+  h->qperm = perm;
+  h->count_queries = d_queries;
+  h->count_m = m;
+  h->count_radius = radius;
+  h->count_valid = true;
+  return ARBORX_OK;
+}
+
+int arborx_query_spatial_fill(arborx_handle h, const float *d_queries, int64_t m, float radius, void *stream,
+                              const int64_t *d_offsets, int32_t *d_indices, int64_t capacity) {
+  if (!h || m < 0 || !d_offsets || (m > 0 && !d_queries) || !finite_radius(radius) || capacity < 0 ||
+      (capacity > 0 && !d_indices))
+    return ARBORX_EINVAL;
+  if (!h->count_valid || h->count_queries != d_queries || h->count_m != m || h->count_radius != radius)
+    return ARBORX_ESTATE;
+  const cudaStream_t s = (cudaStream_t)stream;
+  const float r2 = radius * radius;  // one IEEE single rounding
+  launch_spatial_fill(h->rec, (uint32_t)h->n, d_queries, h->qperm, (uint32_t)m, r2, d_offsets, d_indices, capacity,
+                      &h->meta->err, trav_cfg(h->opts), s);
+  return launch_status();
+}
+
+int arborx_query_spatial(arborx_handle h, const float *d_queries, int64_t m, float radius, void *stream,
+                         int64_t *d_offsets, int32_t **d_indices, int64_t *nnz) {
+  if (!d_indices || !nnz) return ARBORX_EINVAL;
+  *d_indices = nullptr;
+  *nnz = 0;
+  int st = arborx_query_spatial_count(h, d_queries, m, radius, stream, d_offsets);
+  if (st) return st;
+  const cudaStream_t s = (cudaStream_t)stream;
+  int64_t total = 0;
+  uint32_t bits = 0;
+  if (cudaMemcpyAsync(&total, d_offsets + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(&bits, &h->meta->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return ARBORX_ECUDA;
+  st = err_bits_to_status(bits);
+  if (st) return st;
+  int32_t *idx = (int32_t *)dev_alloc(h->opts, (size_t)total * sizeof(int32_t), s);
+  if (!idx) return ARBORX_ENOMEM;
+  st = arborx_query_spatial_fill(h, d_queries, m, radius, stream, d_offsets, idx, total);
+  if (st) {
+    dev_free(h->opts, idx, (size_t)total * sizeof(int32_t), s);
+    return st;
+  }
+  *d_indices = idx;
+  *nnz = total;
+  return ARBORX_OK;
+}
+
+int arborx_free(arborx_handle h, void *d_ptr, size_t bytes, void *stream) {
+  if (!h) return ARBORX_EINVAL;
+  dev_free(h->opts, d_ptr, bytes, (cudaStream_t)stream);
+  return launch_status();
+}
+
+int arborx_query_nearest(arborx_handle h, const float *d_queries, int64_t m, int32_t k, void *stream,
+                         int64_t *d_offsets, int32_t *d_indices, float *d_dist2) {
+  if (!h || m < 0 || m >= ARBORX_MAX_QUERIES || k < 1 || k > ARBORX_MAX_K || (m > 0 && !d_queries))
+    return ARBORX_EINVAL;
+  const int64_t kk = k < h->n ? k : h->n;
+  if (m > 0 && kk > 0 && !d_indices) return ARBORX_EINVAL;
+  const cudaStream_t s = (cudaStream_t)stream;
+  h->stream = s;
+  if (m == 0 || kk == 0) {
+    if (d_offsets) cudaMemsetAsync(d_offsets, 0, (size_t)(m + 1) * sizeof(int64_t), s);
+    return launch_status();
+  }
+  QueryWs q;
+  int st = get_query_ws(h, m, s, &q);
+  if (st) return st;
+  const uint32_t *perm;
+  st = order_queries(h, d_queries, m, s, q, &perm);
+  if (st) return st;
+  if (launch_nearest(h->rec, (uint32_t)h->n, d_queries, perm, (uint32_t)m, k, d_offsets, d_indices, d_dist2, nullptr,
+                     nullptr, nullptr, &h->meta->err, trav_cfg(h->opts), s))
+    return ARBORX_EINVAL;
+  return launch_status();
+}
+
+int arborx_export_tree(arborx_handle h, void *stream, float *d_records, float *d_scene, uint64_t *d_codes,
+                       uint32_t *d_perm) {
+  if (!h) return ARBORX_EINVAL;
+  const cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = h->n;
+  if ((d_codes || d_perm) && !h->order && n > 0) return ARBORX_ESTATE;
+  if (d_records && n > 0)
+    cudaMemcpyAsync(d_records, h->rec, (size_t)(2 + 2 * (n - 1)) * 8 * sizeof(float), cudaMemcpyDeviceToDevice, s);
+  if (d_scene) cudaMemcpyAsync(d_scene, h->meta->scene, 6 * sizeof(float), cudaMemcpyDeviceToDevice, s);
+  if (n > 0 && h->order) {
+    Carver oc(h->order);
+    uint64_t *codes64 = oc.take<uint64_t>(n);
+    uint32_t *perm = oc.take<uint32_t>(n);
+    if (d_codes) cudaMemcpyAsync(d_codes, codes64, n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s);
+    if (d_perm) cudaMemcpyAsync(d_perm, perm, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
+  }
+  return launch_status();
+}
+
+int arborx_sort_pairs(void *d_keys, uint32_t *d_perm, int64_t n, int32_t key_bits, void *stream) {
+  if (n < 0 || n >= ARBORX_MAX_PRIMS || key_bits < 1 || key_bits > 64 || (n > 0 && (!d_keys || !d_perm)))
+    return ARBORX_EINVAL;
+  if (n == 0) return ARBORX_OK;
+  const cudaStream_t s = (cudaStream_t)stream;
+  arborx_opts o;
+  arborx_default_opts(&o);
+  const bool wide = key_bits > 32;
+  const size_t kb = wide ? 8 : 4;
+  const size_t ws_words = wide ? sort_ws_words<uint64_t>(n, key_bits) : sort_ws_words<uint32_t>(n, key_bits);
+  const size_t bytes = align_up(n * kb) + align_up(n * 4) + align_up(ws_words * 4) + align_up(4);
+  void *tmp = dev_alloc(o, bytes, s);
+  if (!tmp) return ARBORX_ENOMEM;
+  Carver c(tmp);
+  void *kB = c.take<char>(n * kb);
+  uint32_t *vB = c.take<uint32_t>(n);
+  uint32_t *wsb = c.take<uint32_t>(ws_words);
+  uint32_t *err = c.take<uint32_t>(1);
+  cudaMemsetAsync(wsb, 0, align_up(ws_words * 4) + align_up(4), s);
+  bool inA;
+  if (wide) {
+    const SortWs ws = sort_ws_carve<uint64_t>(wsb, n, key_bits);
+    launch_histogram<uint64_t>((const uint64_t *)d_keys, (uint32_t)n, ws.passes, ws.hist, s);
+    inA = launch_onesweep<uint64_t>((uint64_t *)d_keys, (uint64_t *)kB, d_perm, vB, (uint32_t)n, ws, err, s);
+  } else {
+    const SortWs ws = sort_ws_carve<uint32_t>(wsb, n, key_bits);
+    launch_histogram<uint32_t>((const uint32_t *)d_keys, (uint32_t)n, ws.passes, ws.hist, s);
+    inA = launch_onesweep<uint32_t>((uint32_t *)d_keys, (uint32_t *)kB, d_perm, vB, (uint32_t)n, ws, err, s);
+  }
+  if (!inA) {
+    cudaMemcpyAsync(d_keys, kB, n * kb, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(d_perm, vB, n * 4, cudaMemcpyDeviceToDevice, s);
+  }
+  uint32_t bits = 0;
+  cudaMemcpyAsync(&bits, err, 4, cudaMemcpyDeviceToHost, s);
+  dev_free(o, tmp, bytes, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return ARBORX_ECUDA;
+  const int st = launch_status();
+  if (st) return st;
+  return err_bits_to_status(bits);
+}
+
+}  // extern "C"

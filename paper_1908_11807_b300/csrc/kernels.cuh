@@ -1,0 +1,43 @@
+// Launchers of the LBVH kernels (internal to the library).
+#pragma once
+
+#include "common.cuh"
+
+namespace abx {
+
+// ---- construction (build.cu)
+void launch_init_meta(DevMeta *meta, cudaStream_t s);
+void launch_bounds(const float *prims, int64_t n, int kind, DevMeta *meta, cudaStream_t s);
+template <typename K>
+void launch_morton(const float *prims, uint32_t n, int kind, DevMeta *meta, K *codes, uint32_t *hist, int passes,
+                   bool write_scene, cudaStream_t s);
+template <typename K>
+void launch_hierarchy(const K *codes, uint32_t n, int32_t *parent, cudaStream_t s);
+void launch_fit(const float *prims, uint32_t n, int kind, const uint32_t *perm, const int32_t *parent,
+                uint32_t *arrival, float4 *rec, uint32_t *err, cudaStream_t s);
+
+// ---- traversal (traverse.cu)
+struct TravCfg {
+  int block;       // threads per block
+  int stack_smem;  // stack entries per thread kept in shared memory
+};
+
+// counts[j] (j in original query order) = number of primitives within r2
+void launch_spatial_count(const float4 *rec, uint32_t n, const float *queries, const uint32_t *qperm, uint32_t m,
+                          float r2, int32_t *counts, uint32_t *err, const TravCfg &cfg, cudaStream_t s);
+// fill rows at offsets[j]
+void launch_spatial_fill(const float4 *rec, uint32_t n, const float *queries, const uint32_t *qperm, uint32_t m,
+                         float r2, const int64_t *offsets, int32_t *indices, int64_t capacity, uint32_t *err,
+                         const TravCfg &cfg, cudaStream_t s);
+// exclusive scan counts[m] -> offsets[m+1]; tmp holds scan_tmp_words(m) int64
+size_t scan_tmp_words(uint32_t m);
+void launch_scan(const int32_t *counts, uint32_t m, int64_t *offsets, int64_t *tmp, cudaStream_t s);
+
+// nearest: rows of kk = min(k, n) (index, d2) in (d2, index) order.
+// init_bound2 (nullable, by original query index): initial k-th bound; rows that
+// end with fewer than kk real hits are appended to miss_list (if non-null).
+int launch_nearest(const float4 *rec, uint32_t n, const float *queries, const uint32_t *qperm, uint32_t m, int k,
+                   int64_t *offsets, int32_t *out_idx, float *out_d2, const float *init_bound2,
+                   uint32_t *miss_list, uint32_t *miss_count, uint32_t *err, const TravCfg &cfg, cudaStream_t s);
+
+}  // namespace abx

@@ -1,0 +1,226 @@
+// Onesweep LSD radix sort of (key, index) pairs; see radix_sort.cuh.
+#include <algorithm>
+
+#include "prof.cuh"
+#include "radix_sort.cuh"
+
+namespace abx {
+
+namespace {
+
+constexpr uint32_t kFlagAgg = 1u << 30;   // tile's own digit count published
+constexpr uint32_t kFlagPre = 2u << 30;   // inclusive prefix over tiles 0..t published
+constexpr uint32_t kValMask = (1u << 30) - 1u;
+constexpr uint32_t kSpinCap = 1u << 21;   // look-back give-up bound (~1 s)
+
+// Exclusive scans over the 256 threads of a block, two values at once.
+__device__ __forceinline__ void block_excl_scan2(uint32_t a, uint32_t b, uint32_t &a_ex, uint32_t &b_ex,
+                                                 uint32_t (*s_scan)[kSortWarps]) {
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = a, y = b;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t xo = __shfl_up_sync(0xffffffffu, x, o);
+    uint32_t yo = __shfl_up_sync(0xffffffffu, y, o);
+    if (lane >= (uint32_t)o) {
+      x += xo;
+      y += yo;
+    }
+  }
+  if (lane == 31) {
+    s_scan[0][warp] = x;
+    s_scan[1][warp] = y;
+  }
+  __syncthreads();
+  uint32_t wa = 0, wb = 0;
+#pragma unroll
+  for (int w = 0; w < kSortWarps; ++w) {
+    if ((uint32_t)w < warp) {
+      wa += s_scan[0][w];
+      wb += s_scan[1][w];
+    }
+  }
+  a_ex = wa + x - a;
+  b_ex = wb + y - b;
+}
+
+template <typename K, bool FIRST>
+__global__ void __launch_bounds__(kSortThreads) k_onesweep(const K *__restrict__ kin, const uint32_t *__restrict__ vin,
+                                                          K *__restrict__ kout, uint32_t *__restrict__ vout,
+                                                          uint32_t n, int shift, const uint32_t *__restrict__ hist,
+                                                          uint32_t *__restrict__ status,
+                                                          uint32_t *__restrict__ tile_ctr, uint32_t *__restrict__ err) {
+  constexpr int ITEMS = SortTile<K>::items;
+  constexpr int TILE = SortTile<K>::tile;
+  __shared__ uint32_t s_whist[kSortWarps][kRadix];  // per-warp digit counts, then per-warp offsets
+  __shared__ uint32_t s_dstart[kRadix];             // tile-local start of each digit run
+  __shared__ uint32_t s_gofs[kRadix];               // global destination of run start minus s_dstart
+  __shared__ uint32_t s_scan[2][kSortWarps];
+  __shared__ uint32_t s_tile;
+  __shared__ K s_k[TILE];
+  __shared__ uint32_t s_v[TILE];
+
+  const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);  // dynamic tile order: predecessors already run
+  for (int i = tid; i < kSortWarps * kRadix; i += kSortThreads) (&s_whist[0][0])[i] = 0;
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  const uint32_t tbase = tile * (uint32_t)TILE;
+  const uint32_t wbase = tbase + warp * (uint32_t)(ITEMS * 32);
+
+  K k[ITEMS];
+  uint32_t v[ITEMS];
+  uint32_t rk[ITEMS];
+#pragma unroll
+  for (int i = 0; i < ITEMS; ++i) {
+    const uint32_t pos = wbase + i * 32 + lane;
+    if (pos < n) {
+      k[i] = kin[pos];
+      v[i] = FIRST ? pos : vin[pos];
+    } else {
+      k[i] = 0;
+      v[i] = 0;
+    }
+  }
+
+  // warp-level ranking in input order (item-major, lane-minor)
+  const uint32_t lt = lanemask_lt(), gt = lanemask_gt();
+#pragma unroll
+  for (int i = 0; i < ITEMS; ++i) {
+    const uint32_t pos = wbase + i * 32 + lane;
+    const uint32_t d = pos < n ? (uint32_t)(k[i] >> shift) & (kRadix - 1) : (uint32_t)kRadix;
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    const uint32_t prev = d < (uint32_t)kRadix ? s_whist[warp][d] : 0u;
+    rk[i] = prev + __popc(peers & lt);
+    __syncwarp();
+    if (d < (uint32_t)kRadix && (peers & gt) == 0) s_whist[warp][d] = prev + __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+
+  // one thread per digit: warp offsets, tile count, publish, look back
+  const uint32_t d = tid;
+  uint32_t cnt = 0;
+#pragma unroll
+  for (int w = 0; w < kSortWarps; ++w) {
+    const uint32_t c = s_whist[w][d];
+    s_whist[w][d] = cnt;
+    cnt += c;
+  }
+  uint32_t *my_status = status + (size_t)tile * kRadix + d;
+  st_relaxed_gpu(my_status, (tile == 0 ? kFlagPre : kFlagAgg) | cnt);
+
+  uint32_t cnt_ex, h_ex;
+  block_excl_scan2(cnt, hist[d], cnt_ex, h_ex, s_scan);
+  s_dstart[d] = cnt_ex;
+
+  uint32_t excl = 0;
+  if (tile > 0) {
+    int j = (int)tile - 1;
+    while (j >= 0) {
+      const uint32_t *ps = status + (size_t)j * kRadix + d;
+      uint32_t st;
+      uint32_t spins = 0;
+      while (true) {
+        st = ld_relaxed_gpu(ps);
+        if (st & (kFlagAgg | kFlagPre)) break;
+        if (++spins >= kSpinCap) {  // give up: flag the error, unblock successors
+          set_err(err, ERR_TIMEOUT);
+          st = kFlagPre;
+          break;
+        }
+        if (spins > 256) __nanosleep(64);
+      }
+      excl += st & kValMask;
+      if (st & kFlagPre) break;
+      --j;
+    }
+    st_relaxed_gpu(my_status, kFlagPre | ((excl + cnt) & kValMask));
+  }
+  s_gofs[d] = h_ex + excl - cnt_ex;
+  __syncthreads();
+
+  // stage in digit order
+#pragma unroll
+  for (int i = 0; i < ITEMS; ++i) {
+    const uint32_t pos = wbase + i * 32 + lane;
+    if (pos < n) {
+      const uint32_t dd = (uint32_t)(k[i] >> shift) & (kRadix - 1);
+      const uint32_t p = s_dstart[dd] + s_whist[warp][dd] + rk[i];
+      s_k[p] = k[i];
+      s_v[p] = v[i];
+    }
+  }
+  __syncthreads();
+
+  // write runs
+  const uint32_t tn = min((uint32_t)TILE, n - tbase);
+  for (uint32_t j = tid; j < tn; j += kSortThreads) {
+    const K key = s_k[j];
+    const uint32_t dd = (uint32_t)(key >> shift) & (kRadix - 1);
+    const uint32_t dst = s_gofs[dd] + j;
+    kout[dst] = key;
+    vout[dst] = s_v[j];
+  }
+}
+
+template <typename K>
+__global__ void __launch_bounds__(256) k_histogram(const K *__restrict__ keys, uint32_t n, int passes,
+                                                  uint32_t *__restrict__ hist) {
+  __shared__ uint32_t s_h[8][kRadix];
+  for (int i = threadIdx.x; i < 8 * kRadix; i += blockDim.x) (&s_h[0][0])[i] = 0;
+  __syncthreads();
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const K key = keys[i];
+    for (int p = 0; p < passes; ++p) atomicAdd(&s_h[p][(uint32_t)(key >> (p * kRadixBits)) & (kRadix - 1)], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < passes * kRadix; i += blockDim.x) {
+    const uint32_t c = (&s_h[0][0])[i];
+    if (c) atomicAdd(&hist[i], c);
+  }
+}
+
+}  // namespace
+
+template <typename K>
+void launch_histogram(const K *keys, uint32_t n, int passes, uint32_t *hist, cudaStream_t s) {
+  if (n == 0) return;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  uint32_t blocks = std::min<uint32_t>(ceil_div<uint32_t>(n, 256u * 8u), (uint32_t)sms * 4u);
+  prof::Scope ps(s, "histogram");
+  k_histogram<K><<<blocks, 256, 0, s>>>(keys, n, passes, hist);
+}
+
+template <typename K>
+bool launch_onesweep(K *kA, K *kB, uint32_t *vA, uint32_t *vB, uint32_t n, const SortWs &ws, uint32_t *err,
+                     cudaStream_t s) {
+  if (n == 0) return true;
+  K *kin = kA, *kout = kB;
+  uint32_t *vin = vA, *vout = vB;
+  const uint32_t tiles = ceil_div<uint32_t>(n, (uint32_t)SortTile<K>::tile);
+  for (int p = 0; p < ws.passes; ++p) {
+    const uint32_t *h = ws.hist + (size_t)p * kRadix;
+    uint32_t *st = ws.status + (size_t)p * ws.tiles * kRadix;
+    uint32_t *ctr = ws.tile_ctr + p;
+    prof::Scope ps(s, "onesweep_pass");
+    if (p == 0)
+      k_onesweep<K, true><<<tiles, kSortThreads, 0, s>>>(kin, nullptr, kout, vout, n, 0, h, st, ctr, err);
+    else
+      k_onesweep<K, false><<<tiles, kSortThreads, 0, s>>>(kin, vin, kout, vout, n, p * kRadixBits, h, st, ctr, err);
+    K *tk = kin; kin = kout; kout = tk;
+    uint32_t *tv = vin; vin = vout; vout = tv;
+  }
+  return kin == kA;
+}
+
+template void launch_histogram<uint32_t>(const uint32_t *, uint32_t, int, uint32_t *, cudaStream_t);
+template void launch_histogram<uint64_t>(const uint64_t *, uint32_t, int, uint32_t *, cudaStream_t);
+template bool launch_onesweep<uint32_t>(uint32_t *, uint32_t *, uint32_t *, uint32_t *, uint32_t, const SortWs &,
+                                        uint32_t *, cudaStream_t);
+template bool launch_onesweep<uint64_t>(uint64_t *, uint64_t *, uint32_t *, uint32_t *, uint32_t, const SortWs &,
+                                        uint32_t *, cudaStream_t);
+
+}  // namespace abx

@@ -1,0 +1,498 @@
+// Tree traversal kernels (ArborX Sec. 2.2): spatial count / fill (2P), the
+// offsets scan, and nearest queries with a bounded candidate list.
+//
+// One thread per query, queries taken in Morton order through qperm so that a
+// warp's threads walk similar paths (Sec. 2.2, "Query ordering").  Each
+// internal node stores both child boxes side by side (64 bytes), so a step
+// loads one node and tests both children; leaf children are tested and
+// reported directly from the parent, leaves are never loaded separately.  The
+// per-thread stack keeps its first `stack_smem` entries in shared memory
+// (laid out [level][thread], conflict-free) and spills deeper entries to
+// local memory; its total capacity exceeds the largest possible LBVH depth
+// (each level consumes one bit of the <= 64 + 32 bit augmented key).
+#include <climits>
+
+#include <algorithm>
+
+#include "kernels.cuh"
+#include "prof.cuh"
+
+namespace abx {
+
+namespace {
+
+constexpr int kSpill = 96;     // local-memory stack entries beyond the shared part
+constexpr int kMaxBlock = 256;  // traversal block size limit (register budget)
+
+__device__ __forceinline__ bool finite3(float x, float y, float z) {
+  return is_finite_bits(x) && is_finite_bits(y) && is_finite_bits(z);
+}
+
+// (d, i) strictly before (e, j) in (distance, index) order
+__device__ __forceinline__ bool pless(float d, int32_t i, float e, int32_t j) {
+  return d < e || (d == e && i < j);
+}
+
+template <bool FILL>
+__global__ void __launch_bounds__(kMaxBlock) k_spatial(const float4 *__restrict__ rec, uint32_t n,
+                                                 const float *__restrict__ queries, const uint32_t *__restrict__ qperm,
+                                                 uint32_t m, float r2, int32_t *__restrict__ counts,
+                                                 const int64_t *__restrict__ offsets, int32_t *__restrict__ indices,
+                                                 int64_t capacity, uint32_t *__restrict__ err, int stack_smem) {
+  extern __shared__ int32_t s_stack[];
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= m) return;
+  const uint32_t qi = qperm ? __ldg(qperm + t) : t;
+  const float qx = __ldg(queries + 3 * (uint64_t)qi);
+  const float qy = __ldg(queries + 3 * (uint64_t)qi + 1);
+  const float qz = __ldg(queries + 3 * (uint64_t)qi + 2);
+  int64_t base = 0;
+  if (FILL) base = __ldg(offsets + qi);
+  uint32_t cnt = 0;
+
+#define ABX_EMIT(v)                                   \
+  do {                                                \
+    if (FILL) {                                       \
+      const int64_t pos_ = base + cnt;                \
+      if (pos_ < capacity) indices[pos_] = (v);       \
+      else set_err(err, ERR_CSR);                     \
+    }                                                 \
+    ++cnt;                                            \
+  } while (0)
+
+  if (n > 0 && finite3(qx, qy, qz)) {
+    const float4 r0 = __ldg(rec), r1 = __ldg(rec + 1);
+    if (dist2_box(qx, qy, qz, r0, r1) <= r2) {
+      const int e0 = __float_as_int(r0.w);
+      if (e0 < 0) {
+        ABX_EMIT(~e0);
+      } else {
+        int32_t *my = s_stack + threadIdx.x;
+        const int stride = blockDim.x;
+        int32_t spill[kSpill];
+        int sp = 0;
+        int node = e0;
+        while (true) {
+          if ((uint32_t)node >= n - 1) {  // corrupt tree: never read outside the records
+            set_err(err, ERR_STACK);
+            break;
+          }
+          const float4 *rp = rec + 4 + 4 * (uint64_t)node;
+          const float4 a0 = __ldg(rp), a1 = __ldg(rp + 1), b0 = __ldg(rp + 2), b1 = __ldg(rp + 3);
+          const bool hl = dist2_box(qx, qy, qz, a0, a1) <= r2;
+          const bool hr = dist2_box(qx, qy, qz, b0, b1) <= r2;
+          const int el = __float_as_int(a0.w), er = __float_as_int(b0.w);
+          if (hl && el < 0) ABX_EMIT(~el);
+          if (hr && er < 0) ABX_EMIT(~er);
+          const bool gl = hl && el >= 0, gr = hr && er >= 0;
+          if (gl) {
+            if (gr) {
+              if (sp < stack_smem) {
+                my[sp * stride] = er;
+                ++sp;
+              } else if (sp - stack_smem < kSpill) {
+                spill[sp - stack_smem] = er;
+                ++sp;
+              } else {
+                set_err(err, ERR_STACK);  // cannot happen: capacity exceeds the deepest LBVH
+              }
+            }
+            node = el;
+          } else if (gr) {
+            node = er;
+          } else {
+            if (sp == 0) break;
+            --sp;
+            node = sp < stack_smem ? my[sp * stride] : spill[sp - stack_smem];
+          }
+        }
+      }
+    }
+  }
+#undef ABX_EMIT
+  if (!FILL) counts[qi] = (int32_t)cnt;
+}
+
+// ---------------------------------------------------------------- nearest
+
+// Ascending list of the KC best (d2, index) pairs in registers; the k-th entry
+// (k <= KC) is the pruning bound.
+template <int KC>
+struct RegList {
+  // slots [0, KC - k) hold (-inf, INT_MIN) fillers that nothing displaces, so
+  // the k-th best is always slot KC - 1 (no run-time register indexing)
+  float d[KC];
+  int32_t i[KC];
+  int off;
+  __device__ __forceinline__ void init(float b, int k) {
+    off = KC - k;
+#pragma unroll
+    for (int j = 0; j < KC; ++j) {
+      const bool filler = j < off;
+      d[j] = filler ? __int_as_float(0xff800000) : b;
+      i[j] = filler ? INT_MIN : INT_MAX;
+    }
+  }
+  __device__ __forceinline__ float bound() const { return d[KC - 1]; }
+  __device__ __forceinline__ int32_t bound_idx() const { return i[KC - 1]; }
+  __device__ __forceinline__ bool accepts(float dc, int32_t ic) const { return pless(dc, ic, d[KC - 1], i[KC - 1]); }
+  __device__ __forceinline__ void insert(float dc, int32_t ic, int) {
+#pragma unroll
+    for (int j = KC - 1; j > 0; --j) {
+      const bool lt = pless(dc, ic, d[j], i[j]);
+      const bool ltp = pless(dc, ic, d[j - 1], i[j - 1]);
+      if (lt) {
+        d[j] = ltp ? d[j - 1] : dc;
+        i[j] = ltp ? i[j - 1] : ic;
+      }
+    }
+    if (pless(dc, ic, d[0], i[0])) {
+      d[0] = dc;
+      i[0] = ic;
+    }
+  }
+  __device__ __forceinline__ void write(int64_t row, int kk, int32_t *out_idx, float *out_d2) const {
+#pragma unroll
+    for (int j = 0; j < KC; ++j) {
+      const int o = j - off;
+      if (o >= 0 && o < kk) {
+        const bool real = i[j] != INT_MAX;
+        out_idx[row + o] = real ? i[j] : -1;
+        if (out_d2) out_d2[row + o] = real ? d[j] : __int_as_float(0x7f800000);
+      }
+    }
+  }
+};
+
+// Max-heap of k (d2, index) pairs in shared memory ([slot][thread] layout);
+// the root is the k-th best and the pruning bound.
+struct SmemHeap {
+  float *hd;
+  int32_t *hi;
+  int s;  // stride between a thread's consecutive slots
+  int k;
+  float kd;
+  int32_t ki;
+  __device__ __forceinline__ float bound() const { return kd; }
+  __device__ __forceinline__ int32_t bound_idx() const { return ki; }
+  __device__ __forceinline__ void init(float b, int) {
+    for (int j = 0; j < k; ++j) {
+      hd[j * s] = b;
+      hi[j * s] = INT_MAX;
+    }
+    kd = b;
+    ki = INT_MAX;
+  }
+  __device__ __forceinline__ bool accepts(float dc, int32_t ic) const { return pless(dc, ic, kd, ki); }
+  __device__ __forceinline__ void sift(float dc, int32_t ic, int size) {
+    int pos = 0;
+    while (true) {
+      const int l = 2 * pos + 1;
+      if (l >= size) break;
+      int c = l;
+      float dm = hd[l * s];
+      int32_t im = hi[l * s];
+      if (l + 1 < size) {
+        const float dr = hd[(l + 1) * s];
+        const int32_t ir = hi[(l + 1) * s];
+        if (pless(dm, im, dr, ir)) {
+          c = l + 1;
+          dm = dr;
+          im = ir;
+        }
+      }
+      if (!pless(dc, ic, dm, im)) break;
+      hd[pos * s] = dm;
+      hi[pos * s] = im;
+      pos = c;
+    }
+    hd[pos * s] = dc;
+    hi[pos * s] = ic;
+  }
+  __device__ __forceinline__ void insert(float dc, int32_t ic, int) {
+    sift(dc, ic, k);
+    kd = hd[0];
+    ki = hi[0];
+  }
+  __device__ __forceinline__ void write(int64_t row, int kk, int32_t *out_idx, float *out_d2) {
+    for (int j = k - 1; j >= 0; --j) {
+      const float d = hd[0];
+      const int32_t i = hi[0];
+      if (j < kk) {
+        const bool real = i != INT_MAX;
+        out_idx[row + j] = real ? i : -1;
+        if (out_d2) out_d2[row + j] = real ? d : __int_as_float(0x7f800000);
+      }
+      if (j > 0) sift(hd[j * s], hi[j * s], j);
+    }
+  }
+};
+
+template <class List>
+__device__ __forceinline__ void knn_traverse(const float4 *__restrict__ rec, uint32_t n, float qx, float qy, float qz, List &L,
+                                             int k, int32_t *s_node, float *s_dist, int stride, int stack_smem,
+                                             uint32_t *err) {
+  const float4 r0 = __ldg(rec), r1 = __ldg(rec + 1);
+  const int e0 = __float_as_int(r0.w);
+  const float d0 = dist2_box(qx, qy, qz, r0, r1);
+  if (e0 < 0) {
+    if (L.accepts(d0, ~e0)) L.insert(d0, ~e0, k);
+    return;
+  }
+  if (d0 > L.bound()) return;
+  int32_t spn[kSpill];
+  float spd[kSpill];
+  int sp = 0;
+  int node = e0;
+  while (true) {
+    if ((uint32_t)node >= n - 1) {  // corrupt tree: never read outside the records
+      set_err(err, ERR_STACK);
+      break;
+    }
+    const float4 *rp = rec + 4 + 4 * (uint64_t)node;
+    const float4 a0 = __ldg(rp), a1 = __ldg(rp + 1), b0 = __ldg(rp + 2), b1 = __ldg(rp + 3);
+    const float dl = dist2_box(qx, qy, qz, a0, a1);
+    const float dr = dist2_box(qx, qy, qz, b0, b1);
+    const int el = __float_as_int(a0.w), er = __float_as_int(b0.w);
+    if (el < 0 && L.accepts(dl, ~el)) L.insert(dl, ~el, k);
+    if (er < 0 && L.accepts(dr, ~er)) L.insert(dr, ~er, k);
+    const bool gl = el >= 0 && dl <= L.bound();  // prune only when strictly farther than the k-th
+    const bool gr = er >= 0 && dr <= L.bound();
+    if (gl && gr) {
+      // visit the closer child next, keep the farther one on the stack
+      const bool lfirst = dl <= dr;
+      const int far = lfirst ? er : el;
+      const float fd = lfirst ? dr : dl;
+      if (sp < stack_smem) {
+        s_node[sp * stride] = far;
+        s_dist[sp * stride] = fd;
+        ++sp;
+      } else if (sp - stack_smem < kSpill) {
+        spn[sp - stack_smem] = far;
+        spd[sp - stack_smem] = fd;
+        ++sp;
+      } else {
+        set_err(err, ERR_STACK);  // cannot happen: capacity exceeds the deepest LBVH
+      }
+      node = lfirst ? el : er;
+    } else if (gl) {
+      node = el;
+    } else if (gr) {
+      node = er;
+    } else {
+      node = -1;
+      while (sp > 0) {
+        --sp;
+        const bool sm = sp < stack_smem;
+        const int nd = sm ? s_node[sp * stride] : spn[sp - stack_smem];
+        const float dd = sm ? s_dist[sp * stride] : spd[sp - stack_smem];
+        if (dd <= L.bound()) {
+          node = nd;
+          break;
+        }
+      }
+      if (node < 0) break;
+    }
+  }
+}
+
+// Threads t <= m also write offsets[t] = t * kk (CSR view of the rows).
+template <int KC>
+__global__ void __launch_bounds__(kMaxBlock) k_nearest(const float4 *__restrict__ rec, uint32_t n,
+                                                 const float *__restrict__ queries, const uint32_t *__restrict__ qperm,
+                                                 uint32_t m, int k, int kk, int64_t *__restrict__ offsets,
+                                                 int32_t *__restrict__ out_idx, float *__restrict__ out_d2,
+                                                 const float *__restrict__ init_bound2, uint32_t *__restrict__ miss_list,
+                                                 uint32_t *__restrict__ miss_count, uint32_t *__restrict__ err,
+                                                 int stack_smem) {
+  extern __shared__ unsigned char s_raw[];
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (offsets && t <= m) offsets[t] = (int64_t)t * kk;
+  if (t >= m) return;
+  const int B = blockDim.x;
+  int32_t *s_node = reinterpret_cast<int32_t *>(s_raw) + threadIdx.x;
+  float *s_dist = reinterpret_cast<float *>(s_raw) + (size_t)stack_smem * B + threadIdx.x;
+  const uint32_t qi = qperm ? __ldg(qperm + t) : t;
+  const float qx = __ldg(queries + 3 * (uint64_t)qi);
+  const float qy = __ldg(queries + 3 * (uint64_t)qi + 1);
+  const float qz = __ldg(queries + 3 * (uint64_t)qi + 2);
+  const float b0 = init_bound2 ? __ldg(init_bound2 + qi) : __int_as_float(0x7f800000);
+  const bool ok = finite3(qx, qy, qz);
+  const int64_t row = (int64_t)qi * kk;
+  if constexpr (KC > 0) {
+    RegList<KC> L;
+    L.init(b0, k);
+    if (ok && n > 0) knn_traverse(rec, n, qx, qy, qz, L, k, s_node, s_dist, B, stack_smem, err);
+    if (miss_list && ok && L.bound_idx() == INT_MAX) miss_list[atomicAdd(miss_count, 1u)] = qi;
+    L.write(row, kk, out_idx, out_d2);
+  } else {
+    SmemHeap H;
+    H.hd = reinterpret_cast<float *>(s_raw) + (size_t)2 * stack_smem * B + threadIdx.x;
+    H.hi = reinterpret_cast<int32_t *>(s_raw) + (size_t)(2 * stack_smem + k) * B + threadIdx.x;
+    H.s = B;
+    H.k = k;
+    H.init(b0, k);
+    if (ok && n > 0) knn_traverse(rec, n, qx, qy, qz, H, k, s_node, s_dist, B, stack_smem, err);
+    if (miss_list && ok && H.bound_idx() == INT_MAX) miss_list[atomicAdd(miss_count, 1u)] = qi;
+    H.write(row, kk, out_idx, out_d2);
+  }
+}
+
+// ------------------------------------------------------------------- scan
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ int64_t block_excl_scan_i64(int64_t v, int64_t *s_w, int64_t &total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int64_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_w[warp] = x;
+  __syncthreads();
+  int64_t before = 0, tot = 0;
+  for (int w = 0; w < nw; ++w) {
+    const int64_t sw = s_w[w];
+    if (w < warp) before += sw;
+    tot += sw;
+  }
+  __syncthreads();
+  total = tot;
+  return before + x - v;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const int32_t *__restrict__ c, uint32_t m,
+                                                             int64_t *__restrict__ tsum) {
+  __shared__ int64_t s_w[32];
+  const uint64_t base = (uint64_t)blockIdx.x * kScanTile;
+  int64_t s = 0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    const uint64_t p = base + (uint64_t)i * kScanThreads + threadIdx.x;
+    if (p < m) s += c[p];
+  }
+  int64_t tot;
+  block_excl_scan_i64(s, s_w, tot);
+  if (threadIdx.x == 0) tsum[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_tiles(int64_t *__restrict__ tsum, uint32_t tiles) {
+  __shared__ int64_t s_w[32];
+  int64_t carry = 0;
+  for (uint32_t b = 0; b < tiles; b += blockDim.x) {
+    const uint32_t i = b + threadIdx.x;
+    const int64_t v = i < tiles ? tsum[i] : 0;
+    int64_t tot;
+    const int64_t ex = block_excl_scan_i64(v, s_w, tot);
+    if (i < tiles) tsum[i] = carry + ex;
+    carry += tot;
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(const int32_t *__restrict__ c, uint32_t m,
+                                                           const int64_t *__restrict__ toff,
+                                                           int64_t *__restrict__ off) {
+  __shared__ int64_t s_w[32];
+  const uint64_t base = (uint64_t)blockIdx.x * kScanTile + (uint64_t)threadIdx.x * kScanItems;
+  int32_t v[kScanItems];
+  int64_t s = 0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    v[i] = base + i < m ? c[base + i] : 0;
+    s += v[i];
+  }
+  int64_t tot;
+  int64_t run = block_excl_scan_i64(s, s_w, tot) + toff[blockIdx.x];
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    if (base + i < m) off[base + i] = run;
+    run += v[i];
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == blockDim.x - 1) off[m] = run;
+}
+
+}  // namespace
+
+void launch_spatial_count(const float4 *rec, uint32_t n, const float *queries, const uint32_t *qperm, uint32_t m,
+                          float r2, int32_t *counts, uint32_t *err, const TravCfg &cfg, cudaStream_t s) {
+  if (m == 0) return;
+  const size_t smem = (size_t)cfg.stack_smem * cfg.block * sizeof(int32_t);
+  prof::Scope ps(s, "spatial_count");
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k_spatial<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_spatial<false><<<ceil_div<uint32_t>(m, cfg.block), cfg.block, smem, s>>>(
+      rec, n, queries, qperm, m, r2, counts, nullptr, nullptr, 0, err, cfg.stack_smem);
+}
+
+void launch_spatial_fill(const float4 *rec, uint32_t n, const float *queries, const uint32_t *qperm, uint32_t m,
+                         float r2, const int64_t *offsets, int32_t *indices, int64_t capacity, uint32_t *err,
+                         const TravCfg &cfg, cudaStream_t s) {
+  if (m == 0) return;
+  const size_t smem = (size_t)cfg.stack_smem * cfg.block * sizeof(int32_t);
+  prof::Scope ps(s, "spatial_fill");
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k_spatial<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_spatial<true><<<ceil_div<uint32_t>(m, cfg.block), cfg.block, smem, s>>>(
+      rec, n, queries, qperm, m, r2, nullptr, offsets, indices, capacity, err, cfg.stack_smem);
+}
+
+size_t scan_tmp_words(uint32_t m) { return (size_t)ceil_div<uint32_t>(m > 0 ? m : 1, (uint32_t)kScanTile) + 1; }
+
+void launch_scan(const int32_t *counts, uint32_t m, int64_t *offsets, int64_t *tmp, cudaStream_t s) {
+  if (m == 0) {
+    cudaMemsetAsync(offsets, 0, sizeof(int64_t), s);
+    return;
+  }
+  const uint32_t tiles = ceil_div<uint32_t>(m, (uint32_t)kScanTile);
+  prof::Scope ps(s, "scan");
+  k_scan_reduce<<<tiles, kScanThreads, 0, s>>>(counts, m, tmp);
+  k_scan_tiles<<<1, 1024, 0, s>>>(tmp, tiles);
+  k_scan_down<<<tiles, kScanThreads, 0, s>>>(counts, m, tmp, offsets);
+}
+
+template <int KC>
+static void nearest_kc(dim3 grid, int block, size_t smem, cudaStream_t s, const float4 *rec, uint32_t n,
+                       const float *queries, const uint32_t *qperm, uint32_t m, int k, int kk, int64_t *offsets,
+                       int32_t *out_idx, float *out_d2, const float *init_bound2, uint32_t *miss_list,
+                       uint32_t *miss_count, uint32_t *err, int stack_smem) {
+  prof::Scope ps(s, "nearest");
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k_nearest<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_nearest<KC><<<grid, block, smem, s>>>(rec, n, queries, qperm, m, k, kk, offsets, out_idx, out_d2, init_bound2,
+                                          miss_list, miss_count, err, stack_smem);
+}
+
+int launch_nearest(const float4 *rec, uint32_t n, const float *queries, const uint32_t *qperm, uint32_t m, int k,
+                   int64_t *offsets, int32_t *out_idx, float *out_d2, const float *init_bound2, uint32_t *miss_list,
+                   uint32_t *miss_count, uint32_t *err, const TravCfg &cfg, cudaStream_t s) {
+  const int kk = (int)std::min<int64_t>(k, n);
+  const uint32_t threads = m + 1;
+  int block = cfg.block;
+  size_t smem = (size_t)2 * cfg.stack_smem * block * sizeof(int32_t);
+  if (k > 32) {
+    // heap of k pairs per thread in shared memory: shrink the block to fit
+    while (block > 32 && smem + (size_t)2 * k * block * sizeof(int32_t) > 200 * 1024) {
+      block >>= 1;
+      smem = (size_t)2 * cfg.stack_smem * block * sizeof(int32_t);
+    }
+    smem += (size_t)2 * k * block * sizeof(int32_t);
+    if (smem > 227 * 1024) return -1;
+  }
+  const dim3 grid(ceil_div<uint32_t>(threads, (uint32_t)block));
+#define ABX_NEAREST(KC)                                                                                           \
+  nearest_kc<KC>(grid, block, smem, s, rec, n, queries, qperm, m, k, kk, offsets, out_idx, out_d2, init_bound2, \
+                 miss_list, miss_count, err, cfg.stack_smem)
+  if (k <= 1) ABX_NEAREST(1);
+  else if (k <= 2) ABX_NEAREST(2);
+  else if (k <= 4) ABX_NEAREST(4);
+  else if (k <= 8) ABX_NEAREST(8);
+  else if (k <= 10) ABX_NEAREST(10);
+  else if (k <= 16) ABX_NEAREST(16);
+  else if (k <= 32) ABX_NEAREST(32);
+  else ABX_NEAREST(0);
+#undef ABX_NEAREST
+  return 0;
+}
+
+}  // namespace abx

@@ -1,0 +1,136 @@
+"""GPU parity of the LBVH construction (Sec. 2.1): scene box, Morton codes and
+the stable sort bit-exact against the oracle, tree invariants of the hierarchy
+and the bottom-up fit, error behaviour."""
+import numpy as np
+import pytest
+
+import datagen
+import oracle
+from oracle import tree_check
+from tests.gpu_helpers import dev, host
+
+pytestmark = pytest.mark.gpu
+
+
+def _ab():
+    import paper_1908_11807_b300 as ab
+    return ab
+
+
+CLOUDS = {
+    "cube_1e4": lambda: datagen.cube(10_000, datagen.SEED0 + 1),
+    "hollow_sphere_2e4": lambda: datagen.hollow_sphere(20_000, datagen.SEED0 + 2),
+    "gaussian_3e4": lambda: datagen.gaussian_mixture(30_000, datagen.SEED0 + 5),
+    "ragged_4097": lambda: datagen.cube(4097, 7),  # one full sort tile + 1
+    "ragged_12289": lambda: datagen.cube(12289, 8),
+    "duplicates": lambda: np.repeat(datagen.cube(700, 9), 13, axis=0),
+    "all_equal": lambda: np.full((5000, 3), 0.25, np.float32),
+    "flat_plane": lambda: np.concatenate([datagen.cube(6000, 10)[:, :2], np.full((6000, 1), 2.0, np.float32)], 1),
+    "collinear": lambda: np.stack([np.linspace(-1, 1, 3001, dtype=np.float32)] * 3, 1),
+    "lattice_32": lambda: datagen.lattice(32),
+    "tiny_2": lambda: datagen.cube(2, 11),
+    "tiny_3": lambda: datagen.cube(3, 12),
+    "boxes_2e4": lambda: datagen.boxes(20_000, datagen.SEED0 + 2),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CLOUDS))
+@pytest.mark.parametrize("key_bits", [30, 63])
+def test_build_bit_exact_and_invariants(name, key_bits):
+    ab = _ab()
+    p = CLOUDS[name]()
+    bvh = ab.BVH(dev(p), keep_order=1, key_bits=key_bits)
+    rec, scene, codes, perm = bvh.export_tree(order=True)
+    bvh.check()
+    rec, scene, codes, perm = host(rec), host(scene), host(codes).view(np.uint64), host(perm).astype(np.int64)
+    sb, bad = oracle.scene_box(p)
+    assert bad == 0
+    assert np.array_equal(scene, sb)
+    want_codes = oracle.morton(p, sb, key_bits)
+    # stable sort by code: ties keep index order (codes augmented with the index)
+    want_perm = np.lexsort((np.arange(len(p)), want_codes))
+    assert np.array_equal(perm, want_perm)
+    assert np.array_equal(codes, want_codes[want_perm])
+    tree_check.check_lbvh(rec, p, perm, codes, sb)
+
+
+@pytest.mark.parametrize("n", [1, 2, 5])
+def test_build_tiny_and_single_leaf(n):
+    ab = _ab()
+    p = datagen.cube(n, 40 + n)
+    bvh = ab.BVH(dev(p), keep_order=1)
+    rec, scene, codes, perm = bvh.export_tree(order=True)
+    tree_check.check_lbvh(host(rec), p, host(perm), host(codes).view(np.uint64), host(scene))
+
+
+def test_empty_tree():
+    ab = _ab()
+    import torch
+    bvh = ab.BVH(torch.zeros((0, 3), device="cuda"))
+    q = dev(datagen.cube(100, 1))
+    off, idx = bvh.query_spatial(q, 1.0)
+    assert host(off).tolist() == [0] * 101 and idx.numel() == 0
+    ii, dd = bvh.query_nearest(q, 5)
+    assert tuple(ii.shape) == (100, 0)
+
+
+def test_nonfinite_primitive_rejected():
+    ab = _ab()
+    p = datagen.cube(1000, 3)
+    p[500, 1] = np.nan
+    with pytest.raises(ab.ArborXError) as e:
+        ab.BVH(dev(p))
+    assert e.value.code == 1
+    p[500, 1] = np.inf
+    with pytest.raises(ab.ArborXError):
+        ab.BVH(dev(p))
+    # asynchronous build: reported by check()
+    bvh = ab.BVH(dev(p), validate=0)
+    with pytest.raises(ab.ArborXError) as e:
+        bvh.check()
+    assert e.value.code == 1
+
+
+def test_unaligned_input_pointer():
+    ab = _ab()
+    import torch
+    p = datagen.cube(3001, 4)
+    buf = torch.zeros(3 * 3001 + 1, dtype=torch.float32, device="cuda")
+    buf[1:] = dev(p.ravel())
+    view = buf[1:].view(3001, 3)  # 4-byte aligned, not 16
+    bvh = ab.BVH(view, keep_order=1)
+    rec, scene, codes, perm = bvh.export_tree(order=True)
+    sb, _ = oracle.scene_box(p)
+    assert np.array_equal(host(scene), sb)
+    tree_check.check_lbvh(host(rec), p, host(perm), host(codes).view(np.uint64), sb)
+
+
+@pytest.mark.parametrize("n", [1, 100, 4096, 4097, 100_003, 1_000_000])
+@pytest.mark.parametrize("key_bits", [8, 16, 30, 32])
+def test_sort_pairs_u32_matches_stable_argsort(n, key_bits):
+    ab = _ab()
+    g = np.random.default_rng(n + key_bits)
+    hi = 1 << key_bits
+    keys = g.integers(0, hi, size=n, dtype=np.uint64).astype(np.uint32)
+    keys[: n // 3] = keys[0]  # many ties
+    import torch
+    sk, perm = ab.arborx_sort_pairs(torch.from_numpy(keys.view(np.int32)).cuda(), key_bits)
+    want = np.argsort(keys, kind="stable")
+    assert np.array_equal(host(perm), want)
+    assert np.array_equal(host(sk).view(np.uint32), keys[want])
+
+
+@pytest.mark.parametrize("n", [3, 3072, 3073, 500_000])
+@pytest.mark.parametrize("key_bits", [40, 63, 64])
+def test_sort_pairs_u64_matches_stable_argsort(n, key_bits):
+    ab = _ab()
+    import torch
+    g = np.random.default_rng(n * 7 + key_bits)
+    keys = g.integers(0, 1 << 62, size=n, dtype=np.uint64) & np.uint64((1 << key_bits) - 1)
+    if key_bits == 64:
+        keys |= np.uint64(1 << 63) * (g.integers(0, 2, size=n).astype(np.uint64))
+    keys[::5] = keys[1]
+    sk, perm = ab.arborx_sort_pairs(torch.from_numpy(keys.view(np.int64)).cuda(), key_bits)
+    want = np.argsort(keys, kind="stable")
+    assert np.array_equal(host(perm), want)
+    assert np.array_equal(host(sk).view(np.uint64), keys[want])

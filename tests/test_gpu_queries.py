@@ -1,0 +1,207 @@
+"""GPU parity of the traversals (Sec. 2.2) against the oracle's brute force:
+spatial count-and-fill CSR rows as exact index sets, nearest rows exact in
+(d^2, index) order with identical squared distances, edge cases, and the
+closed-form lattice pins."""
+import math
+
+import numpy as np
+import pytest
+
+import datagen
+import oracle
+from tests.gpu_helpers import assert_nearest_equal, assert_spatial_equal, dev, host
+
+pytestmark = pytest.mark.gpu
+
+
+def _ab():
+    import paper_1908_11807_b300 as ab
+    return ab
+
+
+S1 = datagen.SEED0 + 1
+CASES = {
+    # small workload: 1e4 cube points, 1e4 queries, r for mean 10, k = 10
+    "cube_1e4": lambda: (*datagen.workload("cube", 10_000, 10_000, S1), datagen.radius_for_mean(10_000, "cube")),
+    "hollow_sphere_2e4": lambda: (*datagen.workload("hollow_sphere", 20_000, 5000, S1),
+                                  datagen.radius_for_mean(20_000, "hollow_sphere")),
+    "gaussian_2e4": lambda: (*datagen.workload("gaussian_mixture", 20_000, 5000, S1), 0.01),
+    "duplicates": lambda: (np.repeat(datagen.cube(600, 3), 9, 0), datagen.cube(3001, 4), 0.03),
+    "flat_plane": lambda: (np.concatenate([datagen.cube(8000, 5)[:, :2], np.full((8000, 1), 0.5, np.float32)], 1),
+                           datagen.cube(2999, 6), 0.02),
+    "collinear": lambda: (np.stack([np.linspace(0, 1, 5000, dtype=np.float32)] * 3, 1), datagen.cube(1000, 7), 0.01),
+    "paper_filled": lambda: (datagen.paper_shape(20_000, "filled_cube", 8),
+                             datagen.paper_shape(5000, "filled_sphere", 9), datagen.paper_radius(20_000)),
+    "paper_hollow": lambda: (datagen.paper_shape(20_000, "hollow_cube", 10),
+                             datagen.paper_shape(5000, "hollow_sphere", 11), datagen.paper_radius(20_000)),
+    "boxes": lambda: (datagen.boxes(20_000, 12, half_max=0.01), datagen.cube(5000, 13), 0.01),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_spatial_matches_brute_force(name):
+    ab = _ab()
+    p, q, r = CASES[name]()
+    bvh = ab.BVH(dev(p))
+    og, ig = bvh.query_spatial(dev(q), r)
+    bvh.check()
+    oo, io = oracle.spatial_brute(p, q, r)
+    assert_spatial_equal(host(og), host(ig), oo, io)
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+@pytest.mark.parametrize("k", [1, 10, 27, 50])
+def test_nearest_matches_brute_force(name, k):
+    ab = _ab()
+    p, q, _ = CASES[name]()
+    bvh = ab.BVH(dev(p))
+    ig, dg = bvh.query_nearest(dev(q), k)
+    bvh.check()
+    io, do = oracle.nearest_brute(p, q, k)
+    assert_nearest_equal(host(ig), host(dg), io, do)
+
+
+@pytest.mark.parametrize("k", [2, 3, 4, 5, 8, 9, 16, 17, 31, 32, 33, 64, 100, 256, 512])
+def test_nearest_every_list_width(k):
+    ab = _ab()
+    p, q = datagen.workload("cube", 3000, 700, 21)
+    bvh = ab.BVH(dev(p))
+    ig, dg = bvh.query_nearest(dev(q), k)
+    io, do = oracle.nearest_brute(p, q, k)
+    assert_nearest_equal(host(ig), host(dg), io, do)
+
+
+@pytest.mark.parametrize("opts", [dict(sort_queries=0), dict(key_bits=63), dict(stack_smem=1),
+                                  dict(stack_smem=64, block_size=64), dict(block_size=256, stack_smem=4),
+                                  dict(block_size=32)])
+def test_options_do_not_change_results(opts):
+    ab = _ab()
+    p, q = datagen.workload("hollow_sphere", 30_000, 4000, 22)
+    r = datagen.radius_for_mean(30_000, "hollow_sphere") * 3
+    bvh = ab.BVH(dev(p), **opts)
+    og, ig = bvh.query_spatial(dev(q), r)
+    kg, dg = bvh.query_nearest(dev(q), 10)
+    bvh.check()
+    oo, io = oracle.spatial_brute(p, q, r)
+    assert_spatial_equal(host(og), host(ig), oo, io)
+    ko, do = oracle.nearest_brute(p, q, 10)
+    assert_nearest_equal(host(kg), host(dg), ko, do)
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 3, 9, 10, 11])
+def test_small_trees_and_k_above_n(n):
+    ab = _ab()
+    import torch
+    p = datagen.cube(n, 30 + n).reshape(n, 3)
+    q = datagen.cube(257, 31)
+    bvh = ab.BVH(dev(p) if n else torch.zeros((0, 3), device="cuda"))
+    og, ig = bvh.query_spatial(dev(q), 0.4)
+    oo, io = oracle.spatial_brute(p, q, 0.4)
+    assert_spatial_equal(host(og), host(ig), oo, io)
+    kg, dg, offs = bvh.query_nearest(dev(q), 10, with_offsets=True)
+    ko, do = oracle.nearest_brute(p, q, 10)
+    assert_nearest_equal(host(kg), host(dg), ko, do)
+    kk = min(10, n)
+    assert host(offs).tolist() == [j * kk for j in range(258)]
+
+
+def test_query_edge_cases():
+    ab = _ab()
+    p = datagen.cube(5000, 40)
+    q = np.concatenate([datagen.cube(1000, 41), np.array([[np.nan, 0, 0], [0, np.inf, 0], [-5, -5, -5],
+                                                          [9, 9, 9], p[17], p[4000]], np.float32)])
+    bvh = ab.BVH(dev(p))
+    for r in (0.0, 1e-7, 0.05, 2.0, float("inf")):
+        og, ig = bvh.query_spatial(dev(q), r)
+        oo, io = oracle.spatial_brute(p, q, r)
+        assert_spatial_equal(host(og), host(ig), oo, io)
+    kg, dg = bvh.query_nearest(dev(q), 7)
+    ko, do = oracle.nearest_brute(p, q, 7)
+    assert_nearest_equal(host(kg), host(dg), ko, do)
+    assert host(kg)[1000].tolist() == [-1] * 7
+    # empty query set
+    import torch
+    og, ig = bvh.query_spatial(torch.zeros((0, 3), device="cuda"), 0.1)
+    assert host(og).tolist() == [0]
+    with pytest.raises(ab.ArborXError):
+        bvh.query_spatial(dev(q), -1.0)
+    with pytest.raises(ab.ArborXError):
+        bvh.query_spatial(dev(q), float("nan"))
+    with pytest.raises(ab.ArborXError):
+        bvh.query_nearest(dev(q), 0)
+    with pytest.raises(ab.ArborXError):
+        bvh.query_nearest(dev(q), 513)
+
+
+def test_adversarial_radius_edge_points():
+    # points placed at exactly the FP32 radius from the query and one ulp
+    # either side; pruning must never lose a result (conservative node boxes)
+    ab = _ab()
+    g = np.random.default_rng(50)
+    q = np.array([[0.5, 0.5, 0.5]], np.float32)
+    r = np.float32(0.1)
+    dirs = g.standard_normal((3000, 3))
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    p = (0.5 + dirs * float(r)).astype(np.float32)
+    p = np.concatenate([p, np.nextafter(p, np.float32(0.5)), np.nextafter(p, np.float32(2.0)),
+                        datagen.cube(5000, 51)]).astype(np.float32)
+    bvh = ab.BVH(dev(p))
+    og, ig = bvh.query_spatial(dev(q), float(r))
+    oo, io = oracle.spatial_brute(p, q, float(r))
+    assert_spatial_equal(host(og), host(ig), oo, io)
+    kg, dg = bvh.query_nearest(dev(q), 200)
+    ko, do = oracle.nearest_brute(p, q, 200)
+    assert_nearest_equal(host(kg), host(dg), ko, do)
+
+
+def test_spatial_split_calls_and_capacity():
+    ab = _ab()
+    import torch
+    p, q = datagen.workload("cube", 20_000, 3000, 60)
+    r = datagen.radius_for_mean(20_000, "cube")
+    bvh = ab.BVH(dev(p))
+    qd = dev(q)
+    off = bvh.query_spatial_count(qd, r)
+    nnz = int(off[-1].item())
+    idx = torch.empty(nnz, dtype=torch.int32, device="cuda")
+    bvh.query_spatial_fill(qd, r, off, idx)
+    oo, io = oracle.spatial_brute(p, q, r)
+    assert_spatial_equal(host(off), host(idx), oo, io)
+    # too small a capacity: writes are skipped and reported
+    small = torch.empty(nnz // 2, dtype=torch.int32, device="cuda")
+    bvh.query_spatial_fill(qd, r, off, small)
+    with pytest.raises(ab.ArborXError) as e:
+        bvh.check()
+    assert e.value.code == 5
+    bvh.check()  # cleared
+
+
+@pytest.mark.parametrize("side", [48])
+def test_lattice_closed_form_counts_and_knn27(side):
+    ab = _ab()
+    pts = datagen.lattice(side)
+    bvh = ab.BVH(dev(pts))
+    g = np.random.default_rng(70)
+    idx = g.integers(0, side ** 3, size=20_000)
+    sites = np.stack([idx % side, (idx // side) % side, idx // (side * side)], 1)
+    q = sites.astype(np.float32)
+    golden = {1.0: 7, 2.5: 81, 4.0: 257}
+    for r, want in golden.items():
+        og, ig = bvh.query_spatial(dev(q), r)
+        cnt = np.diff(host(og))
+        R = math.ceil(r)
+        interior = np.all((sites >= R) & (sites <= side - 1 - R), axis=1)
+        assert np.all(cnt[interior] == want)
+        # boundary sites: exact against brute force
+        b = np.nonzero(~interior)[0][:2000]
+        oo, io = oracle.spatial_brute(pts, q[b], r)
+        og_h, ig_h = host(og), host(ig)
+        sub_off = np.concatenate([[0], np.cumsum(cnt[b])])
+        sub_idx = np.concatenate([ig_h[og_h[j]:og_h[j + 1]] for j in b])
+        assert_spatial_equal(sub_off, sub_idx, oo, io)
+    kg, dg = bvh.query_nearest(dev(q), 27)
+    interior = np.all((sites >= 1) & (sites <= side - 2), axis=1)
+    off3 = np.array([dx + side * dy + side * side * dz for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)])
+    want = np.sort(idx[interior, None] + off3[None, :], axis=1)
+    assert np.array_equal(np.sort(host(kg)[interior], axis=1), want)
+    assert np.array_equal(np.unique(host(dg)[interior]), np.array([0, 1, 2, 3], np.float32))

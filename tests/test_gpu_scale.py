@@ -1,0 +1,143 @@
+"""Full-size parity: the paper-scale workloads (1e6 and 1e7 points in a
+uniform cube and on a hollow sphere, 1e7 boxes) and the 256^3 lattice, in the
+launch configuration the benchmark uses.  Results are checked on sampled
+queries against the oracle's CPU BVH (exact rows) and FP64 checker, and at
+every query through size-independent properties (closed-form lattice counts,
+CSR structure, row order)."""
+import math
+
+import numpy as np
+import pytest
+
+import datagen
+import oracle
+from oracle import tree_check
+from tests.gpu_helpers import assert_nearest_equal, assert_spatial_equal, dev, host
+
+pytestmark = pytest.mark.gpu
+
+S2 = datagen.SEED0 + 2
+S3 = datagen.SEED0 + 3
+
+
+def _ab():
+    import paper_1908_11807_b300 as ab
+    return ab
+
+
+def _sub_csr(off, idx, rows):
+    cnt = off[rows + 1] - off[rows]
+    sub_off = np.concatenate([[0], np.cumsum(cnt)])
+    sub_idx = np.concatenate([idx[off[j]:off[j + 1]] for j in rows]) if len(rows) else np.zeros(0, np.int32)
+    return sub_off, sub_idx
+
+
+@pytest.mark.parametrize("dist,n", [("cube", 1_000_000), ("hollow_sphere", 1_000_000),
+                                    ("cube", 10_000_000), ("hollow_sphere", 10_000_000)])
+def test_paper_scale_sampled_exact(dist, n):
+    ab = _ab()
+    m = 1_000_000
+    p, q = datagen.workload(dist, n, m, S2)
+    r = datagen.radius_for_mean(n, dist)
+    bvh = ab.BVH(dev(p))
+    og, ig = bvh.query_spatial(dev(q), r)
+    kg, dg = bvh.query_nearest(dev(q), 10)
+    bvh.check()
+    og, ig, kg, dg = host(og), host(ig), host(kg), host(dg)
+    # every row: CSR well formed, nearest rows sorted by (d2, index), distinct
+    assert og[0] == 0 and np.all(np.diff(og) >= 0) and og[-1] == ig.size
+    assert ig.min() >= 0 and ig.max() < n
+    assert np.all((np.diff(dg, axis=1) > 0) | ((np.diff(dg, axis=1) == 0) & (np.diff(kg, axis=1) > 0)))
+    mean = ig.size / m
+    if dist == "cube":
+        assert 9.0 < mean < 11.0  # the radius was chosen for a mean of 10 neighbours
+    # sampled rows exact against the oracle's CPU BVH
+    g = np.random.default_rng(n)
+    rows = np.sort(g.choice(m, 20_000, replace=False))
+    cpu = oracle.CpuBVH(p)
+    oo, io = cpu.spatial(q[rows], r)
+    so, si = _sub_csr(og, ig, rows)
+    assert_spatial_equal(so, si, oo, io)
+    ko, do = cpu.nearest(q[rows], 10)
+    assert_nearest_equal(kg[rows], dg[rows], ko, do)
+    # FP64 checker on a smaller sample: disagreements only at the 1e-6 edge
+    few = rows[:64]
+    bad, _ = oracle.fp64_check_spatial(p, q, r, og, ig, few)
+    assert bad == 0
+    bad, _ = oracle.fp64_check_nearest(p, q, 10, kg, few)
+    assert bad == 0
+
+
+def test_boxes_1e7_build_and_queries():
+    ab = _ab()
+    n = 10_000_000
+    b = datagen.boxes(n, S2)
+    bvh = ab.BVH(dev(b), keep_order=1)
+    rec, scene, codes, perm = bvh.export_tree(order=True)
+    bvh.check()
+    sb, _ = oracle.scene_box(b)
+    assert np.array_equal(host(scene), sb)
+    tree_check.check_lbvh(host(rec), b, host(perm), host(codes).view(np.uint64), sb, check_split=False)
+    del rec, codes, perm
+    q = datagen.cube(200_000, S2, datagen.STREAM_QUERIES)
+    og, ig = bvh.query_spatial(dev(q), 1e-3)
+    kg, dg = bvh.query_nearest(dev(q), 10)
+    rows = np.arange(0, 200_000, 50)
+    cpu = oracle.CpuBVH(b)
+    oo, io = cpu.spatial(q[rows], 1e-3)
+    so, si = _sub_csr(host(og), host(ig), rows)
+    assert_spatial_equal(so, si, oo, io)
+    ko, do = cpu.nearest(q[rows], 10)
+    assert_nearest_equal(host(kg)[rows], host(dg)[rows], ko, do)
+
+
+def _lattice_counts(sites, side, r):
+    """Closed form with clipping: number of integer offsets in the ball whose
+    target stays inside the grid, per site."""
+    R = int(math.ceil(r))
+    cnt = np.zeros(len(sites), np.int64)
+    for dx in range(-R, R + 1):
+        for dy in range(-R, R + 1):
+            for dz in range(-R, R + 1):
+                if dx * dx + dy * dy + dz * dz <= r * r:
+                    t = sites + np.array([dx, dy, dz])
+                    cnt += np.all((t >= 0) & (t < side), axis=1)
+    return cnt
+
+
+def test_lattice_256_all_sites():
+    ab = _ab()
+    side = datagen.LATTICE_SIDE
+    pts = datagen.lattice(side)
+    bvh = ab.BVH(dev(pts))
+    idx, q = datagen.lattice_sites(1_000_000, S3)
+    sites = q.astype(np.int64)
+    qd = dev(q)
+    for r, interior_count in ((1.0, 7), (2.5, 81), (4.0, 257)):
+        og, ig = bvh.query_spatial(qd, r)
+        cnt = np.diff(host(og))
+        assert np.array_equal(cnt, _lattice_counts(sites, side, r))
+        R = int(math.ceil(r))
+        interior = np.all((sites >= R) & (sites <= side - 1 - R), axis=1)
+        assert np.all(cnt[interior] == interior_count)
+        # index sets of sampled sites equal the enumerated offsets
+        og_h, ig_h = host(og), host(ig)
+        for j in np.random.default_rng(int(r * 10)).choice(len(q), 300, replace=False):
+            sx, sy, sz = sites[j]
+            want = sorted(int(x + side * y + side * side * z)
+                          for x in range(sx - R, sx + R + 1) for y in range(sy - R, sy + R + 1)
+                          for z in range(sz - R, sz + R + 1)
+                          if 0 <= x < side and 0 <= y < side and 0 <= z < side
+                          and (x - sx) ** 2 + (y - sy) ** 2 + (z - sz) ** 2 <= r * r)
+            assert sorted(ig_h[og_h[j]:og_h[j + 1]].tolist()) == want
+    kg, dg = bvh.query_nearest(qd, 27)
+    kg, dg = host(kg), host(dg)
+    interior = np.all((sites >= 1) & (sites <= side - 2), axis=1)
+    off3 = np.array([dx + side * dy + side * side * dz for dz in (-1, 0, 1) for dy in (-1, 0, 1)
+                     for dx in (-1, 0, 1)])
+    want = np.sort(idx[interior, None] + off3[None, :], axis=1)
+    assert np.array_equal(np.sort(kg[interior], axis=1), want)
+    # boundary sites (ties in the cut shell): exact against brute force
+    bnd = np.nonzero(~interior)[0][:150]
+    ko, do = oracle.nearest_brute(pts, q[bnd], 27)
+    assert_nearest_equal(kg[bnd], dg[bnd], ko, do)
