@@ -1,9 +1,9 @@
 """Benchmark of the LBVH search path on B300.
 
 One step = the whole hot path over one batch of synthetic input: build the
-tree over n points (scene box, Morton codes, radix sort, hierarchy, fit),
-Morton-sort the queries, spatial query in two passes (count, scan, read the
-total, fill) and k-nearest query.  Default workload: n = 1e7 points uniform in
+tree over n points (scene box, Morton codes, radix sort, hierarchy and box
+fit), Morton-sort the queries once, spatial query in two passes (count, scan,
+read the total, fill) and k-nearest query, both in that order.  Default workload: n = 1e7 points uniform in
 the unit cube, m = 1e6 queries from the same distribution, radius for a mean
 of 10 neighbours, k = 10.
 
@@ -130,9 +130,10 @@ def kernel_bytes(name, n, m, k, nnz, nodes):
         "onesweep_pass": sort_b(n) + sort_b(m),
         "hierarchy": 12 * n,                        # codes read, parent links written
         "fit": 52 * n + 76 * max(n - 1, 0),         # gather + leaf record, then per internal node
+        "apetrei": 48 * n + 80 * max(n - 1, 0),     # gather + leaf record, then per internal node
         "scan": 12 * m + 8,                         # counts read twice, offsets written
-        "spatial_count": 20 * m + 64 * nodes.get("spatial", 0),
-        "spatial_fill": 28 * m + 4 * nnz + 64 * nodes.get("spatial", 0),
+        "spatial_count": 20 * m + 64 * nodes.get("spatial", 0) // 2,
+        "spatial_fill": 28 * m + 4 * nnz + 64 * nodes.get("spatial", 0) // 2,
         "nearest": m * (16 + 8 * k + 8) + 64 * nodes.get("nearest", 0),
     }
     return table.get(name)
@@ -160,17 +161,17 @@ def run_gpu(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
-    def step(points, queries, out=None):
+    def step(points, queries, **opts):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         ev[0].record(stream)
-        bvh = ab.BVH(points)
+        bvh = ab.BVH(points, **opts)
         ev[1].record(stream)
-        off, idx = bvh.query_spatial(queries, r)
+        order = bvh.query_order(queries)
+        off, idx = bvh.query_spatial(queries, r, order=order)
         ev[2].record(stream)
-        kidx, kd2 = bvh.query_nearest(queries, k)
+        kidx, kd2 = bvh.query_nearest(queries, k, order=order)
         ev[3].record(stream)
-        bvh.destroy()
-        return ev, (off, idx, kidx, kd2)
+        return ev, (off, idx, kidx, kd2), bvh
 
     def barrier():
         torch.cuda.synchronize()
@@ -178,11 +179,14 @@ def run_gpu(args):
             dist.barrier()
 
     for _ in range(args.warmup):
-        step(p, q)
+        step(p, q)[2].destroy()
     barrier()
 
-    # nodes visited per query (instrumented untimed run)
-    nodes = {}
+    # internal nodes loaded per query (instrumented, untimed run)
+    _, _, sbvh = step(p, q, stats=1)
+    st = sbvh.stats()
+    sbvh.destroy()
+    nodes = {"spatial": int(st["spatial_nodes"]), "nearest": int(st["nearest_nodes"])}
 
     ab.profile_enable(True)
     ab.profile_report()  # reset
@@ -193,7 +197,8 @@ def run_gpu(args):
         for _ in range(args.steps):
             flush.fill_(1.0)  # evict L2 between steps (outside the timed interval)
             barrier()
-            ev, res = step(p, q)
+            ev, res, bvh = step(p, q)
+            bvh.destroy()
             torch.cuda.synchronize()
             t = [ev[0].elapsed_time(e) for e in ev[1:]]
             phase += np.array([t[0], t[1] - t[0], t[2] - t[1]])
@@ -212,48 +217,54 @@ def run_gpu(args):
     build_ms, spatial_ms, knn_ms = phase / args.steps
 
     # ---- end to end: pinned host buffers in, results back to host, every step
-    p_pin = torch.from_numpy(p_h).pin_memory()
-    q_pin = torch.from_numpy(q_h).pin_memory()
-    kk = min(k, n)
-    outs = dict(off=torch.empty(m + 1, dtype=torch.int64).pin_memory(),
-                kidx=torch.empty((m, kk), dtype=torch.int32).pin_memory(),
-                kd2=torch.empty((m, kk), dtype=torch.float32).pin_memory())
-    idx_pin = torch.empty(max(nnz, 1) * 2, dtype=torch.int32).pin_memory()
-    pd = torch.empty_like(p)
-    qd = torch.empty_like(q)
+    e2e = None
+    if not args.no_e2e:
+        p_pin = torch.from_numpy(p_h).pin_memory()
+        q_pin = torch.from_numpy(q_h).pin_memory()
+        kk = min(k, n)
+        outs = dict(off=torch.empty(m + 1, dtype=torch.int64).pin_memory(),
+                    kidx=torch.empty((m, kk), dtype=torch.int32).pin_memory(),
+                    kd2=torch.empty((m, kk), dtype=torch.float32).pin_memory())
+        idx_pin = torch.empty(max(nnz, 1) * 2, dtype=torch.int32).pin_memory()
+        pd = torch.empty_like(p)
+        qd = torch.empty_like(q)
 
-    def e2e_step():
-        pd.copy_(p_pin, non_blocking=True)
-        qd.copy_(q_pin, non_blocking=True)
-        ev, (off, idx, kidx, kd2) = step(pd, qd)
-        outs["off"].copy_(off, non_blocking=True)
-        idx_pin[: idx.numel()].copy_(idx, non_blocking=True)
-        outs["kidx"].copy_(kidx, non_blocking=True)
-        outs["kd2"].copy_(kd2, non_blocking=True)
-        return idx.numel()
+        def e2e_step():
+            pd.copy_(p_pin, non_blocking=True)
+            qd.copy_(q_pin, non_blocking=True)
+            ev, (off, idx, kidx, kd2), bvh = step(pd, qd)
+            bvh.destroy()
+            outs["off"].copy_(off, non_blocking=True)
+            idx_pin[: idx.numel()].copy_(idx, non_blocking=True)
+            outs["kidx"].copy_(kidx, non_blocking=True)
+            outs["kd2"].copy_(kd2, non_blocking=True)
+            return idx.numel()
 
-    for _ in range(max(1, args.warmup)):
-        e2e_step()
-    torch.cuda.synchronize()
-    e2e_ms = 0.0
-    d2h = 0
-    for _ in range(args.steps):
-        flush.fill_(1.0)
-        barrier()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        got = e2e_step()
-        e1.record(stream)
+        for _ in range(max(1, args.warmup)):
+            e2e_step()
         torch.cuda.synchronize()
-        e2e_ms += e0.elapsed_time(e1)
-        d2h = (m + 1) * 8 + got * 4 + m * kk * 8
-    e2e_ms /= args.steps
-    if ws > 1:
-        tt = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
-    e2e_value = ws * 2 * m / (e2e_ms * 1e-3) / 1e6
+        e2e_ms = 0.0
+        d2h = 0
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            got = e2e_step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            e2e_ms += e0.elapsed_time(e1)
+            d2h = (m + 1) * 8 + got * 4 + m * kk * 8
+        e2e_ms /= args.steps
+        if ws > 1:
+            tt = torch.tensor([e2e_ms], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e_ms = float(tt.item())
+        e2e_value = ws * 2 * m / (e2e_ms * 1e-3) / 1e6
+
+        e2e = {"value": round(e2e_value, 3), "unit": UNIT, "ms_per_step": round(e2e_ms, 4),
+               "h2d_bytes_per_step": int(p_h.nbytes + q_h.nbytes), "d2h_bytes_per_step": int(d2h)}
 
     # ---- roofline of the dominant kernel
     peak, peak_kind = measured_peaks()
@@ -292,9 +303,10 @@ def run_gpu(args):
                        "build_ms": round(build_ms, 4), "radius_ms": round(spatial_ms, 4),
                        "knn_ms": round(knn_ms, 4), "nnz": nnz},
         "kernels": kernels,
+        "traversal": {"spatial_nodes_per_query_per_pass": round(nodes["spatial"] / (2 * m), 2),
+                      "nearest_nodes_per_query": round(nodes["nearest"] / m, 2), "node_bytes": 64},
         "roofline": roofline,
-        "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "ms_per_step": round(e2e_ms, 4),
-                "h2d_bytes_per_step": int(p_h.nbytes + q_h.nbytes), "d2h_bytes_per_step": int(d2h)},
+        "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clocks,
     }
@@ -380,6 +392,7 @@ def main():
     ap.add_argument("--workload", default="cube_1e7", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "b300":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

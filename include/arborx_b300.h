@@ -56,6 +56,10 @@ typedef enum {
 #define ARBORX_POINTS 0 /* d_prims is float[n][3] */
 #define ARBORX_BOXES 1  /* d_prims is float[n][6] = lo.xyz, hi.xyz (lo <= hi per axis) */
 
+/* hierarchy construction (arborx_opts.build_method) */
+#define ARBORX_BUILD_APETREI 0 /* one bottom-up pass for hierarchy and boxes (Apetrei 2014) */
+#define ARBORX_BUILD_KARRAS 1  /* top-down split search per internal node (Karras 2012), then the box fit */
+
 /* limits */
 #define ARBORX_MAX_PRIMS ((int64_t)1 << 30) /* n must be < this */
 #define ARBORX_MAX_QUERIES ((int64_t)1 << 30) /* m must be < this */
@@ -89,6 +93,9 @@ typedef struct arborx_opts {
   int32_t block_size;   /* traversal threads per block: 0 = default (128); 32..256, multiple of 32 */
   int32_t stack_smem;   /* per-thread traversal-stack entries held in shared memory (0 = default 16);
                            deeper entries spill to local memory, never dropped */
+  int32_t build_method; /* ARBORX_BUILD_APETREI (default) or ARBORX_BUILD_KARRAS; both build the same binary
+                           radix tree (node numbering differs) */
+  int32_t stats;        /* 1: count the internal nodes each traversal loads (read with arborx_stats) */
   arborx_alloc_fn alloc; /* NULL: stream-ordered cudaMallocAsync / cudaFreeAsync */
   arborx_free_fn free;
   void *alloc_ctx;
@@ -133,15 +140,25 @@ ARBORX_API int arborx_size(arborx_handle h, int64_t *n, int32_t *kind);
  * clears them. */
 ARBORX_API int arborx_check(arborx_handle h, void *stream);
 
+/* Traversal order of a query set (Sec. 2.2, "Query ordering"): Morton codes of the query points
+ * scaled by the tree's scene box (points outside clamped to it), stably sorted; d_order[i] is the
+ * query traversed i-th.  Pass it to the query calls below to sort a query set once for several
+ * queries.  A tree with n = 0 or m < 2 gives the identity.
+ *   d_order  device uint32[m], written */
+ARBORX_API int arborx_query_order(arborx_handle h, const float *d_queries, int64_t m, void *stream,
+                                  uint32_t *d_order);
+
 /* Spatial query, pass 1 of the count-and-fill scheme (Sec. 2.2, "2P"): traverse the tree for
  * each of the m query points, count the primitives within distance `radius`, and write the
  * exclusive prefix sum of the counts to d_offsets[0..m] (d_offsets[m] = total, int64).
  *   d_queries  device float[m][3]; radius >= 0 and not NaN (+inf selects everything)
+ *   d_order    NULL (order the queries here when opts.sort_queries, else input order) or a
+ *              permutation of 0..m-1 from arborx_query_order (must stay valid until the fill)
  *   d_offsets  device int64[m + 1], written
- * Keeps the query permutation in the handle for the matching arborx_query_spatial_fill.
+ * Keeps the traversal order in the handle for the matching arborx_query_spatial_fill.
  * Does not synchronise. */
-ARBORX_API int arborx_query_spatial_count(arborx_handle h, const float *d_queries, int64_t m, float radius, void *stream,
-                               int64_t *d_offsets);
+ARBORX_API int arborx_query_spatial_count(arborx_handle h, const float *d_queries, int64_t m, float radius,
+                                          const uint32_t *d_order, void *stream, int64_t *d_offsets);
 
 /* Spatial query, pass 2: traverse again and write row j (the primitives within `radius` of
  * query j) to d_indices[d_offsets[j] .. d_offsets[j+1]).  Must follow
@@ -154,13 +171,14 @@ ARBORX_API int arborx_query_spatial_fill(arborx_handle h, const float *d_queries
                               const int64_t *d_offsets, int32_t *d_indices, int64_t capacity);
 
 /* Spatial query, both passes: count, read the total back to the host (synchronises `stream`),
- * allocate the indices with the handle's allocator, fill.
+ * allocate the indices with the handle's allocator, fill.  d_order as for the count pass.
  *   d_offsets   device int64[m + 1], written (CSR offsets, original query order)
  *   d_indices   receives a device int32[*nnz] array allocated with the handle's allocator
  *               (opts.alloc, else cudaMallocAsync); release it with arborx_free
  *   nnz         receives the total number of results */
-ARBORX_API int arborx_query_spatial(arborx_handle h, const float *d_queries, int64_t m, float radius, void *stream,
-                         int64_t *d_offsets, int32_t **d_indices, int64_t *nnz);
+ARBORX_API int arborx_query_spatial(arborx_handle h, const float *d_queries, int64_t m, float radius,
+                                    const uint32_t *d_order, void *stream, int64_t *d_offsets, int32_t **d_indices,
+                                    int64_t *nnz);
 
 /* Release memory returned by arborx_query_spatial (stream-ordered on `stream`). */
 ARBORX_API int arborx_free(arborx_handle h, void *d_ptr, size_t bytes, void *stream);
@@ -169,13 +187,15 @@ ARBORX_API int arborx_free(arborx_handle h, void *d_ptr, size_t bytes, void *str
  * primitives first in (d^2, index) order, found by a stack traversal that visits the closer
  * child first and skips a node whose box distance exceeds the current k-th candidate.
  *   k           1 <= k <= ARBORX_MAX_K
+ *   d_order     NULL or a traversal order from arborx_query_order (as for the spatial count)
  *   d_offsets   NULL or device int64[m + 1]: written with j * kk (CSR view of the rows)
  *   d_indices   device int32[m * kk]: row j holds query j's neighbours in (d^2, index) order;
  *               -1 where a query has fewer (non-finite query)
  *   d_dist2     NULL or device float[m * kk]: the matching squared distances (+inf for -1)
  * Does not synchronise. */
-ARBORX_API int arborx_query_nearest(arborx_handle h, const float *d_queries, int64_t m, int32_t k, void *stream,
-                         int64_t *d_offsets, int32_t *d_indices, float *d_dist2);
+ARBORX_API int arborx_query_nearest(arborx_handle h, const float *d_queries, int64_t m, int32_t k,
+                                    const uint32_t *d_order, void *stream, int64_t *d_offsets, int32_t *d_indices,
+                                    float *d_dist2);
 
 /* Copy the tree out for inspection (device to device, stream-ordered):
  *   d_records  NULL or device float[(2 + 2(n-1)) * 8] in the record layout above (n >= 1)
@@ -192,6 +212,15 @@ ARBORX_API int arborx_export_tree(arborx_handle h, void *stream, float *d_record
  * of its key (ties keep input order).  Needs temporary memory from cudaMallocAsync.
  *   1 <= key_bits <= 64; 0 <= n < ARBORX_MAX_PRIMS */
 ARBORX_API int arborx_sort_pairs(void *d_keys, uint32_t *d_perm, int64_t n, int32_t key_bits, void *stream);
+
+/* Traversal statistics of a tree built with opts.stats = 1 (synchronises `stream`): out[0], out[1] =
+ * internal nodes loaded by spatial and nearest traversals, out[2], out[3] = queries traversed,
+ * since the previous call; resets them. */
+ARBORX_API int arborx_stats(arborx_handle h, void *stream, uint64_t out[4]);
+
+/* Return the library's cached device memory (freed trees and workspaces) to the driver.  The
+ * library's stream-ordered pool keeps freed blocks for reuse until this call. */
+ARBORX_API int arborx_release_cached_memory(void);
 
 /* Process-wide kernel timing.  With on = 1, every kernel launch of the library is bracketed by a
  * pair of CUDA events on its stream (a few microseconds of host overhead per launch). */

@@ -96,15 +96,16 @@ def check_lbvh(records: np.ndarray, prims: np.ndarray, perm: np.ndarray | None =
         if enc[0] != ~0:
             _fail(f"single-leaf root must hold primitive 0, enc={enc[0]}")
         return dict(n=1, depth=0)
-    if enc[0] != 0:
-        _fail(f"root record must point at internal node 0, enc={enc[0]}")
+    root = int(enc[0])
+    if root < 0 or root >= n_int:
+        _fail(f"root record must point at an internal node, enc={root}")
 
     child = enc[2:].reshape(n_int, 2)
-    # every internal id 1..n-2 appears exactly once as a child, 0 never
+    # every internal id other than the root appears exactly once as a child
     internal_children = child[child >= 0]
     if internal_children.size != n_int - 1:
         _fail(f"{internal_children.size} internal child slots, expected {n_int - 1}")
-    if np.any(internal_children == 0) or np.any(internal_children >= n_int):
+    if np.any(internal_children == root) or np.any(internal_children >= n_int):
         _fail("internal child id out of range or pointing at the root")
     if np.unique(internal_children).size != internal_children.size:
         _fail("an internal node has two parents")
@@ -115,8 +116,8 @@ def check_lbvh(records: np.ndarray, prims: np.ndarray, perm: np.ndarray | None =
     # BFS from the root: reachability, depth, parent links
     parent = np.full(n_int, -1, np.int64)
     slot_of = np.full(n_int, -1, np.int64)  # record slot holding the node's own box
-    slot_of[0] = 0
-    frontier = np.array([0], np.int64)
+    slot_of[root] = 0
+    frontier = np.array([root], np.int64)
     seen = 1
     depth = 0
     while frontier.size:
@@ -169,7 +170,7 @@ def check_lbvh(records: np.ndarray, prims: np.ndarray, perm: np.ndarray | None =
 
     # leaf-position range per internal node, bottom-up by reverse BFS order
     order = []
-    frontier = np.array([0], np.int64)
+    frontier = np.array([root], np.int64)
     while frontier.size:
         order.append(frontier)
         kids = enc[np.stack([2 + 2 * frontier, 3 + 2 * frontier], axis=1).ravel()]
@@ -197,7 +198,7 @@ def check_lbvh(records: np.ndarray, prims: np.ndarray, perm: np.ndarray | None =
         cnt[level] = ac + bc
     if np.any(rmax - rmin + 1 != cnt):
         _fail("an internal node covers a non-contiguous leaf range")
-    if rmin[0] != 0 or rmax[0] != n - 1:
+    if rmin[root] != 0 or rmax[root] != n - 1:
         _fail("root does not cover all leaves")
 
     if check_split and codes is not None:

@@ -6,6 +6,8 @@ binding over it.  PyTorch supplies device memory and streams only.
 """
 from ._binding import (  # noqa: F401
     ARBORX_BOXES,
+    ARBORX_BUILD_APETREI,
+    ARBORX_BUILD_KARRAS,
     ARBORX_MAX_K,
     ARBORX_POINTS,
     ArborXError,
@@ -17,6 +19,7 @@ from ._binding import (  # noqa: F401
     default_opts,
     profile_enable,
     profile_report,
+    release_cached_memory,
     error_string,
     lib,
     version,

@@ -24,6 +24,8 @@ ARBORX_EOVERFLOW = 5
 ARBORX_ESTATE = 6
 ARBORX_POINTS = 0
 ARBORX_BOXES = 1
+ARBORX_BUILD_APETREI = 0
+ARBORX_BUILD_KARRAS = 1
 ARBORX_MAX_K = 512
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -38,6 +40,8 @@ class arborx_opts(ctypes.Structure):
         ("keep_order", ctypes.c_int32),
         ("block_size", ctypes.c_int32),
         ("stack_smem", ctypes.c_int32),
+        ("build_method", ctypes.c_int32),
+        ("stats", ctypes.c_int32),
         ("alloc", _ALLOC_FN),
         ("free", _FREE_FN),
         ("alloc_ctx", ctypes.c_void_p),
@@ -70,12 +74,14 @@ def lib() -> ctypes.CDLL:
         L.arborx_destroy.argtypes = [vp]
         L.arborx_size.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i32)]
         L.arborx_check.argtypes = [vp, vp]
-        L.arborx_query_spatial_count.argtypes = [vp, vp, i64, ctypes.c_float, vp, vp]
+        L.arborx_query_spatial_count.argtypes = [vp, vp, i64, ctypes.c_float, vp, vp, vp]
         L.arborx_query_spatial_fill.argtypes = [vp, vp, i64, ctypes.c_float, vp, vp, vp, i64]
-        L.arborx_query_spatial.argtypes = [vp, vp, i64, ctypes.c_float, vp, vp, ctypes.POINTER(vp),
+        L.arborx_query_spatial.argtypes = [vp, vp, i64, ctypes.c_float, vp, vp, vp, ctypes.POINTER(vp),
                                            ctypes.POINTER(i64)]
         L.arborx_free.argtypes = [vp, vp, ctypes.c_size_t, vp]
-        L.arborx_query_nearest.argtypes = [vp, vp, i64, i32, vp, vp, vp, vp]
+        L.arborx_query_nearest.argtypes = [vp, vp, i64, i32, vp, vp, vp, vp, vp]
+        L.arborx_query_order.argtypes = [vp, vp, i64, vp, vp]
+        L.arborx_stats.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_uint64)]
         L.arborx_export_tree.argtypes = [vp, vp, vp, vp, vp, vp]
         L.arborx_sort_pairs.argtypes = [vp, vp, i64, i32, vp]
         L.arborx_profile_enable.argtypes = [ctypes.c_int]
@@ -163,15 +169,32 @@ class BVH:
         _check(lib().arborx_check(self.handle, _stream()), "arborx_check")
 
     # -- spatial (2P)
+    def query_order(self, queries: torch.Tensor) -> torch.Tensor:
+        """Morton traversal order of a query set (int32 [m]), reusable across query calls."""
+        q = _as_f32_cuda(queries, 3, "queries")
+        order = torch.empty(q.shape[0], dtype=torch.int32, device=q.device)
+        _check(lib().arborx_query_order(self.handle, _ptr(q), q.shape[0], _stream(), _ptr(order)),
+               "arborx_query_order")
+        return order
+
+    def stats(self) -> dict:
+        """Internal nodes loaded and queries traversed since the last call (needs stats=1)."""
+        out = (ctypes.c_uint64 * 4)()
+        _check(lib().arborx_stats(self.handle, _stream(), out), "arborx_stats")
+        return {"spatial_nodes": out[0], "nearest_nodes": out[1], "spatial_queries": out[2],
+                "nearest_queries": out[3]}
+
     def query_spatial_count(self, queries: torch.Tensor, radius: float,
-                            offsets: Optional[torch.Tensor] = None) -> torch.Tensor:
+                            offsets: Optional[torch.Tensor] = None,
+                            order: Optional[torch.Tensor] = None) -> torch.Tensor:
         q = _as_f32_cuda(queries, 3, "queries")
         m = q.shape[0]
         if offsets is None:
             offsets = torch.empty(m + 1, dtype=torch.int64, device=q.device)
-        _check(lib().arborx_query_spatial_count(self.handle, _ptr(q), m, ctypes.c_float(radius), _stream(),
-                                                _ptr(offsets)), "arborx_query_spatial_count")
+        _check(lib().arborx_query_spatial_count(self.handle, _ptr(q), m, ctypes.c_float(radius), _ptr(order),
+                                                _stream(), _ptr(offsets)), "arborx_query_spatial_count")
         self._count_q = q
+        self._count_order = order  # must stay alive until the fill
         return offsets
 
     def query_spatial_fill(self, queries: torch.Tensor, radius: float, offsets: torch.Tensor,
@@ -184,10 +207,11 @@ class BVH:
                "arborx_query_spatial_fill")
         return indices
 
-    def query_spatial(self, queries: torch.Tensor, radius: float) -> Tuple[torch.Tensor, torch.Tensor]:
+    def query_spatial(self, queries: torch.Tensor, radius: float,
+                      order: Optional[torch.Tensor] = None) -> Tuple[torch.Tensor, torch.Tensor]:
         """CSR (offsets int64 [m+1], indices int32 [nnz]) of the primitives within
         ``radius`` of each query (count, read the total back, fill)."""
-        offsets = self.query_spatial_count(queries, radius)
+        offsets = self.query_spatial_count(queries, radius, order=order)
         nnz = int(offsets[-1].item())
         self.check()
         indices = torch.empty(nnz, dtype=torch.int32, device=offsets.device)
@@ -196,7 +220,7 @@ class BVH:
 
     # -- nearest
     def query_nearest(self, queries: torch.Tensor, k: int, return_dist2: bool = True,
-                      with_offsets: bool = False):
+                      with_offsets: bool = False, order: Optional[torch.Tensor] = None):
         """Rows [m][min(k, n)] of neighbour indices (int32) in (d2, index) order,
         and their squared distances (float32) if requested."""
         q = _as_f32_cuda(queries, 3, "queries")
@@ -205,8 +229,8 @@ class BVH:
         idx = torch.empty((m, kk), dtype=torch.int32, device=q.device)
         d2 = torch.empty((m, kk), dtype=torch.float32, device=q.device) if return_dist2 else None
         off = torch.empty(m + 1, dtype=torch.int64, device=q.device) if with_offsets else None
-        _check(lib().arborx_query_nearest(self.handle, _ptr(q), m, int(k), _stream(), _ptr(off), _ptr(idx),
-                                          _ptr(d2)), "arborx_query_nearest")
+        _check(lib().arborx_query_nearest(self.handle, _ptr(q), m, int(k), _ptr(order), _stream(), _ptr(off),
+                                          _ptr(idx), _ptr(d2)), "arborx_query_nearest")
         out = (idx, d2) if return_dist2 else (idx,)
         if with_offsets:
             out = out + (off,)
@@ -265,3 +289,8 @@ def profile_report() -> dict:
         name, cnt, ms = line.split()
         out[name] = (int(cnt), float(ms))
     return out
+
+
+def release_cached_memory() -> None:
+    """Return the library's pooled device memory to the driver."""
+    _check(lib().arborx_release_cached_memory(), "arborx_release_cached_memory")

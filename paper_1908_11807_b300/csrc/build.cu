@@ -89,6 +89,8 @@ __global__ void k_init_meta(DevMeta *meta) {
   else if (t == 7) meta->err = 0;
   else if (t >= 8 && t < 11) meta->scene[t - 8] = __int_as_float(0x7f800000);   // empty box: +inf
   else if (t >= 11 && t < 14) meta->scene[t - 8] = __int_as_float(0xff800000);  // -inf
+  else if (t >= 14 && t < 16) meta->nodes[t - 14] = 0ull;
+  else if (t >= 16 && t < 18) meta->queries[t - 16] = 0ull;
 }
 
 // ------------------------------------------------------------ Morton codes
@@ -310,6 +312,74 @@ __global__ void __launch_bounds__(256) k_fit(const float *__restrict__ prims, ui
   }
 }
 
+// Single bottom-up pass (Apetrei 2014): hierarchy and boxes together.  Internal
+// node p is the node whose split lies between sorted leaves p and p + 1.  A
+// thread starts at leaf t with range [t, t] and climbs: the parent of a node
+// covering [l, r] splits at r (node is its left child) when the augmented keys
+// share a longer prefix across r | r+1 than across l-1 | l, else at l - 1 (node
+// is its right child).  Each child writes its box record into the parent's
+// slot and exchanges its outer range end through `other[p]`; the first
+// arriver stops, the second learns the parent's full range, merges the two
+// boxes and continues.  Same binary radix tree as the top-down split rule.
+template <typename K, int KIND>
+__global__ void __launch_bounds__(256) k_apetrei(const float *__restrict__ prims, uint32_t n,
+                                                const K *__restrict__ codes, const uint32_t *__restrict__ perm,
+                                                int32_t *__restrict__ other, float4 *__restrict__ rec,
+                                                uint32_t *__restrict__ err) {
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const uint32_t prim = perm[t];
+  float lx, ly, lz, hx, hy, hz;
+  if (KIND == 0) {
+    const float *p = prims + 3 * (uint64_t)prim;
+    lx = hx = p[0]; ly = hy = p[1]; lz = hz = p[2];
+  } else {
+    const float *p = prims + 6 * (uint64_t)prim;
+    lx = p[0]; ly = p[1]; lz = p[2]; hx = p[3]; hy = p[4]; hz = p[5];
+  }
+  int enc = ~(int)prim;
+  if (n == 1) {
+    rec[0] = make_float4(lx, ly, lz, __int_as_float(enc));
+    rec[1] = make_float4(hx, hy, hz, 0.0f);
+    return;
+  }
+  const int N = (int)n;
+  int l = (int)t, r = (int)t;
+  for (int level = 0;; ++level) {
+    bool left_child;  // true: parent splits at r
+    if (l == 0) {
+      left_child = true;
+    } else if (r == N - 1) {
+      left_child = false;
+    } else {
+      const K cl = __ldg(codes + l), cr = __ldg(codes + r);
+      left_child = delta<K>(codes, cr, r, r + 1, N) > delta<K>(codes, cl, l, l - 1, N);
+    }
+    const int p = left_child ? r : l - 1;
+    if (p < 0 || p >= N - 1 || level > 128) {  // cannot happen for sorted keys; never write outside
+      set_err(err, ERR_STACK);
+      return;
+    }
+    float4 *slot = rec + 4 + 4 * (uint64_t)p + (left_child ? 0 : 2);
+    slot[0] = make_float4(lx, ly, lz, __int_as_float(enc));
+    slot[1] = make_float4(hx, hy, hz, 0.0f);
+    const int got = atom_exch_acq_rel_gpu(other + p, left_child ? l : r);
+    if (got < 0) return;  // sibling not done yet
+    if (left_child) r = got;
+    else l = got;
+    const float4 *sib = rec + 4 + 4 * (uint64_t)p + (left_child ? 2 : 0);
+    const float4 slo = ld_cg_f4(sib), shi = ld_cg_f4(sib + 1);
+    lx = fminf(lx, slo.x); ly = fminf(ly, slo.y); lz = fminf(lz, slo.z);
+    hx = fmaxf(hx, shi.x); hy = fmaxf(hy, shi.y); hz = fmaxf(hz, shi.z);
+    enc = p;
+    if (l == 0 && r == N - 1) {
+      rec[0] = make_float4(lx, ly, lz, __int_as_float(p));
+      rec[1] = make_float4(hx, hy, hz, 0.0f);
+      return;
+    }
+  }
+}
+
 int sm_count() {
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
@@ -363,6 +433,21 @@ void launch_fit(const float *prims, uint32_t n, int kind, const uint32_t *perm, 
     k_fit<1><<<ceil_div<uint32_t>(n, 256u), 256, 0, s>>>(prims, n, perm, parent, arrival, rec, err);
 }
 
+template <typename K>
+void launch_apetrei(const float *prims, uint32_t n, int kind, const K *codes, const uint32_t *perm, int32_t *other,
+                    float4 *rec, uint32_t *err, cudaStream_t s) {
+  if (n == 0) return;
+  prof::Scope ps(s, "apetrei");
+  if (kind == 0)
+    k_apetrei<K, 0><<<ceil_div<uint32_t>(n, 256u), 256, 0, s>>>(prims, n, codes, perm, other, rec, err);
+  else
+    k_apetrei<K, 1><<<ceil_div<uint32_t>(n, 256u), 256, 0, s>>>(prims, n, codes, perm, other, rec, err);
+}
+
+template void launch_apetrei<uint32_t>(const float *, uint32_t, int, const uint32_t *, const uint32_t *, int32_t *,
+                                       float4 *, uint32_t *, cudaStream_t);
+template void launch_apetrei<uint64_t>(const float *, uint32_t, int, const uint64_t *, const uint32_t *, int32_t *,
+                                       float4 *, uint32_t *, cudaStream_t);
 template void launch_morton<uint32_t>(const float *, uint32_t, int, DevMeta *, uint32_t *, uint32_t *, int, bool,
                                       cudaStream_t);
 template void launch_morton<uint64_t>(const float *, uint32_t, int, DevMeta *, uint64_t *, uint32_t *, int, bool,

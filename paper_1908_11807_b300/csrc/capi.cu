@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "../../include/arborx_b300.h"
@@ -34,6 +35,8 @@ struct arborx_bvh_s {
   int64_t count_m;
   float count_radius;
   bool count_valid;
+  // queries traversed since the last arborx_stats (spatial, nearest)
+  uint64_t stat_queries[2];
 };
 
 namespace {
@@ -53,11 +56,43 @@ struct Carver {
   }
 };
 
+// Library-owned stream-ordered pool per device.  Its release threshold is
+// unlimited so that memory freed by one build is reused by the next without
+// being unmapped at every synchronisation (the default pool trims to zero).
+constexpr int kMaxDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[kMaxDevices] = {};
+
+cudaMemPool_t lib_pool() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= kMaxDevices) return nullptr;
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (!g_pool[dev]) {
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof props);
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    uint64_t thr = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    g_pool[dev] = pool;
+  }
+  return g_pool[dev];
+}
+
 void *dev_alloc(const arborx_opts &o, size_t bytes, cudaStream_t s) {
   if (bytes == 0) bytes = kAlign;
   if (o.alloc) return o.alloc(bytes, (void *)s, o.alloc_ctx);
   void *p = nullptr;
-  if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+  cudaMemPool_t pool = lib_pool();
+  const cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, bytes, pool, s) : cudaMallocAsync(&p, bytes, s);
+  if (e != cudaSuccess) {
     cudaGetLastError();
     return nullptr;
   }
@@ -86,10 +121,11 @@ int err_bits_to_status(uint32_t bits) {
   return ARBORX_OK;
 }
 
-TravCfg trav_cfg(const arborx_opts &o) {
+TravCfg trav_cfg(const arborx_bvh_s *h, int which) {
   TravCfg c;
-  c.block = o.block_size > 0 ? o.block_size : 128;
-  c.stack_smem = o.stack_smem > 0 ? o.stack_smem : 16;
+  c.block = h->opts.block_size > 0 ? h->opts.block_size : 128;
+  c.stack_smem = h->opts.stack_smem > 0 ? h->opts.stack_smem : 16;
+  c.stats_nodes = h->opts.stats ? &h->meta->nodes[which] : nullptr;
   return c;
 }
 
@@ -98,6 +134,7 @@ bool opts_ok(const arborx_opts &o) {
   if (o.block_size != 0 && (o.block_size < 32 || o.block_size > 256 || o.block_size % 32)) return false;
   if (o.stack_smem < 0 || o.stack_smem > 64) return false;
   if ((o.alloc == nullptr) != (o.free == nullptr)) return false;
+  if (o.build_method != ARBORX_BUILD_APETREI && o.build_method != ARBORX_BUILD_KARRAS) return false;
   return true;
 }
 
@@ -147,11 +184,14 @@ int build_impl(arborx_bvh_s *h, const float *d_prims, cudaStream_t s) {
     if (nonfinite) return ARBORX_EINVAL;
   }
 
-  // scratch: keys A/B, vals A/B, parent, then the zero-initialised region
+  // scratch: keys A/B, vals A/B, parent links (Karras) or range ends
+  // (Apetrei, preset to -1), then the zero-initialised region
+  const bool karras = h->opts.build_method == ARBORX_BUILD_KARRAS;
   const size_t ws_words = sort_ws_words<K>(n, key_bits);
   const size_t zero_bytes = align_up((size_t)n_int * sizeof(uint32_t)) + align_up(ws_words * sizeof(uint32_t));
+  const size_t link_words = karras ? (size_t)(2 * n - 1) : (size_t)n_int;
   const size_t scratch_bytes = 2 * align_up((size_t)n * sizeof(K)) + 2 * align_up((size_t)n * sizeof(uint32_t)) +
-                               align_up((size_t)(2 * n - 1) * sizeof(int32_t)) + zero_bytes;
+                               align_up(link_words * sizeof(int32_t)) + zero_bytes;
   void *scratch = dev_alloc(h->opts, scratch_bytes, s);
   if (!scratch) return ARBORX_ENOMEM;
   Carver c(scratch);
@@ -159,20 +199,24 @@ int build_impl(arborx_bvh_s *h, const float *d_prims, cudaStream_t s) {
   K *kB = c.take<K>(n);
   uint32_t *vA = c.take<uint32_t>(n);
   uint32_t *vB = c.take<uint32_t>(n);
-  int32_t *parent = c.take<int32_t>(2 * n - 1);
+  int32_t *links = c.take<int32_t>(link_words);
   char *zero_base = c.base + c.off;
   uint32_t *arrival = c.take<uint32_t>(n_int);
   uint32_t *wsbase = c.take<uint32_t>(ws_words);
   cudaMemsetAsync(zero_base, 0, zero_bytes, s);
-  cudaMemsetAsync(parent, 0xff, (size_t)(2 * n - 1) * sizeof(int32_t), s);  // unset links read as -1
+  cudaMemsetAsync(links, 0xff, link_words * sizeof(int32_t), s);  // unset links read as -1
   const SortWs ws = sort_ws_carve<K>(wsbase, n, key_bits);
 
   launch_morton<K>(d_prims, un, h->kind, h->meta, kA, ws.hist, passes, true, s);
   K *skeys;
   uint32_t *perm;
   sort_pairs<K>(kA, kB, vA, vB, un, ws, &h->meta->err, s, &skeys, &perm);
-  launch_hierarchy<K>(skeys, un, parent, s);
-  launch_fit(d_prims, un, h->kind, perm, parent, arrival, h->rec, &h->meta->err, s);
+  if (karras) {
+    launch_hierarchy<K>(skeys, un, links, s);
+    launch_fit(d_prims, un, h->kind, perm, links, arrival, h->rec, &h->meta->err, s);
+  } else {
+    launch_apetrei<K>(d_prims, un, h->kind, skeys, perm, links, h->rec, &h->meta->err, s);
+  }
   st = launch_status();
   if (st == ARBORX_OK && h->opts.keep_order) {
     h->order_bytes = align_up((size_t)n * sizeof(uint64_t)) + align_up((size_t)n * sizeof(uint32_t));
@@ -249,9 +293,10 @@ int get_query_ws(arborx_bvh_s *h, int64_t m, cudaStream_t s, QueryWs *q) {
 
 // Morton-sort the queries against the tree's scene box; returns the
 // permutation (sorted position -> query index), or NULL for input order.
-int order_queries(arborx_bvh_s *h, const float *d_q, int64_t m, cudaStream_t s, QueryWs &q, const uint32_t **perm) {
-  *perm = nullptr;
-  if (!h->opts.sort_queries || m < 2 || h->n == 0) return ARBORX_OK;
+int order_queries(arborx_bvh_s *h, const float *d_q, int64_t m, cudaStream_t s, QueryWs &q, const uint32_t **perm,
+                  const uint32_t *given = nullptr) {
+  *perm = given;
+  if (given || !h->opts.sort_queries || m < 2 || h->n == 0) return ARBORX_OK;
   cudaMemsetAsync(q.sortws, 0, q.sort_words * sizeof(uint32_t), s);
   const SortWs ws = sort_ws_carve<uint32_t>(q.sortws, m, 30);
   launch_morton<uint32_t>(d_q, (uint32_t)m, ARBORX_POINTS, h->meta, q.cA, ws.hist, ws.passes, false, s);
@@ -291,6 +336,8 @@ int arborx_default_opts(arborx_opts *o) {
   o->keep_order = 0;
   o->block_size = 0;
   o->stack_smem = 0;
+  o->build_method = ARBORX_BUILD_APETREI;
+  o->stats = 0;
   return ARBORX_OK;
 }
 
@@ -351,8 +398,8 @@ int arborx_check(arborx_handle h, void *stream) {
   return err_bits_to_status(bits);
 }
 
-int arborx_query_spatial_count(arborx_handle h, const float *d_queries, int64_t m, float radius, void *stream,
-                               int64_t *d_offsets) {
+int arborx_query_spatial_count(arborx_handle h, const float *d_queries, int64_t m, float radius,
+                               const uint32_t *d_order, void *stream, int64_t *d_offsets) {
   if (!h || m < 0 || m >= ARBORX_MAX_QUERIES || !d_offsets || (m > 0 && !d_queries) || !finite_radius(radius))
     return ARBORX_EINVAL;
   const cudaStream_t s = (cudaStream_t)stream;
@@ -362,11 +409,12 @@ int arborx_query_spatial_count(arborx_handle h, const float *d_queries, int64_t 
   int st = get_query_ws(h, m, s, &q);
   if (st) return st;
   const uint32_t *perm;
-  st = order_queries(h, d_queries, m, s, q, &perm);
+  st = order_queries(h, d_queries, m, s, q, &perm, d_order);
   if (st) return st;
   const float r2 = radius * radius;  // one IEEE single rounding
   launch_spatial_count(h->rec, (uint32_t)h->n, d_queries, perm, (uint32_t)m, r2, q.counts, &h->meta->err,
-                       trav_cfg(h->opts), s);
+                       trav_cfg(h, 0), s);
+  h->stat_queries[0] += (uint64_t)m;
   launch_scan(q.counts, (uint32_t)m, d_offsets, q.scan_tmp, s);
   st = launch_status();
   if (st) return st;
@@ -388,16 +436,16 @@ int arborx_query_spatial_fill(arborx_handle h, const float *d_queries, int64_t m
   const cudaStream_t s = (cudaStream_t)stream;
   const float r2 = radius * radius;  // one IEEE single rounding
   launch_spatial_fill(h->rec, (uint32_t)h->n, d_queries, h->qperm, (uint32_t)m, r2, d_offsets, d_indices, capacity,
-                      &h->meta->err, trav_cfg(h->opts), s);
+                      &h->meta->err, trav_cfg(h, 0), s);
   return launch_status();
 }
 
-int arborx_query_spatial(arborx_handle h, const float *d_queries, int64_t m, float radius, void *stream,
-                         int64_t *d_offsets, int32_t **d_indices, int64_t *nnz) {
+int arborx_query_spatial(arborx_handle h, const float *d_queries, int64_t m, float radius, const uint32_t *d_order,
+                         void *stream, int64_t *d_offsets, int32_t **d_indices, int64_t *nnz) {
   if (!d_indices || !nnz) return ARBORX_EINVAL;
   *d_indices = nullptr;
   *nnz = 0;
-  int st = arborx_query_spatial_count(h, d_queries, m, radius, stream, d_offsets);
+  int st = arborx_query_spatial_count(h, d_queries, m, radius, d_order, stream, d_offsets);
   if (st) return st;
   const cudaStream_t s = (cudaStream_t)stream;
   int64_t total = 0;
@@ -426,8 +474,8 @@ int arborx_free(arborx_handle h, void *d_ptr, size_t bytes, void *stream) {
   return launch_status();
 }
 
-int arborx_query_nearest(arborx_handle h, const float *d_queries, int64_t m, int32_t k, void *stream,
-                         int64_t *d_offsets, int32_t *d_indices, float *d_dist2) {
+int arborx_query_nearest(arborx_handle h, const float *d_queries, int64_t m, int32_t k, const uint32_t *d_order,
+                         void *stream, int64_t *d_offsets, int32_t *d_indices, float *d_dist2) {
   if (!h || m < 0 || m >= ARBORX_MAX_QUERIES || k < 1 || k > ARBORX_MAX_K || (m > 0 && !d_queries))
     return ARBORX_EINVAL;
   const int64_t kk = k < h->n ? k : h->n;
@@ -442,11 +490,12 @@ int arborx_query_nearest(arborx_handle h, const float *d_queries, int64_t m, int
   int st = get_query_ws(h, m, s, &q);
   if (st) return st;
   const uint32_t *perm;
-  st = order_queries(h, d_queries, m, s, q, &perm);
+  st = order_queries(h, d_queries, m, s, q, &perm, d_order);
   if (st) return st;
   if (launch_nearest(h->rec, (uint32_t)h->n, d_queries, perm, (uint32_t)m, k, d_offsets, d_indices, d_dist2, nullptr,
-                     nullptr, nullptr, &h->meta->err, trav_cfg(h->opts), s))
+                     nullptr, nullptr, &h->meta->err, trav_cfg(h, 1), s))
     return ARBORX_EINVAL;
+  h->stat_queries[1] += (uint64_t)m;
   return launch_status();
 }
 
@@ -509,6 +558,54 @@ int arborx_sort_pairs(void *d_keys, uint32_t *d_perm, int64_t n, int32_t key_bit
   const int st = launch_status();
   if (st) return st;
   return err_bits_to_status(bits);
+}
+
+int arborx_query_order(arborx_handle h, const float *d_queries, int64_t m, void *stream, uint32_t *d_order) {
+  if (!h || m < 0 || m >= ARBORX_MAX_QUERIES || (m > 0 && (!d_queries || !d_order))) return ARBORX_EINVAL;
+  if (m == 0) return ARBORX_OK;
+  const cudaStream_t s = (cudaStream_t)stream;
+  h->stream = s;
+  QueryWs q;
+  int st = get_query_ws(h, m, s, &q);
+  if (st) return st;
+  const uint32_t *perm = nullptr;
+  if (h->n > 0 && m > 1) {
+    cudaMemsetAsync(q.sortws, 0, q.sort_words * sizeof(uint32_t), s);
+    const SortWs ws = sort_ws_carve<uint32_t>(q.sortws, m, 30);
+    launch_morton<uint32_t>(d_queries, (uint32_t)m, ARBORX_POINTS, h->meta, q.cA, ws.hist, ws.passes, false, s);
+    uint32_t *sk, *pm;
+    sort_pairs<uint32_t>(q.cA, q.cB, q.pA, q.pB, (uint32_t)m, ws, &h->meta->err, s, &sk, &pm);
+    perm = pm;
+  }
+  if (perm) {
+    cudaMemcpyAsync(d_order, perm, (size_t)m * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
+  } else {
+    launch_iota(d_order, (uint32_t)m, s);
+  }
+  return launch_status();
+}
+
+int arborx_stats(arborx_handle h, void *stream, uint64_t out[4]) {
+  if (!h || !out) return ARBORX_EINVAL;
+  const cudaStream_t s = (cudaStream_t)stream;
+  unsigned long long nodes[2] = {0, 0};
+  if (cudaMemcpyAsync(nodes, h->meta->nodes, sizeof nodes, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return ARBORX_ECUDA;
+  cudaMemsetAsync(h->meta->nodes, 0, sizeof nodes, s);
+  out[0] = nodes[0];
+  out[1] = nodes[1];
+  out[2] = h->stat_queries[0];
+  out[3] = h->stat_queries[1];
+  h->stat_queries[0] = h->stat_queries[1] = 0;
+  return cudaStreamSynchronize(s) == cudaSuccess ? ARBORX_OK : ARBORX_ECUDA;
+}
+
+int arborx_release_cached_memory(void) {
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  for (int d = 0; d < kMaxDevices; ++d)
+    if (g_pool[d]) cudaMemPoolTrimTo(g_pool[d], 0);
+  return launch_status();
 }
 
 }  // extern "C"

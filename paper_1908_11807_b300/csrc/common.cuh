@@ -21,6 +21,8 @@ struct DevMeta {
   uint32_t err;            // ERR_* bits, sticky until read by arborx_check
   float scene[6];          // decoded scene box lo.xyz, hi.xyz
   uint32_t pad[2];
+  unsigned long long nodes[2];    // traversal statistics: internal nodes loaded (spatial, nearest)
+  unsigned long long queries[2];  // queries traversed (spatial, nearest)
 };
 
 constexpr int kRadixBits = 8;
@@ -64,6 +66,12 @@ __device__ __forceinline__ uint32_t ld_relaxed_gpu(const uint32_t *p) {
 }
 __device__ __forceinline__ void st_relaxed_gpu(uint32_t *p, uint32_t v) {
   asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+// acq_rel exchange: publishes this thread's earlier writes, acquires the other arriver's
+__device__ __forceinline__ int32_t atom_exch_acq_rel_gpu(int32_t *p, int32_t v) {
+  int32_t old;
+  asm volatile("atom.acq_rel.gpu.global.exch.b32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
 }
 // acq_rel add: releases this thread's earlier writes, acquires the other arriver's
 __device__ __forceinline__ uint32_t atom_add_acq_rel_gpu(uint32_t *p, uint32_t v) {

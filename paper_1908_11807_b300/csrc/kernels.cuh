@@ -13,14 +13,20 @@ void launch_morton(const float *prims, uint32_t n, int kind, DevMeta *meta, K *c
                    bool write_scene, cudaStream_t s);
 template <typename K>
 void launch_hierarchy(const K *codes, uint32_t n, int32_t *parent, cudaStream_t s);
+template <typename K>
+void launch_apetrei(const float *prims, uint32_t n, int kind, const K *codes, const uint32_t *perm, int32_t *other,
+                    float4 *rec, uint32_t *err, cudaStream_t s);
 void launch_fit(const float *prims, uint32_t n, int kind, const uint32_t *perm, const int32_t *parent,
                 uint32_t *arrival, float4 *rec, uint32_t *err, cudaStream_t s);
 
 // ---- traversal (traverse.cu)
 struct TravCfg {
-  int block;       // threads per block
-  int stack_smem;  // stack entries per thread kept in shared memory
+  int block;                       // threads per block
+  int stack_smem;                  // stack entries per thread kept in shared memory
+  unsigned long long *stats_nodes; // nullable: add the internal nodes loaded here
 };
+
+void launch_iota(uint32_t *out, uint32_t m, cudaStream_t s);
 
 // counts[j] (j in original query order) = number of primitives within r2
 void launch_spatial_count(const float4 *rec, uint32_t n, const float *queries, const uint32_t *qperm, uint32_t m,

@@ -12,6 +12,7 @@ constexpr uint32_t kFlagAgg = 1u << 30;   // tile's own digit count published
 constexpr uint32_t kFlagPre = 2u << 30;   // inclusive prefix over tiles 0..t published
 constexpr uint32_t kValMask = (1u << 30) - 1u;
 constexpr uint32_t kSpinCap = 1u << 21;   // look-back give-up bound (~1 s)
+constexpr int kWin = 16;                  // predecessors loaded per look-back round trip
 
 // Exclusive scans over the 256 threads of a block, two values at once.
 __device__ __forceinline__ void block_excl_scan2(uint32_t a, uint32_t b, uint32_t &a_ex, uint32_t &b_ex,
@@ -114,26 +115,38 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(const K *__restrict__
   block_excl_scan2(cnt, hist[d], cnt_ex, h_ex, s_scan);
   s_dstart[d] = cnt_ex;
 
+  // decoupled look-back over a window of kWin predecessors at a time (independent
+  // loads, one round trip per window); stops at the first inclusive prefix
   uint32_t excl = 0;
   if (tile > 0) {
-    int j = (int)tile - 1;
-    while (j >= 0) {
-      const uint32_t *ps = status + (size_t)j * kRadix + d;
-      uint32_t st;
-      uint32_t spins = 0;
-      while (true) {
-        st = ld_relaxed_gpu(ps);
-        if (st & (kFlagAgg | kFlagPre)) break;
+    int j = (int)tile - 1;  // nearest predecessor not yet accounted for
+    uint32_t spins = 0;
+    bool done = false;
+    while (!done) {
+      uint32_t st[kWin];
+#pragma unroll
+      for (int w = 0; w < kWin; ++w)
+        st[w] = (j - w >= 0) ? ld_relaxed_gpu(status + (size_t)(j - w) * kRadix + d) : kFlagPre;
+      bool blocked = false;
+#pragma unroll
+      for (int w = 0; w < kWin; ++w) {
+        if (done || blocked) continue;
+        if ((st[w] & (kFlagAgg | kFlagPre)) == 0) {
+          blocked = true;  // predecessor j not published yet: wait for it
+        } else {
+          excl += st[w] & kValMask;
+          if (st[w] & kFlagPre) done = true;
+          --j;
+        }
+      }
+      if (blocked) {
         if (++spins >= kSpinCap) {  // give up: flag the error, unblock successors
           set_err(err, ERR_TIMEOUT);
-          st = kFlagPre;
-          break;
+          done = true;
+        } else if (spins > 256) {
+          __nanosleep(64);
         }
-        if (spins > 256) __nanosleep(64);
       }
-      excl += st & kValMask;
-      if (st & kFlagPre) break;
-      --j;
     }
     st_relaxed_gpu(my_status, kFlagPre | ((excl + cnt) & kValMask));
   }

@@ -38,7 +38,8 @@ __global__ void __launch_bounds__(kMaxBlock) k_spatial(const float4 *__restrict_
                                                  const float *__restrict__ queries, const uint32_t *__restrict__ qperm,
                                                  uint32_t m, float r2, int32_t *__restrict__ counts,
                                                  const int64_t *__restrict__ offsets, int32_t *__restrict__ indices,
-                                                 int64_t capacity, uint32_t *__restrict__ err, int stack_smem) {
+                                                 int64_t capacity, uint32_t *__restrict__ err, int stack_smem,
+                                                 unsigned long long *__restrict__ stats) {
   extern __shared__ int32_t s_stack[];
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= m) return;
@@ -49,6 +50,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_spatial(const float4 *__restrict_
   int64_t base = 0;
   if (FILL) base = __ldg(offsets + qi);
   uint32_t cnt = 0;
+  uint32_t visited = 0;  // internal nodes loaded (statistics)
 
 #define ABX_EMIT(v)                                   \
   do {                                                \
@@ -79,6 +81,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_spatial(const float4 *__restrict_
           }
           const float4 *rp = rec + 4 + 4 * (uint64_t)node;
           const float4 a0 = __ldg(rp), a1 = __ldg(rp + 1), b0 = __ldg(rp + 2), b1 = __ldg(rp + 3);
+          ++visited;
           const bool hl = dist2_box(qx, qy, qz, a0, a1) <= r2;
           const bool hr = dist2_box(qx, qy, qz, b0, b1) <= r2;
           const int el = __float_as_int(a0.w), er = __float_as_int(b0.w);
@@ -111,6 +114,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_spatial(const float4 *__restrict_
   }
 #undef ABX_EMIT
   if (!FILL) counts[qi] = (int32_t)cnt;
+  if (stats) atomicAdd(stats, (unsigned long long)visited);
 }
 
 // ---------------------------------------------------------------- nearest
@@ -231,7 +235,7 @@ struct SmemHeap {
 template <class List>
 __device__ __forceinline__ void knn_traverse(const float4 *__restrict__ rec, uint32_t n, float qx, float qy, float qz, List &L,
                                              int k, int32_t *s_node, float *s_dist, int stride, int stack_smem,
-                                             uint32_t *err) {
+                                             uint32_t *err, uint32_t &visited) {
   const float4 r0 = __ldg(rec), r1 = __ldg(rec + 1);
   const int e0 = __float_as_int(r0.w);
   const float d0 = dist2_box(qx, qy, qz, r0, r1);
@@ -251,6 +255,7 @@ __device__ __forceinline__ void knn_traverse(const float4 *__restrict__ rec, uin
     }
     const float4 *rp = rec + 4 + 4 * (uint64_t)node;
     const float4 a0 = __ldg(rp), a1 = __ldg(rp + 1), b0 = __ldg(rp + 2), b1 = __ldg(rp + 3);
+    ++visited;
     const float dl = dist2_box(qx, qy, qz, a0, a1);
     const float dr = dist2_box(qx, qy, qz, b0, b1);
     const int el = __float_as_int(a0.w), er = __float_as_int(b0.w);
@@ -304,7 +309,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_nearest(const float4 *__restrict_
                                                  int32_t *__restrict__ out_idx, float *__restrict__ out_d2,
                                                  const float *__restrict__ init_bound2, uint32_t *__restrict__ miss_list,
                                                  uint32_t *__restrict__ miss_count, uint32_t *__restrict__ err,
-                                                 int stack_smem) {
+                                                 int stack_smem, unsigned long long *__restrict__ stats) {
   extern __shared__ unsigned char s_raw[];
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
   if (offsets && t <= m) offsets[t] = (int64_t)t * kk;
@@ -319,10 +324,11 @@ __global__ void __launch_bounds__(kMaxBlock) k_nearest(const float4 *__restrict_
   const float b0 = init_bound2 ? __ldg(init_bound2 + qi) : __int_as_float(0x7f800000);
   const bool ok = finite3(qx, qy, qz);
   const int64_t row = (int64_t)qi * kk;
+  uint32_t visited = 0;
   if constexpr (KC > 0) {
     RegList<KC> L;
     L.init(b0, k);
-    if (ok && n > 0) knn_traverse(rec, n, qx, qy, qz, L, k, s_node, s_dist, B, stack_smem, err);
+    if (ok && n > 0) knn_traverse(rec, n, qx, qy, qz, L, k, s_node, s_dist, B, stack_smem, err, visited);
     if (miss_list && ok && L.bound_idx() == INT_MAX) miss_list[atomicAdd(miss_count, 1u)] = qi;
     L.write(row, kk, out_idx, out_d2);
   } else {
@@ -332,10 +338,11 @@ __global__ void __launch_bounds__(kMaxBlock) k_nearest(const float4 *__restrict_
     H.s = B;
     H.k = k;
     H.init(b0, k);
-    if (ok && n > 0) knn_traverse(rec, n, qx, qy, qz, H, k, s_node, s_dist, B, stack_smem, err);
+    if (ok && n > 0) knn_traverse(rec, n, qx, qy, qz, H, k, s_node, s_dist, B, stack_smem, err, visited);
     if (miss_list && ok && H.bound_idx() == INT_MAX) miss_list[atomicAdd(miss_count, 1u)] = qi;
     H.write(row, kk, out_idx, out_d2);
   }
+  if (stats) atomicAdd(stats, (unsigned long long)visited);
 }
 
 // ------------------------------------------------------------------- scan
@@ -415,7 +422,17 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const int32_t *__res
   if (blockIdx.x == gridDim.x - 1 && threadIdx.x == blockDim.x - 1) off[m] = run;
 }
 
+__global__ void k_iota(uint32_t *__restrict__ out, uint32_t m) {
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < m) out[t] = t;
+}
+
 }  // namespace
+
+void launch_iota(uint32_t *out, uint32_t m, cudaStream_t s) {
+  if (m == 0) return;
+  k_iota<<<ceil_div<uint32_t>(m, 256u), 256, 0, s>>>(out, m);
+}
 
 void launch_spatial_count(const float4 *rec, uint32_t n, const float *queries, const uint32_t *qperm, uint32_t m,
                           float r2, int32_t *counts, uint32_t *err, const TravCfg &cfg, cudaStream_t s) {
@@ -424,7 +441,7 @@ void launch_spatial_count(const float4 *rec, uint32_t n, const float *queries, c
   prof::Scope ps(s, "spatial_count");
   if (smem > 48 * 1024) cudaFuncSetAttribute(k_spatial<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_spatial<false><<<ceil_div<uint32_t>(m, cfg.block), cfg.block, smem, s>>>(
-      rec, n, queries, qperm, m, r2, counts, nullptr, nullptr, 0, err, cfg.stack_smem);
+      rec, n, queries, qperm, m, r2, counts, nullptr, nullptr, 0, err, cfg.stack_smem, cfg.stats_nodes);
 }
 
 void launch_spatial_fill(const float4 *rec, uint32_t n, const float *queries, const uint32_t *qperm, uint32_t m,
@@ -435,7 +452,7 @@ void launch_spatial_fill(const float4 *rec, uint32_t n, const float *queries, co
   prof::Scope ps(s, "spatial_fill");
   if (smem > 48 * 1024) cudaFuncSetAttribute(k_spatial<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_spatial<true><<<ceil_div<uint32_t>(m, cfg.block), cfg.block, smem, s>>>(
-      rec, n, queries, qperm, m, r2, nullptr, offsets, indices, capacity, err, cfg.stack_smem);
+      rec, n, queries, qperm, m, r2, nullptr, offsets, indices, capacity, err, cfg.stack_smem, cfg.stats_nodes);
 }
 
 size_t scan_tmp_words(uint32_t m) { return (size_t)ceil_div<uint32_t>(m > 0 ? m : 1, (uint32_t)kScanTile) + 1; }
@@ -456,11 +473,11 @@ template <int KC>
 static void nearest_kc(dim3 grid, int block, size_t smem, cudaStream_t s, const float4 *rec, uint32_t n,
                        const float *queries, const uint32_t *qperm, uint32_t m, int k, int kk, int64_t *offsets,
                        int32_t *out_idx, float *out_d2, const float *init_bound2, uint32_t *miss_list,
-                       uint32_t *miss_count, uint32_t *err, int stack_smem) {
+                       uint32_t *miss_count, uint32_t *err, int stack_smem, unsigned long long *stats) {
   prof::Scope ps(s, "nearest");
   if (smem > 48 * 1024) cudaFuncSetAttribute(k_nearest<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_nearest<KC><<<grid, block, smem, s>>>(rec, n, queries, qperm, m, k, kk, offsets, out_idx, out_d2, init_bound2,
-                                          miss_list, miss_count, err, stack_smem);
+                                          miss_list, miss_count, err, stack_smem, stats);
 }
 
 int launch_nearest(const float4 *rec, uint32_t n, const float *queries, const uint32_t *qperm, uint32_t m, int k,
@@ -482,7 +499,7 @@ int launch_nearest(const float4 *rec, uint32_t n, const float *queries, const ui
   const dim3 grid(ceil_div<uint32_t>(threads, (uint32_t)block));
 #define ABX_NEAREST(KC)                                                                                           \
   nearest_kc<KC>(grid, block, smem, s, rec, n, queries, qperm, m, k, kk, offsets, out_idx, out_d2, init_bound2, \
-                 miss_list, miss_count, err, cfg.stack_smem)
+                 miss_list, miss_count, err, cfg.stack_smem, cfg.stats_nodes)
   if (k <= 1) ABX_NEAREST(1);
   else if (k <= 2) ABX_NEAREST(2);
   else if (k <= 4) ABX_NEAREST(4);

@@ -49,7 +49,8 @@ def test_error_strings_and_defaults():
     assert ab.error_string(4) == "bounded device wait timed out"
     assert ab.error_string(99) == "unknown"
     o = ab.default_opts()
-    assert (o.key_bits, o.sort_queries, o.validate, o.keep_order, o.block_size, o.stack_smem) == (30, 1, 1, 0, 0, 0)
+    assert (o.key_bits, o.sort_queries, o.validate, o.keep_order, o.block_size, o.stack_smem, o.build_method,
+            o.stats) == (30, 1, 1, 0, 0, 0, 0, 0)
     assert ab.version().startswith("arborx-b300")
 
 
@@ -63,12 +64,15 @@ def test_invalid_arguments_rejected_without_device(L):
     assert L.arborx_build(None, 10, 0, ctypes.byref(o), None, None) == b.ARBORX_EINVAL
     assert L.arborx_build(None, 10, 0, ctypes.byref(o), None, ctypes.byref(h)) == b.ARBORX_EINVAL
     assert L.arborx_build(None, 1 << 30, 0, ctypes.byref(o), None, ctypes.byref(h)) == b.ARBORX_EINVAL
-    for field, val in (("key_bits", 31), ("block_size", 48), ("block_size", 512), ("stack_smem", -1)):
+    for field, val in (("key_bits", 31), ("block_size", 48), ("block_size", 512), ("stack_smem", -1),
+                       ("build_method", 2)):
         bad = b.default_opts(**{field: val})
         assert L.arborx_build(ctypes.c_void_p(16), 10, 0, ctypes.byref(bad), None, ctypes.byref(h)) == b.ARBORX_EINVAL
     # NULL handle everywhere
-    assert L.arborx_query_nearest(None, None, 0, 10, None, None, None, None) == b.ARBORX_EINVAL
-    assert L.arborx_query_spatial_count(None, None, 0, ctypes.c_float(1.0), None, None) == b.ARBORX_EINVAL
+    assert L.arborx_query_nearest(None, None, 0, 10, None, None, None, None, None) == b.ARBORX_EINVAL
+    assert L.arborx_query_spatial_count(None, None, 0, ctypes.c_float(1.0), None, None, None) == b.ARBORX_EINVAL
+    assert L.arborx_query_order(None, None, 0, None, None) == b.ARBORX_EINVAL
+    assert L.arborx_stats(None, None, None) == b.ARBORX_EINVAL
     assert L.arborx_check(None, None) == b.ARBORX_EINVAL
     assert L.arborx_destroy(None) == b.ARBORX_OK
     assert L.arborx_default_opts(None) == b.ARBORX_EINVAL

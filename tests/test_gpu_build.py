@@ -36,10 +36,11 @@ CLOUDS = {
 
 @pytest.mark.parametrize("name", sorted(CLOUDS))
 @pytest.mark.parametrize("key_bits", [30, 63])
-def test_build_bit_exact_and_invariants(name, key_bits):
+@pytest.mark.parametrize("method", [0, 1], ids=["apetrei", "karras"])
+def test_build_bit_exact_and_invariants(name, key_bits, method):
     ab = _ab()
     p = CLOUDS[name]()
-    bvh = ab.BVH(dev(p), keep_order=1, key_bits=key_bits)
+    bvh = ab.BVH(dev(p), keep_order=1, key_bits=key_bits, build_method=method)
     rec, scene, codes, perm = bvh.export_tree(order=True)
     bvh.check()
     rec, scene, codes, perm = host(rec), host(scene), host(codes).view(np.uint64), host(perm).astype(np.int64)
@@ -55,10 +56,11 @@ def test_build_bit_exact_and_invariants(name, key_bits):
 
 
 @pytest.mark.parametrize("n", [1, 2, 5])
-def test_build_tiny_and_single_leaf(n):
+@pytest.mark.parametrize("method", [0, 1], ids=["apetrei", "karras"])
+def test_build_tiny_and_single_leaf(n, method):
     ab = _ab()
     p = datagen.cube(n, 40 + n)
-    bvh = ab.BVH(dev(p), keep_order=1)
+    bvh = ab.BVH(dev(p), keep_order=1, build_method=method)
     rec, scene, codes, perm = bvh.export_tree(order=True)
     tree_check.check_lbvh(host(rec), p, host(perm), host(codes).view(np.uint64), host(scene))
 
@@ -134,3 +136,47 @@ def test_sort_pairs_u64_matches_stable_argsort(n, key_bits):
     want = np.argsort(keys, kind="stable")
     assert np.array_equal(host(perm), want)
     assert np.array_equal(host(sk).view(np.uint64), keys[want])
+
+
+def test_apetrei_and_karras_build_the_same_tree():
+    # same binary radix tree up to node numbering: identical sets of (range, box)
+    ab = _ab()
+    p = datagen.gaussian_mixture(50_000, 77)
+    trees = []
+    for method in (0, 1):
+        bvh = ab.BVH(dev(p), keep_order=1, build_method=method)
+        rec, scene, codes, perm = bvh.export_tree(order=True)
+        rec = host(rec)
+        st = tree_check.check_lbvh(rec, p, host(perm), host(codes).view(np.uint64), host(scene))
+        # child records sorted by content describe the tree independent of numbering
+        kids = rec[2:].copy()
+        enc = kids[:, 3].view(np.int32)
+        kids[:, 3] = np.where(enc < 0, enc, 0).view(np.float32)  # keep leaves, forget internal ids
+        trees.append((np.sort(kids.view(np.uint32).view([("", np.uint32)] * 8), axis=0), st["depth"]))
+    assert np.array_equal(trees[0][0], trees[1][0])
+    assert trees[0][1] == trees[1][1]
+
+
+def test_query_order_is_stable_morton_order():
+    ab = _ab()
+    p = datagen.cube(20_000, 78)
+    q = np.concatenate([datagen.cube(5000, 79) * 1.2 - 0.1, p[:100]]).astype(np.float32)  # some outside
+    bvh = ab.BVH(dev(p))
+    order = host(bvh.query_order(dev(q))).astype(np.int64)
+    sb, _ = oracle.scene_box(p)
+    codes = oracle.morton(q, sb, 30)  # clamped into the tree's scene box
+    assert np.array_equal(order, np.lexsort((np.arange(len(q)), codes)))
+
+
+def test_traversal_statistics():
+    ab = _ab()
+    p, q = datagen.workload("cube", 100_000, 10_000, 80)
+    bvh = ab.BVH(dev(p), stats=1)
+    bvh.query_spatial(dev(q), 0.02)
+    bvh.query_nearest(dev(q), 10)
+    st = bvh.stats()
+    assert st["spatial_queries"] == 10_000 and st["nearest_queries"] == 10_000
+    # every query loads at least the root's children, at most every internal node twice (2 passes)
+    assert 10_000 * 2 <= st["spatial_nodes"] <= 2 * 10_000 * 99_999
+    assert 10_000 <= st["nearest_nodes"] <= 10_000 * 99_999
+    assert bvh.stats()["nearest_nodes"] == 0  # reset

@@ -71,7 +71,7 @@ def test_nearest_every_list_width(k):
     assert_nearest_equal(host(ig), host(dg), io, do)
 
 
-@pytest.mark.parametrize("opts", [dict(sort_queries=0), dict(key_bits=63), dict(stack_smem=1),
+@pytest.mark.parametrize("opts", [dict(sort_queries=0), dict(key_bits=63), dict(build_method=1), dict(stack_smem=1),
                                   dict(stack_smem=64, block_size=64), dict(block_size=256, stack_smem=4),
                                   dict(block_size=32)])
 def test_options_do_not_change_results(opts):
@@ -152,6 +152,26 @@ def test_adversarial_radius_edge_points():
     kg, dg = bvh.query_nearest(dev(q), 200)
     ko, do = oracle.nearest_brute(p, q, 200)
     assert_nearest_equal(host(kg), host(dg), ko, do)
+
+
+def test_shared_query_order():
+    ab = _ab()
+    p, q = datagen.workload("cube", 50_000, 7000, 61)
+    r = datagen.radius_for_mean(50_000, "cube")
+    bvh = ab.BVH(dev(p))
+    qd = dev(q)
+    order = bvh.query_order(qd)
+    og, ig = bvh.query_spatial(qd, r, order=order)
+    kg, dg = bvh.query_nearest(qd, 10, order=order)
+    oo, io = oracle.spatial_brute(p, q, r)
+    assert_spatial_equal(host(og), host(ig), oo, io)
+    ko, do = oracle.nearest_brute(p, q, 10)
+    assert_nearest_equal(host(kg), host(dg), ko, do)
+    # any permutation is a valid traversal order: results do not depend on it
+    import torch
+    rev = torch.flip(order, [0]).contiguous()
+    og2, ig2 = bvh.query_spatial(qd, r, order=rev)
+    assert_spatial_equal(host(og2), host(ig2), oo, io)
 
 
 def test_spatial_split_calls_and_capacity():
