@@ -213,6 +213,46 @@ ARBORX_API int arborx_export_tree(arborx_handle h, void *stream, float *d_record
  *   1 <= key_bits <= 64; 0 <= n < ARBORX_MAX_PRIMS */
 ARBORX_API int arborx_sort_pairs(void *d_keys, uint32_t *d_perm, int64_t n, int32_t key_bits, void *stream);
 
+/* ---------------------------------------------------------------------------------------------
+ * Learned initial bound for nearest queries.  A regressor 3 -> 64 -> 64 -> 1 (ReLU) maps a query,
+ * normalised by the tree's scene box ((q - lo) / (hi - lo), 0 on a flat axis), to an estimate y of
+ * log d_k, the distance to its k-th nearest primitive.  The paper has no such component: it only
+ * seeds the nearest traversal of Sec. 2.2 with the squared bound exp(2 (y + margin)); queries that
+ * find fewer than k primitives inside the bound are traversed again without it, so results are
+ * exactly those of arborx_query_nearest.  Parameters are one float32 vector of ARBORX_MLP_PARAMS
+ * values: W1 [64][3], b1 [64], W2 [64][64] (row = output unit), b2 [64], w3 [64], b3. */
+#define ARBORX_MLP_PARAMS 4481
+
+/* Regressor output y for m queries: tensor_cores = 1 runs the BF16 tensor-core kernel used by
+ * arborx_query_nearest_learned (inputs rounded to BF16, FP32 accumulation); 0 runs FP32 on CUDA cores.
+ *   d_params  device float[ARBORX_MLP_PARAMS];  d_y  device float[m], written */
+ARBORX_API int arborx_mlp_forward(arborx_handle h, const float *d_params, const float *d_queries, int64_t m,
+                                  int32_t tensor_cores, void *stream, float *d_y);
+
+/* Mean squared error of y against d_labels over b queries and its gradient w.r.t. the parameters
+ * (FP32 forward and backward on the GPU).
+ *   d_labels  device float[b];  d_grad  device float[ARBORX_MLP_PARAMS], written;
+ *   d_loss    NULL or device float[1], written */
+ARBORX_API int arborx_mlp_grad(arborx_handle h, const float *d_params, const float *d_queries, const float *d_labels,
+                               int64_t b, void *stream, float *d_grad, float *d_loss);
+
+/* Train the regressor on mt training queries: labels log(max(d_k, 1e-30)) come from this tree's own
+ * exact nearest traversal (k-th distance); then `epochs` passes of mini-batch Adam (beta 0.9 / 0.999,
+ * eps 1e-8, learning rate lr) over batches of `batch` queries, each step one gradient kernel and
+ * one update kernel.  d_params holds the initial parameters and receives the trained ones;
+ * d_loss (NULL or device float[epochs]) receives the mean batch loss of each epoch. */
+ARBORX_API int arborx_mlp_train(arborx_handle h, const float *d_queries, int64_t mt, int32_t k, int32_t epochs,
+                                int32_t batch, float lr, void *stream, float *d_params, float *d_loss);
+
+/* Nearest query with the learned initial bound (same outputs as arborx_query_nearest).
+ *   margin       added to the predicted log distance (larger: fewer fallbacks, less pruning)
+ *   h_fallbacks  NULL, or host int64 receiving the number of queries that needed the unbounded
+ *                second traversal (synchronises `stream`) */
+ARBORX_API int arborx_query_nearest_learned(arborx_handle h, const float *d_queries, int64_t m, int32_t k,
+                                            const float *d_params, float margin, const uint32_t *d_order,
+                                            void *stream, int64_t *d_offsets, int32_t *d_indices, float *d_dist2,
+                                            int64_t *h_fallbacks);
+
 /* Traversal statistics of a tree built with opts.stats = 1 (synchronises `stream`): out[0], out[1] =
  * internal nodes loaded by spatial and nearest traversals, out[2], out[3] = queries traversed,
  * since the previous call; resets them. */

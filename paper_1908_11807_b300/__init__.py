@@ -11,6 +11,7 @@ from ._binding import (  # noqa: F401
     ARBORX_MAX_K,
     ARBORX_POINTS,
     ArborXError,
+    MLP_PARAMS,
     BVH,
     arborx_build,
     arborx_query_nearest,

@@ -27,6 +27,7 @@ ARBORX_BOXES = 1
 ARBORX_BUILD_APETREI = 0
 ARBORX_BUILD_KARRAS = 1
 ARBORX_MAX_K = 512
+MLP_PARAMS = 4481
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 _FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -81,6 +82,11 @@ def lib() -> ctypes.CDLL:
         L.arborx_free.argtypes = [vp, vp, ctypes.c_size_t, vp]
         L.arborx_query_nearest.argtypes = [vp, vp, i64, i32, vp, vp, vp, vp, vp]
         L.arborx_query_order.argtypes = [vp, vp, i64, vp, vp]
+        L.arborx_mlp_forward.argtypes = [vp, vp, vp, i64, i32, vp, vp]
+        L.arborx_mlp_grad.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp]
+        L.arborx_mlp_train.argtypes = [vp, vp, i64, i32, i32, i32, ctypes.c_float, vp, vp, vp]
+        L.arborx_query_nearest_learned.argtypes = [vp, vp, i64, i32, vp, ctypes.c_float, vp, vp, vp, vp, vp,
+                                                   ctypes.POINTER(i64)]
         L.arborx_stats.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_uint64)]
         L.arborx_export_tree.argtypes = [vp, vp, vp, vp, vp, vp]
         L.arborx_sort_pairs.argtypes = [vp, vp, i64, i32, vp]
@@ -234,6 +240,51 @@ class BVH:
         out = (idx, d2) if return_dist2 else (idx,)
         if with_offsets:
             out = out + (off,)
+        return out if len(out) > 1 else out[0]
+
+    # -- learned initial bound
+    def mlp_forward(self, params: torch.Tensor, queries: torch.Tensor, tensor_cores: bool = True) -> torch.Tensor:
+        q = _as_f32_cuda(queries, 3, "queries")
+        y = torch.empty(q.shape[0], dtype=torch.float32, device=q.device)
+        _check(lib().arborx_mlp_forward(self.handle, _ptr(params), _ptr(q), q.shape[0], int(bool(tensor_cores)),
+                                        _stream(), _ptr(y)), "arborx_mlp_forward")
+        return y
+
+    def mlp_grad(self, params: torch.Tensor, queries: torch.Tensor, labels: torch.Tensor):
+        q = _as_f32_cuda(queries, 3, "queries")
+        grad = torch.empty(MLP_PARAMS, dtype=torch.float32, device=q.device)
+        loss = torch.empty(1, dtype=torch.float32, device=q.device)
+        _check(lib().arborx_mlp_grad(self.handle, _ptr(params), _ptr(q), _ptr(labels.contiguous()), q.shape[0],
+                                     _stream(), _ptr(grad), _ptr(loss)), "arborx_mlp_grad")
+        return loss, grad
+
+    def mlp_train(self, params: torch.Tensor, queries: torch.Tensor, k: int, epochs: int = 10, batch: int = 4096,
+                  lr: float = 1e-3) -> torch.Tensor:
+        """Train ``params`` (float32 [4481] CUDA tensor, updated in place); returns the loss per epoch."""
+        q = _as_f32_cuda(queries, 3, "queries")
+        if params.dtype != torch.float32 or params.numel() != MLP_PARAMS or not params.is_contiguous():
+            raise ValueError("params must be a contiguous float32 tensor of 4481 values")
+        loss = torch.empty(max(epochs, 1), dtype=torch.float32, device=q.device)
+        _check(lib().arborx_mlp_train(self.handle, _ptr(q), q.shape[0], int(k), int(epochs), int(batch),
+                                      ctypes.c_float(lr), _stream(), _ptr(params), _ptr(loss)), "arborx_mlp_train")
+        return loss[:epochs]
+
+    def query_nearest_learned(self, queries: torch.Tensor, k: int, params: torch.Tensor, margin: float,
+                              order: Optional[torch.Tensor] = None, return_dist2: bool = True,
+                              count_fallbacks: bool = False):
+        q = _as_f32_cuda(queries, 3, "queries")
+        m = q.shape[0]
+        kk = min(int(k), self.n)
+        idx = torch.empty((m, kk), dtype=torch.int32, device=q.device)
+        d2 = torch.empty((m, kk), dtype=torch.float32, device=q.device) if return_dist2 else None
+        fb = ctypes.c_int64(0)
+        _check(lib().arborx_query_nearest_learned(self.handle, _ptr(q), m, int(k), _ptr(params),
+                                                  ctypes.c_float(margin), _ptr(order), _stream(), None, _ptr(idx),
+                                                  _ptr(d2), ctypes.byref(fb) if count_fallbacks else None),
+               "arborx_query_nearest_learned")
+        out = (idx, d2) if return_dist2 else (idx,)
+        if count_fallbacks:
+            out = out + (int(fb.value),)
         return out if len(out) > 1 else out[0]
 
     # -- inspection

@@ -1,5 +1,6 @@
 // C ABI of the LBVH library: handles, memory, argument checks and the launch
 // sequences of the build and the queries (ArborX Sec. 2.1 - 2.3).
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -558,6 +559,123 @@ int arborx_sort_pairs(void *d_keys, uint32_t *d_perm, int64_t n, int32_t key_bit
   const int st = launch_status();
   if (st) return st;
   return err_bits_to_status(bits);
+}
+
+// ------------------------------------------------------------ learned bound
+
+int arborx_mlp_forward(arborx_handle h, const float *d_params, const float *d_queries, int64_t m, int32_t tensor_cores,
+                       void *stream, float *d_y) {
+  if (!h || !d_params || m < 0 || m >= ARBORX_MAX_QUERIES || (m > 0 && (!d_queries || !d_y))) return ARBORX_EINVAL;
+  const cudaStream_t s = (cudaStream_t)stream;
+  if (tensor_cores) launch_mlp_bound(d_params, d_queries, (uint32_t)m, h->meta, 0.f, nullptr, d_y, &h->meta->err, s);
+  else launch_mlp_forward(d_params, d_queries, (uint32_t)m, h->meta, d_y, s);
+  return launch_status();
+}
+
+int arborx_mlp_grad(arborx_handle h, const float *d_params, const float *d_queries, const float *d_labels, int64_t b,
+                    void *stream, float *d_grad, float *d_loss) {
+  if (!h || !d_params || !d_queries || !d_labels || !d_grad || b < 1 || b > (1 << 24)) return ARBORX_EINVAL;
+  const cudaStream_t s = (cudaStream_t)stream;
+  const int nblocks = (int)((b + 31) / 32);
+  const size_t bytes = (size_t)nblocks * (kMlpParams + 1) * sizeof(float);
+  float *partial = (float *)dev_alloc(h->opts, bytes, s);
+  if (!partial) return ARBORX_ENOMEM;
+  if (d_loss) cudaMemsetAsync(d_loss, 0, sizeof(float), s);
+  launch_mlp_grad(d_params, d_queries, d_labels, b, 0, (int)b, h->meta, partial, s);
+  launch_adam(nullptr, nullptr, nullptr, partial, nblocks, 0.f, 0.f, 0.f, 0.f, 1.f, 1.f, d_grad, d_loss, 1.f, s);
+  dev_free(h->opts, partial, bytes, s);
+  return launch_status();
+}
+
+int arborx_mlp_train(arborx_handle h, const float *d_queries, int64_t mt, int32_t k, int32_t epochs, int32_t batch,
+                     float lr, void *stream, float *d_params, float *d_loss) {
+  if (!h || !d_queries || !d_params || mt < 1 || mt >= ARBORX_MAX_QUERIES || k < 1 || k > ARBORX_MAX_K ||
+      epochs < 0 || batch < 1 || batch > (1 << 20) || !(lr >= 0.f) || h->n < 1)
+    return ARBORX_EINVAL;
+  const cudaStream_t s = (cudaStream_t)stream;
+  h->stream = s;
+  const int64_t kk = k < h->n ? k : h->n;
+  const int b = (int)std::min<int64_t>(batch, mt);
+  const int nblocks = (b + 31) / 32;
+  const size_t bytes = align_up((size_t)mt * kk * sizeof(float)) + align_up((size_t)mt * kk * sizeof(int32_t)) +
+                       align_up((size_t)mt * sizeof(float)) +
+                       align_up((size_t)nblocks * (kMlpParams + 1) * sizeof(float)) +
+                       2 * align_up((size_t)kMlpParams * sizeof(float));
+  void *ws = dev_alloc(h->opts, bytes, s);
+  if (!ws) return ARBORX_ENOMEM;
+  Carver c(ws);
+  float *d2 = c.take<float>((size_t)mt * kk);
+  int32_t *idx = c.take<int32_t>((size_t)mt * kk);
+  float *labels = c.take<float>(mt);
+  float *partial = c.take<float>((size_t)nblocks * (kMlpParams + 1));
+  float *mom = c.take<float>(kMlpParams);
+  float *vel = c.take<float>(kMlpParams);
+  // labels: exact k-th distances from the library's own nearest traversal
+  int st = arborx_query_nearest(h, d_queries, mt, k, nullptr, stream, nullptr, idx, d2);
+  if (st == ARBORX_OK) {
+    launch_labels(d2, mt, (int)kk, labels, s);
+    cudaMemsetAsync(mom, 0, 2 * align_up((size_t)kMlpParams * sizeof(float)), s);
+    if (d_loss && epochs > 0) cudaMemsetAsync(d_loss, 0, (size_t)epochs * sizeof(float), s);
+    const int64_t steps = (mt + b - 1) / b;
+    const double b1 = 0.9, b2 = 0.999;
+    int64_t t = 0;
+    for (int e = 0; e < epochs; ++e) {
+      const int64_t shift = ((int64_t)e * 7919) % mt;  // batches differ from epoch to epoch
+      for (int64_t j = 0; j < steps; ++j) {
+        ++t;
+        launch_mlp_grad(d_params, d_queries, labels, mt, (shift + j * b) % mt, b, h->meta, partial, s);
+        launch_adam(d_params, mom, vel, partial, nblocks, lr, (float)b1, (float)b2, 1e-8f,
+                    (float)(1.0 - std::pow(b1, (double)t)), (float)(1.0 - std::pow(b2, (double)t)), nullptr,
+                    d_loss ? d_loss + e : nullptr, 1.0f / (float)steps, s);
+      }
+    }
+    st = launch_status();
+  }
+  dev_free(h->opts, ws, bytes, s);
+  return st;
+}
+
+int arborx_query_nearest_learned(arborx_handle h, const float *d_queries, int64_t m, int32_t k,
+                                 const float *d_params, float margin, const uint32_t *d_order, void *stream,
+                                 int64_t *d_offsets, int32_t *d_indices, float *d_dist2, int64_t *h_fallbacks) {
+  if (!h || m < 0 || m >= ARBORX_MAX_QUERIES || k < 1 || k > ARBORX_MAX_K || (m > 0 && !d_queries) || !d_params ||
+      std::isnan(margin))
+    return ARBORX_EINVAL;
+  if (h_fallbacks) *h_fallbacks = 0;
+  if (h->n < k || m == 0)  // a bound cannot help when every primitive is returned
+    return arborx_query_nearest(h, d_queries, m, k, d_order, stream, d_offsets, d_indices, d_dist2);
+  if (!d_indices) return ARBORX_EINVAL;
+  const cudaStream_t s = (cudaStream_t)stream;
+  h->stream = s;
+  QueryWs q;
+  int st = get_query_ws(h, m, s, &q);
+  if (st) return st;
+  const uint32_t *perm;
+  st = order_queries(h, d_queries, m, s, q, &perm, d_order);
+  if (st) return st;
+  // the initial bounds reuse a Morton-code buffer (free once the order exists)
+  float *bound2 = reinterpret_cast<float *>(q.cA);
+  uint32_t *miss = q.miss;
+  uint32_t *miss_count = q.miss + m;
+  launch_mlp_bound(d_params, d_queries, (uint32_t)m, h->meta, margin, bound2, nullptr, &h->meta->err, s);
+  cudaMemsetAsync(miss_count, 0, sizeof(uint32_t), s);
+  TravCfg cfg = trav_cfg(h, 1);
+  if (launch_nearest(h->rec, (uint32_t)h->n, d_queries, perm, (uint32_t)m, k, d_offsets, d_indices, d_dist2, bound2,
+                     miss, miss_count, &h->meta->err, cfg, s))
+    return ARBORX_EINVAL;
+  // exact fallback: queries with fewer than k hits inside the bound rerun unbounded
+  launch_nearest(h->rec, (uint32_t)h->n, d_queries, miss, (uint32_t)m, k, nullptr, d_indices, d_dist2, nullptr,
+                 nullptr, nullptr, &h->meta->err, cfg, s, miss_count);
+  h->stat_queries[1] += (uint64_t)m;
+  st = launch_status();
+  if (st == ARBORX_OK && h_fallbacks) {
+    uint32_t cnt = 0;
+    if (cudaMemcpyAsync(&cnt, miss_count, sizeof cnt, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return ARBORX_ECUDA;
+    *h_fallbacks = cnt;
+  }
+  return st;
 }
 
 int arborx_query_order(arborx_handle h, const float *d_queries, int64_t m, void *stream, uint32_t *d_order) {

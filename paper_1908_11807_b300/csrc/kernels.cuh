@@ -42,8 +42,23 @@ void launch_scan(const int32_t *counts, uint32_t m, int64_t *offsets, int64_t *t
 // nearest: rows of kk = min(k, n) (index, d2) in (d2, index) order.
 // init_bound2 (nullable, by original query index): initial k-th bound; rows that
 // end with fewer than kk real hits are appended to miss_list (if non-null).
+// m_dev (nullable): device word holding the number of queries to process (<= m).
 int launch_nearest(const float4 *rec, uint32_t n, const float *queries, const uint32_t *qperm, uint32_t m, int k,
                    int64_t *offsets, int32_t *out_idx, float *out_d2, const float *init_bound2,
-                   uint32_t *miss_list, uint32_t *miss_count, uint32_t *err, const TravCfg &cfg, cudaStream_t s);
+                   uint32_t *miss_list, uint32_t *miss_count, uint32_t *err, const TravCfg &cfg, cudaStream_t s,
+                   const uint32_t *m_dev = nullptr);
+
+// ---- learned k-th-distance regressor (mlp.cu)
+constexpr int kMlpParams = 4481;  // W1 64x3, b1 64, W2 64x64, b2 64, w3 64, b3 1
+size_t mlp_grad_smem_bytes();
+void launch_mlp_grad(const float *params, const float *queries, const float *labels, int64_t mt, int64_t start, int b,
+                     const DevMeta *meta, float *partial, cudaStream_t s);
+void launch_adam(float *params, float *mom, float *vel, const float *partial, int nblocks, float lr, float b1, float b2,
+                 float eps, float c1, float c2, float *grad_out, float *loss_out, float loss_scale, cudaStream_t s);
+void launch_labels(const float *d2, int64_t mt, int kk, float *labels, cudaStream_t s);
+void launch_mlp_forward(const float *params, const float *queries, uint32_t m, const DevMeta *meta, float *y,
+                        cudaStream_t s);
+void launch_mlp_bound(const float *params, const float *queries, uint32_t m, const DevMeta *meta, float margin,
+                      float *bound2, float *y_out, uint32_t *err, cudaStream_t s);
 
 }  // namespace abx

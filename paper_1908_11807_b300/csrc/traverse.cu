@@ -301,6 +301,20 @@ __device__ __forceinline__ void knn_traverse(const float4 *__restrict__ rec, uin
   }
 }
 
+// Queries whose bounded traversal found fewer than k candidates: appended with
+// one atomic per converged group, in lane order (keeps the Morton order within
+// a warp for the fallback pass).
+__device__ __forceinline__ void append_miss(bool miss, uint32_t qi, uint32_t *miss_list, uint32_t *miss_count) {
+  const unsigned act = __activemask();
+  const unsigned bal = __ballot_sync(act, miss);
+  if (!bal) return;
+  const int leader = __ffs(act) - 1;
+  uint32_t base = 0;
+  if ((int)lane_id() == leader) base = atomicAdd(miss_count, (uint32_t)__popc(bal));
+  base = __shfl_sync(act, base, leader);
+  if (miss) miss_list[base + __popc(bal & lanemask_lt())] = qi;
+}
+
 // Threads t <= m also write offsets[t] = t * kk (CSR view of the rows).
 template <int KC>
 __global__ void __launch_bounds__(kMaxBlock) k_nearest(const float4 *__restrict__ rec, uint32_t n,
@@ -309,10 +323,12 @@ __global__ void __launch_bounds__(kMaxBlock) k_nearest(const float4 *__restrict_
                                                  int32_t *__restrict__ out_idx, float *__restrict__ out_d2,
                                                  const float *__restrict__ init_bound2, uint32_t *__restrict__ miss_list,
                                                  uint32_t *__restrict__ miss_count, uint32_t *__restrict__ err,
-                                                 int stack_smem, unsigned long long *__restrict__ stats) {
+                                                 int stack_smem, unsigned long long *__restrict__ stats,
+                                                 const uint32_t *__restrict__ m_dev) {
   extern __shared__ unsigned char s_raw[];
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
   if (offsets && t <= m) offsets[t] = (int64_t)t * kk;
+  if (m_dev) m = min(m, *m_dev);  // query count produced on the device (fallback pass)
   if (t >= m) return;
   const int B = blockDim.x;
   int32_t *s_node = reinterpret_cast<int32_t *>(s_raw) + threadIdx.x;
@@ -329,7 +345,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_nearest(const float4 *__restrict_
     RegList<KC> L;
     L.init(b0, k);
     if (ok && n > 0) knn_traverse(rec, n, qx, qy, qz, L, k, s_node, s_dist, B, stack_smem, err, visited);
-    if (miss_list && ok && L.bound_idx() == INT_MAX) miss_list[atomicAdd(miss_count, 1u)] = qi;
+    if (miss_list) append_miss(ok && L.bound_idx() == INT_MAX, qi, miss_list, miss_count);
     L.write(row, kk, out_idx, out_d2);
   } else {
     SmemHeap H;
@@ -339,7 +355,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_nearest(const float4 *__restrict_
     H.k = k;
     H.init(b0, k);
     if (ok && n > 0) knn_traverse(rec, n, qx, qy, qz, H, k, s_node, s_dist, B, stack_smem, err, visited);
-    if (miss_list && ok && H.bound_idx() == INT_MAX) miss_list[atomicAdd(miss_count, 1u)] = qi;
+    if (miss_list) append_miss(ok && H.bound_idx() == INT_MAX, qi, miss_list, miss_count);
     H.write(row, kk, out_idx, out_d2);
   }
   if (stats) atomicAdd(stats, (unsigned long long)visited);
@@ -473,16 +489,17 @@ template <int KC>
 static void nearest_kc(dim3 grid, int block, size_t smem, cudaStream_t s, const float4 *rec, uint32_t n,
                        const float *queries, const uint32_t *qperm, uint32_t m, int k, int kk, int64_t *offsets,
                        int32_t *out_idx, float *out_d2, const float *init_bound2, uint32_t *miss_list,
-                       uint32_t *miss_count, uint32_t *err, int stack_smem, unsigned long long *stats) {
+                       uint32_t *miss_count, uint32_t *err, int stack_smem, unsigned long long *stats,
+                       const uint32_t *m_dev) {
   prof::Scope ps(s, "nearest");
   if (smem > 48 * 1024) cudaFuncSetAttribute(k_nearest<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_nearest<KC><<<grid, block, smem, s>>>(rec, n, queries, qperm, m, k, kk, offsets, out_idx, out_d2, init_bound2,
-                                          miss_list, miss_count, err, stack_smem, stats);
+                                          miss_list, miss_count, err, stack_smem, stats, m_dev);
 }
 
 int launch_nearest(const float4 *rec, uint32_t n, const float *queries, const uint32_t *qperm, uint32_t m, int k,
                    int64_t *offsets, int32_t *out_idx, float *out_d2, const float *init_bound2, uint32_t *miss_list,
-                   uint32_t *miss_count, uint32_t *err, const TravCfg &cfg, cudaStream_t s) {
+                   uint32_t *miss_count, uint32_t *err, const TravCfg &cfg, cudaStream_t s, const uint32_t *m_dev) {
   const int kk = (int)std::min<int64_t>(k, n);
   const uint32_t threads = m + 1;
   int block = cfg.block;
@@ -499,7 +516,7 @@ int launch_nearest(const float4 *rec, uint32_t n, const float *queries, const ui
   const dim3 grid(ceil_div<uint32_t>(threads, (uint32_t)block));
 #define ABX_NEAREST(KC)                                                                                           \
   nearest_kc<KC>(grid, block, smem, s, rec, n, queries, qperm, m, k, kk, offsets, out_idx, out_d2, init_bound2, \
-                 miss_list, miss_count, err, cfg.stack_smem, cfg.stats_nodes)
+                 miss_list, miss_count, err, cfg.stack_smem, cfg.stats_nodes, m_dev)
   if (k <= 1) ABX_NEAREST(1);
   else if (k <= 2) ABX_NEAREST(2);
   else if (k <= 4) ABX_NEAREST(4);

@@ -1,0 +1,133 @@
+"""GPU parity of the learned initial bound: FP32 forward / backward against the
+float64 oracle, the BF16 tensor-core forward within its rounding bound, Adam
+training against the oracle's Adam, exactness of the bounded nearest query
+with its fallback, and the traversal work the trained bound saves."""
+import numpy as np
+import pytest
+
+import datagen
+import oracle
+from oracle import mlp
+from tests.gpu_helpers import assert_nearest_equal, dev, host
+
+pytestmark = pytest.mark.gpu
+
+
+def _ab():
+    import paper_1908_11807_b300 as ab
+    return ab
+
+
+def _theta(seed):
+    g = np.random.default_rng(seed)
+    th = mlp.he_init(g)
+    th += 0.05 * g.standard_normal(th.shape)  # non-zero biases too
+    return th
+
+
+def _setup(n=20_000, m=3000, seed=90):
+    ab = _ab()
+    p = datagen.gaussian_mixture(n, seed)
+    q = datagen.gaussian_mixture(m, seed, datagen.STREAM_QUERIES)
+    bvh = ab.BVH(dev(p))
+    sb, _ = oracle.scene_box(p)
+    return ab, p, q, bvh, sb
+
+
+def test_forward_fp32_matches_oracle():
+    ab, p, q, bvh, sb = _setup()
+    th = _theta(1)
+    y = host(bvh.mlp_forward(dev(th.astype(np.float32)), dev(q), tensor_cores=False))
+    y_ref, _ = mlp.forward(th.astype(np.float32).astype(np.float64), mlp.normalise(q, sb))
+    scale = 1.0 + np.abs(y_ref).max()
+    assert np.max(np.abs(y - y_ref)) <= 1e-5 * scale
+
+
+def test_forward_tensor_cores_within_bf16_bound():
+    ab, p, q, bvh, sb = _setup(m=5003)  # ragged last tile of 128
+    th = _theta(2).astype(np.float32).astype(np.float64)
+    y = host(bvh.mlp_forward(dev(th.astype(np.float32)), dev(q), tensor_cores=True))
+    bvh.check()
+    x = mlp.normalise(q, sb)
+    y_ref, (_, z1, h1, z2, h2) = mlp.forward(th, x)
+    P = mlp.unpack(th)
+    # BF16 rounding of h1 and W2 (relative 2^-9 each): |dz2_i| <= 2^-8 sum_j |W2_ij h1_j| (x2 margin)
+    dz2 = (2.0 ** -7) * (np.abs(h1) @ np.abs(P["W2"]).T) + 1e-6
+    bound = np.abs(dz2) @ np.abs(P["w3"]) + 1e-5 * (1 + np.abs(y_ref))
+    err = np.abs(y - y_ref)
+    assert np.all(err <= bound), (err.max(), bound[np.argmax(err / bound)])
+    # and it is a real product, not a copy of the FP32 path
+    assert np.corrcoef(y, y_ref)[0, 1] > 0.999
+
+
+def test_grad_matches_oracle_backward():
+    ab, p, q, bvh, sb = _setup(m=4096 + 77)
+    th = _theta(3).astype(np.float32).astype(np.float64)
+    t = np.random.default_rng(4).standard_normal(len(q)) * 0.5 - 3.0
+    loss, grad = bvh.mlp_grad(dev(th.astype(np.float32)), dev(q), dev(t.astype(np.float32)))
+    loss_ref, grad_ref = mlp.backward(th, mlp.normalise(q, sb), t.astype(np.float32).astype(np.float64))
+    assert abs(float(host(loss)[0]) - loss_ref) <= 1e-5 * loss_ref
+    g = host(grad).astype(np.float64)
+    assert np.linalg.norm(g - grad_ref) <= 1e-5 * np.linalg.norm(grad_ref)
+
+
+def test_training_steps_match_oracle_adam():
+    ab, p, q, bvh, sb = _setup(m=3 * 1024)
+    th0 = _theta(5).astype(np.float32)
+    params = dev(th0.copy())
+    k = 10
+    bvh.mlp_train(params, dev(q), k, epochs=1, batch=1024, lr=1e-3)
+    got = host(params).astype(np.float64)
+    # oracle: labels from exact brute-force k-th distances, three Adam steps on the same batches
+    _, d2 = oracle.nearest_brute(p, q, k)
+    t = mlp.label(d2[:, -1].astype(np.float64))
+    x = mlp.normalise(q, sb)
+    th = th0.astype(np.float64)
+    opt = mlp.Adam(mlp.N_PARAMS)
+    for j in range(3):
+        _, g = mlp.backward(th, x[j * 1024:(j + 1) * 1024], t[j * 1024:(j + 1) * 1024])
+        th = opt.step(th, g)
+    diff = np.abs(got - th)
+    assert np.mean(diff > 1e-5) < 0.01
+    assert diff.max() <= 2 * 3 * 1e-3
+
+
+@pytest.mark.parametrize("k", [1, 10, 50])
+def test_learned_nearest_is_exact_for_any_margin(k):
+    ab, p, q, bvh, sb = _setup(n=50_000, m=8000, seed=91)
+    qt = datagen.gaussian_mixture(20_000, 91, datagen.STREAM_TRAIN)
+    params = dev(mlp.he_init(np.random.default_rng(6)).astype(np.float32))
+    bvh.mlp_train(params, dev(qt), k, epochs=4, batch=2048, lr=3e-3)
+    ref_i, ref_d = oracle.nearest_brute(p, q, k)
+    plain_i, plain_d = bvh.query_nearest(dev(q), k)
+    assert_nearest_equal(host(plain_i), host(plain_d), ref_i, ref_d)
+    fbs = []
+    for margin in (-3.0, -0.2, 0.0, 0.3, 5.0):
+        ii, dd, fb = bvh.query_nearest_learned(dev(q), k, params, margin, count_fallbacks=True)
+        bvh.check()
+        assert_nearest_equal(host(ii), host(dd), ref_i, ref_d)
+        fbs.append(fb)
+    assert fbs[0] > fbs[-1]  # a tighter bound misses more often, results stay exact
+    assert fbs[-1] == 0
+
+
+def test_learned_bound_prunes_traversal():
+    # the trained bound must load fewer internal nodes than the plain traversal
+    ab = _ab()
+    n, m, k = 1_000_000, 200_000, 10
+    p = datagen.gaussian_mixture(n, 92)
+    q = datagen.gaussian_mixture(m, 92, datagen.STREAM_QUERIES)
+    qt = datagen.gaussian_mixture(100_000, 92, datagen.STREAM_TRAIN)
+    bvh = ab.BVH(dev(p), stats=1)
+    params = dev(mlp.he_init(np.random.default_rng(7)).astype(np.float32))
+    loss = host(bvh.mlp_train(params, dev(qt), k, epochs=8, batch=4096, lr=3e-3))
+    assert loss[-1] < loss[0]
+    qd = dev(q)
+    bvh.stats()
+    pi, pd = bvh.query_nearest(qd, k)
+    plain = bvh.stats()["nearest_nodes"]
+    li, ld, fb = bvh.query_nearest_learned(qd, k, params, 0.3, count_fallbacks=True)
+    learned = bvh.stats()["nearest_nodes"]
+    assert np.array_equal(host(pi), host(li)) and np.array_equal(host(pd), host(ld))
+    print(f"nodes per query: plain {plain / m:.1f}, learned {learned / m:.1f}, fallbacks {fb / m:.3f}")
+    assert learned < plain
