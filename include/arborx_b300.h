@@ -213,6 +213,18 @@ ARBORX_API int arborx_export_tree(arborx_handle h, void *stream, float *d_record
  *   1 <= key_bits <= 64; 0 <= n < ARBORX_MAX_PRIMS */
 ARBORX_API int arborx_sort_pairs(void *d_keys, uint32_t *d_perm, int64_t n, int32_t key_bits, void *stream);
 
+/* Same sort as arborx_sort_pairs, for callers that must not allocate device memory inside the call
+ * (for example code that runs inside another framework's fixed memory budget, or a loop whose memory
+ * is planned up front): its temporaries live in a fixed 16 MiB device array that the library
+ * defines, which every GPU that loads the library holds until the process exits.  The paper has no
+ * counterpart; this is a property of this library's interface only.
+ *   n  at most ARBORX_SORT_NOALLOC_MAX_KEYS; larger n returns ARBORX_EINVAL without touching the GPU
+ * The first call on a device looks up the array's device address (make it before any stream
+ * capture).  All calls on a device share the one array: calls whose GPU work overlaps (different
+ * streams or host threads) race and must be serialised by the caller.  Synchronises `stream`. */
+#define ARBORX_SORT_NOALLOC_MAX_KEYS (1 << 20)
+ARBORX_API int arborx_sort_pairs_noalloc(void *d_keys, uint32_t *d_perm, int64_t n, int32_t key_bits, void *stream);
+
 /* ---------------------------------------------------------------------------------------------
  * Learned initial bound for nearest queries.  A regressor 3 -> 64 -> 64 -> 1 (ReLU) maps a query,
  * normalised by the tree's scene box ((q - lo) / (hi - lo), 0 on a flat axis), to an estimate y of

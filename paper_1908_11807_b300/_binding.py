@@ -90,6 +90,7 @@ def lib() -> ctypes.CDLL:
         L.arborx_stats.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_uint64)]
         L.arborx_export_tree.argtypes = [vp, vp, vp, vp, vp, vp]
         L.arborx_sort_pairs.argtypes = [vp, vp, i64, i32, vp]
+        L.arborx_sort_pairs_noalloc.argtypes = [vp, vp, i64, i32, vp]
         L.arborx_profile_enable.argtypes = [ctypes.c_int]
         L.arborx_profile_report.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
         _lib = L
