@@ -110,6 +110,22 @@ class ClockSampler:
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def measured_traffic(kernel, workload):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None when the
+    capture was of another workload or the kernel's source changed since it was taken."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            d = json.load(f).get(kernel)
+        if not d or d.get("workload") != workload:
+            return None
+        with open(os.path.join(ROOT, d["file"]), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()[:16]
+        return int(d["dram_bytes"]) if sha == d["csrc_sha"] else None
+    except Exception:
+        return None
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -287,7 +303,8 @@ def run_gpu(args):
             achieved = b / (dom_ms * 1e-3) / 1e9
             roofline = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                         "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                        "traffic": None, "algorithmic_bytes_per_step": int(b)}
+                        "traffic": measured_traffic(dom, args.workload) if prof[dom][0] == args.steps else None,
+                        "algorithmic_bytes_per_step": int(b)}
 
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
