@@ -256,6 +256,17 @@ ARBORX_API int arborx_mlp_grad(arborx_handle h, const float *d_params, const flo
 ARBORX_API int arborx_mlp_train(arborx_handle h, const float *d_queries, int64_t mt, int32_t k, int32_t epochs,
                                 int32_t batch, float lr, void *stream, float *d_params, float *d_loss);
 
+/* Nearest query seeded with a caller-supplied upper bound per query (for example the k-th distances
+ * of the previous time step of a simulation): the traversal starts with d_bound2[j] as the k-th
+ * squared distance of query j, and queries that find fewer than k primitives within their bound are
+ * traversed again without it, so outputs equal those of arborx_query_nearest whatever the bounds.
+ *   d_bound2     device float[m] (by query index; +inf = no bound)
+ *   h_fallbacks  NULL, or host int64 receiving the number of second traversals (synchronises) */
+ARBORX_API int arborx_query_nearest_bounded(arborx_handle h, const float *d_queries, int64_t m, int32_t k,
+                                            const float *d_bound2, const uint32_t *d_order, void *stream,
+                                            int64_t *d_offsets, int32_t *d_indices, float *d_dist2,
+                                            int64_t *h_fallbacks);
+
 /* Nearest query with the learned initial bound (same outputs as arborx_query_nearest).
  *   margin       added to the predicted log distance (larger: fewer fallbacks, less pruning)
  *   h_fallbacks  NULL, or host int64 receiving the number of queries that needed the unbounded

@@ -85,6 +85,8 @@ def lib() -> ctypes.CDLL:
         L.arborx_mlp_forward.argtypes = [vp, vp, vp, i64, i32, vp, vp]
         L.arborx_mlp_grad.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp]
         L.arborx_mlp_train.argtypes = [vp, vp, i64, i32, i32, i32, ctypes.c_float, vp, vp, vp]
+        L.arborx_query_nearest_bounded.argtypes = [vp, vp, i64, i32, vp, vp, vp, vp, vp, vp,
+                                                   ctypes.POINTER(i64)]
         L.arborx_query_nearest_learned.argtypes = [vp, vp, i64, i32, vp, ctypes.c_float, vp, vp, vp, vp, vp,
                                                    ctypes.POINTER(i64)]
         L.arborx_stats.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_uint64)]
@@ -269,6 +271,26 @@ class BVH:
         _check(lib().arborx_mlp_train(self.handle, _ptr(q), q.shape[0], int(k), int(epochs), int(batch),
                                       ctypes.c_float(lr), _stream(), _ptr(params), _ptr(loss)), "arborx_mlp_train")
         return loss[:epochs]
+
+    def query_nearest_bounded(self, queries: torch.Tensor, k: int, bound2: torch.Tensor,
+                              order: Optional[torch.Tensor] = None, return_dist2: bool = True,
+                              count_fallbacks: bool = False):
+        """Nearest query whose traversal starts from the given squared bounds (float32 [m])."""
+        q = _as_f32_cuda(queries, 3, "queries")
+        m = q.shape[0]
+        kk = min(int(k), self.n)
+        idx = torch.empty((m, kk), dtype=torch.int32, device=q.device)
+        d2 = torch.empty((m, kk), dtype=torch.float32, device=q.device) if return_dist2 else None
+        fb = ctypes.c_int64(0)
+        b2 = bound2.contiguous()
+        _check(lib().arborx_query_nearest_bounded(self.handle, _ptr(q), m, int(k), _ptr(b2), _ptr(order), _stream(),
+                                                  None, _ptr(idx), _ptr(d2),
+                                                  ctypes.byref(fb) if count_fallbacks else None),
+               "arborx_query_nearest_bounded")
+        out = (idx, d2) if return_dist2 else (idx,)
+        if count_fallbacks:
+            out = out + (int(fb.value),)
+        return out if len(out) > 1 else out[0]
 
     def query_nearest_learned(self, queries: torch.Tensor, k: int, params: torch.Tensor, margin: float,
                               order: Optional[torch.Tensor] = None, return_dist2: bool = True,

@@ -635,6 +635,54 @@ int arborx_mlp_train(arborx_handle h, const float *d_queries, int64_t mt, int32_
   return st;
 }
 
+namespace {
+// Bounded nearest traversal seeded with per-query squared bounds (in `bound2`,
+// by query index; may alias the workspace), then the exact fallback pass over
+// the queries that found fewer than k primitives inside their bound.
+int nearest_bounded(arborx_handle h, const float *d_queries, int64_t m, int32_t k, const float *bound2,
+                    const uint32_t *perm, QueryWs &q, cudaStream_t s, int64_t *d_offsets, int32_t *d_indices,
+                    float *d_dist2, int64_t *h_fallbacks) {
+  uint32_t *miss = q.miss;
+  uint32_t *miss_count = q.miss + m;
+  cudaMemsetAsync(miss_count, 0, sizeof(uint32_t), s);
+  TravCfg cfg = trav_cfg(h, 1);
+  if (launch_nearest(h->rec, (uint32_t)h->n, d_queries, perm, (uint32_t)m, k, d_offsets, d_indices, d_dist2, bound2,
+                     miss, miss_count, &h->meta->err, cfg, s))
+    return ARBORX_EINVAL;
+  launch_nearest(h->rec, (uint32_t)h->n, d_queries, miss, (uint32_t)m, k, nullptr, d_indices, d_dist2, nullptr,
+                 nullptr, nullptr, &h->meta->err, cfg, s, miss_count);
+  h->stat_queries[1] += (uint64_t)m;
+  int st = launch_status();
+  if (st == ARBORX_OK && h_fallbacks) {
+    uint32_t cnt = 0;
+    if (cudaMemcpyAsync(&cnt, miss_count, sizeof cnt, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return ARBORX_ECUDA;
+    *h_fallbacks = cnt;
+  }
+  return st;
+}
+}  // namespace
+
+int arborx_query_nearest_bounded(arborx_handle h, const float *d_queries, int64_t m, int32_t k,
+                                 const float *d_bound2, const uint32_t *d_order, void *stream, int64_t *d_offsets,
+                                 int32_t *d_indices, float *d_dist2, int64_t *h_fallbacks) {
+  if (!h || m < 0 || m >= ARBORX_MAX_QUERIES || k < 1 || k > ARBORX_MAX_K || (m > 0 && (!d_queries || !d_bound2)))
+    return ARBORX_EINVAL;
+  if (h_fallbacks) *h_fallbacks = 0;
+  if (h->n < k || m == 0) return arborx_query_nearest(h, d_queries, m, k, d_order, stream, d_offsets, d_indices, d_dist2);
+  if (!d_indices) return ARBORX_EINVAL;
+  const cudaStream_t s = (cudaStream_t)stream;
+  h->stream = s;
+  QueryWs q;
+  int st = get_query_ws(h, m, s, &q);
+  if (st) return st;
+  const uint32_t *perm;
+  st = order_queries(h, d_queries, m, s, q, &perm, d_order);
+  if (st) return st;
+  return nearest_bounded(h, d_queries, m, k, d_bound2, perm, q, s, d_offsets, d_indices, d_dist2, h_fallbacks);
+}
+
 int arborx_query_nearest_learned(arborx_handle h, const float *d_queries, int64_t m, int32_t k,
                                  const float *d_params, float margin, const uint32_t *d_order, void *stream,
                                  int64_t *d_offsets, int32_t *d_indices, float *d_dist2, int64_t *h_fallbacks) {
@@ -655,27 +703,8 @@ int arborx_query_nearest_learned(arborx_handle h, const float *d_queries, int64_
   if (st) return st;
   // the initial bounds reuse a Morton-code buffer (free once the order exists)
   float *bound2 = reinterpret_cast<float *>(q.cA);
-  uint32_t *miss = q.miss;
-  uint32_t *miss_count = q.miss + m;
   launch_mlp_bound(d_params, d_queries, (uint32_t)m, h->meta, margin, bound2, nullptr, &h->meta->err, s);
-  cudaMemsetAsync(miss_count, 0, sizeof(uint32_t), s);
-  TravCfg cfg = trav_cfg(h, 1);
-  if (launch_nearest(h->rec, (uint32_t)h->n, d_queries, perm, (uint32_t)m, k, d_offsets, d_indices, d_dist2, bound2,
-                     miss, miss_count, &h->meta->err, cfg, s))
-    return ARBORX_EINVAL;
-  // exact fallback: queries with fewer than k hits inside the bound rerun unbounded
-  launch_nearest(h->rec, (uint32_t)h->n, d_queries, miss, (uint32_t)m, k, nullptr, d_indices, d_dist2, nullptr,
-                 nullptr, nullptr, &h->meta->err, cfg, s, miss_count);
-  h->stat_queries[1] += (uint64_t)m;
-  st = launch_status();
-  if (st == ARBORX_OK && h_fallbacks) {
-    uint32_t cnt = 0;
-    if (cudaMemcpyAsync(&cnt, miss_count, sizeof cnt, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
-      return ARBORX_ECUDA;
-    *h_fallbacks = cnt;
-  }
-  return st;
+  return nearest_bounded(h, d_queries, m, k, bound2, perm, q, s, d_offsets, d_indices, d_dist2, h_fallbacks);
 }
 
 int arborx_query_order(arborx_handle h, const float *d_queries, int64_t m, void *stream, uint32_t *d_order) {

@@ -131,3 +131,21 @@ def test_learned_bound_prunes_traversal():
     assert np.array_equal(host(pi), host(li)) and np.array_equal(host(pd), host(ld))
     print(f"nodes per query: plain {plain / m:.1f}, learned {learned / m:.1f}, fallbacks {fb / m:.3f}")
     assert learned < plain
+
+
+def test_bounded_nearest_is_exact_for_any_bounds():
+    # caller-supplied initial bounds: exact, too small, loose, infinite, zero, NaN-free mixture
+    ab, p, q, bvh, sb = _setup(n=30_000, m=6000, seed=93)
+    import torch
+    for k in (1, 10, 50):
+        ref_i, ref_d = oracle.nearest_brute(p, q, k)
+        exact = ref_d[:, -1].astype(np.float32)
+        g = np.random.default_rng(k)
+        choice = g.integers(0, 5, size=len(q))
+        b2 = np.where(choice == 0, exact, np.where(choice == 1, exact * 0.5,
+                      np.where(choice == 2, exact * 3.0, np.where(choice == 3, np.inf, 0.0)))).astype(np.float32)
+        ii, dd, fb = bvh.query_nearest_bounded(dev(q), k, dev(b2), count_fallbacks=True)
+        bvh.check()
+        assert_nearest_equal(host(ii), host(dd), ref_i, ref_d)
+        # queries whose bound was below the k-th distance must have fallen back
+        assert fb >= int(np.sum(b2 < exact))
