@@ -180,6 +180,25 @@ ARBORX_API int arborx_query_spatial(arborx_handle h, const float *d_queries, int
                                     const uint32_t *d_order, void *stream, int64_t *d_offsets, int32_t **d_indices,
                                     int64_t *nnz);
 
+/* One-pass spatial query (Sec. 2.2, "1P"), count call: a single traversal counts the results of
+ * every query and keeps the first `buffer_size` of them in a row buffer owned by the handle
+ * (m * buffer_size int32); the counts are scanned into d_offsets and the total is read back
+ * (synchronises `stream`) into *h_nnz.  buffer_size is the caller's estimate of the largest row;
+ * it only affects speed: rows that do not fit are produced by a second traversal in the fill call.
+ *   1 <= buffer_size <= ARBORX_MAX_BUFFER_SIZE; d_order as for arborx_query_spatial_count */
+#define ARBORX_MAX_BUFFER_SIZE 4096
+ARBORX_API int arborx_query_spatial_buffered_count(arborx_handle h, const float *d_queries, int64_t m, float radius,
+                                                   int32_t buffer_size, const uint32_t *d_order, void *stream,
+                                                   int64_t *d_offsets, int64_t *h_nnz);
+
+/* One-pass spatial query, fill call: compacts the buffered rows into d_indices at d_offsets and
+ * traverses again only for the queries whose rows overflowed the buffer.  Must follow
+ * arborx_query_spatial_buffered_count on the same handle with the same d_queries, m, radius and
+ * d_offsets; d_indices as for arborx_query_spatial_fill.  Does not synchronise. */
+ARBORX_API int arborx_query_spatial_buffered_fill(arborx_handle h, const float *d_queries, int64_t m, float radius,
+                                                  void *stream, const int64_t *d_offsets, int32_t *d_indices,
+                                                  int64_t capacity);
+
 /* Release memory returned by arborx_query_spatial (stream-ordered on `stream`). */
 ARBORX_API int arborx_free(arborx_handle h, void *d_ptr, size_t bytes, void *stream);
 

@@ -85,6 +85,9 @@ def lib() -> ctypes.CDLL:
         L.arborx_mlp_forward.argtypes = [vp, vp, vp, i64, i32, vp, vp]
         L.arborx_mlp_grad.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp]
         L.arborx_mlp_train.argtypes = [vp, vp, i64, i32, i32, i32, ctypes.c_float, vp, vp, vp]
+        L.arborx_query_spatial_buffered_count.argtypes = [vp, vp, i64, ctypes.c_float, i32, vp, vp, vp,
+                                                          ctypes.POINTER(i64)]
+        L.arborx_query_spatial_buffered_fill.argtypes = [vp, vp, i64, ctypes.c_float, vp, vp, vp, i64]
         L.arborx_query_nearest_bounded.argtypes = [vp, vp, i64, i32, vp, vp, vp, vp, vp, vp,
                                                    ctypes.POINTER(i64)]
         L.arborx_query_nearest_learned.argtypes = [vp, vp, i64, i32, vp, ctypes.c_float, vp, vp, vp, vp, vp,
@@ -216,10 +219,26 @@ class BVH:
                "arborx_query_spatial_fill")
         return indices
 
-    def query_spatial(self, queries: torch.Tensor, radius: float,
-                      order: Optional[torch.Tensor] = None) -> Tuple[torch.Tensor, torch.Tensor]:
+    def query_spatial(self, queries: torch.Tensor, radius: float, order: Optional[torch.Tensor] = None,
+                      buffer_size: int = 0) -> Tuple[torch.Tensor, torch.Tensor]:
         """CSR (offsets int64 [m+1], indices int32 [nnz]) of the primitives within
-        ``radius`` of each query (count, read the total back, fill)."""
+        ``radius`` of each query.  buffer_size = 0: two traversals (count, read the total
+        back, fill); buffer_size > 0: one traversal keeping up to buffer_size results per
+        query, a second one only for queries with more."""
+        if buffer_size > 0:
+            q = _as_f32_cuda(queries, 3, "queries")
+            m = q.shape[0]
+            offsets = torch.empty(m + 1, dtype=torch.int64, device=q.device)
+            nnz = ctypes.c_int64(0)
+            _check(lib().arborx_query_spatial_buffered_count(self.handle, _ptr(q), m, ctypes.c_float(radius),
+                                                             int(buffer_size), _ptr(order), _stream(),
+                                                             _ptr(offsets), ctypes.byref(nnz)),
+                   "arborx_query_spatial_buffered_count")
+            indices = torch.empty(nnz.value, dtype=torch.int32, device=q.device)
+            _check(lib().arborx_query_spatial_buffered_fill(self.handle, _ptr(q), m, ctypes.c_float(radius),
+                                                            _stream(), _ptr(offsets), _ptr(indices),
+                                                            indices.numel()), "arborx_query_spatial_buffered_fill")
+            return offsets, indices
         offsets = self.query_spatial_count(queries, radius, order=order)
         nnz = int(offsets[-1].item())
         self.check()

@@ -38,6 +38,11 @@ struct arborx_bvh_s {
   bool count_valid;
   // queries traversed since the last arborx_stats (spatial, nearest)
   uint64_t stat_queries[2];
+  // one-pass spatial: row buffers [m][bs], kept from the count call to the fill call
+  int32_t *sbuf;
+  size_t sbuf_bytes;
+  int buf_bs;
+  bool buffered_valid;
 };
 
 namespace {
@@ -248,6 +253,8 @@ int build_impl(arborx_bvh_s *h, const float *d_prims, cudaStream_t s) {
 void release(arborx_bvh_s *h) {
   if (!h) return;
   dev_free(h->opts, h->qws, h->qws_bytes, h->stream);
+  dev_free(h->opts, h->sbuf, h->sbuf_bytes, h->stream);
+  h->sbuf = nullptr;
   dev_free(h->opts, h->order, h->order_bytes, h->stream);
   dev_free(h->opts, h->persist, h->persist_bytes, h->stream);
   h->qws = h->order = h->persist = nullptr;
@@ -705,6 +712,73 @@ int arborx_query_nearest_learned(arborx_handle h, const float *d_queries, int64_
   float *bound2 = reinterpret_cast<float *>(q.cA);
   launch_mlp_bound(d_params, d_queries, (uint32_t)m, h->meta, margin, bound2, nullptr, &h->meta->err, s);
   return nearest_bounded(h, d_queries, m, k, bound2, perm, q, s, d_offsets, d_indices, d_dist2, h_fallbacks);
+}
+
+int arborx_query_spatial_buffered_count(arborx_handle h, const float *d_queries, int64_t m, float radius,
+                                        int32_t buffer_size, const uint32_t *d_order, void *stream,
+                                        int64_t *d_offsets, int64_t *h_nnz) {
+  if (!h || m < 0 || m >= ARBORX_MAX_QUERIES || !d_offsets || !h_nnz || (m > 0 && !d_queries) ||
+      !finite_radius(radius) || buffer_size < 1 || buffer_size > ARBORX_MAX_BUFFER_SIZE)
+    return ARBORX_EINVAL;
+  const cudaStream_t s = (cudaStream_t)stream;
+  h->stream = s;
+  h->count_valid = false;
+  h->buffered_valid = false;
+  *h_nnz = 0;
+  QueryWs q;
+  int st = get_query_ws(h, m, s, &q);
+  if (st) return st;
+  const size_t need = (size_t)m * buffer_size * sizeof(int32_t);
+  if (need > h->sbuf_bytes) {
+    dev_free(h->opts, h->sbuf, h->sbuf_bytes, s);
+    h->sbuf = (int32_t *)dev_alloc(h->opts, need, s);
+    h->sbuf_bytes = h->sbuf ? need : 0;
+    if (!h->sbuf) return ARBORX_ENOMEM;
+  }
+  const uint32_t *perm;
+  st = order_queries(h, d_queries, m, s, q, &perm, d_order);
+  if (st) return st;
+  const float r2 = radius * radius;  // one IEEE single rounding
+  uint32_t *ovf_count = q.miss + m;
+  cudaMemsetAsync(ovf_count, 0, sizeof(uint32_t), s);
+  launch_spatial_buffered(h->rec, (uint32_t)h->n, d_queries, perm, (uint32_t)m, r2, q.counts, h->sbuf, buffer_size,
+                          q.miss, ovf_count, &h->meta->err, trav_cfg(h, 0), s);
+  launch_scan(q.counts, (uint32_t)m, d_offsets, q.scan_tmp, s);
+  h->stat_queries[0] += (uint64_t)m;
+  int64_t total = 0;
+  uint32_t bits = 0;
+  if (cudaMemcpyAsync(&total, d_offsets + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(&bits, &h->meta->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return ARBORX_ECUDA;
+  st = err_bits_to_status(bits);
+  if (st) return st;
+  *h_nnz = total;
+  h->count_queries = d_queries;
+  h->count_m = m;
+  h->count_radius = radius;
+  h->buf_bs = buffer_size;
+  h->buffered_valid = true;
+  return launch_status();
+}
+
+int arborx_query_spatial_buffered_fill(arborx_handle h, const float *d_queries, int64_t m, float radius, void *stream,
+                                       const int64_t *d_offsets, int32_t *d_indices, int64_t capacity) {
+  if (!h || m < 0 || !d_offsets || (m > 0 && !d_queries) || !finite_radius(radius) || capacity < 0 ||
+      (capacity > 0 && !d_indices))
+    return ARBORX_EINVAL;
+  if (!h->buffered_valid || h->count_queries != d_queries || h->count_m != m || h->count_radius != radius)
+    return ARBORX_ESTATE;
+  const cudaStream_t s = (cudaStream_t)stream;
+  QueryWs q;
+  int st = get_query_ws(h, m, s, &q);  // same m: the same carve as the count call
+  if (st) return st;
+  launch_compact(h->sbuf, h->buf_bs, q.counts, d_offsets, (uint32_t)m, d_indices, capacity, &h->meta->err, s);
+  // queries whose rows did not fit the buffer: second traversal straight into the CSR rows
+  const float r2 = radius * radius;
+  launch_spatial_fill(h->rec, (uint32_t)h->n, d_queries, q.miss, (uint32_t)m, r2, d_offsets, d_indices, capacity,
+                      &h->meta->err, trav_cfg(h, 0), s, q.miss + m);
+  return launch_status();
 }
 
 int arborx_query_order(arborx_handle h, const float *d_queries, int64_t m, void *stream, uint32_t *d_order) {

@@ -28,13 +28,40 @@ struct TravCfg {
 
 void launch_iota(uint32_t *out, uint32_t m, cudaStream_t s);
 
+struct SpatialArgs {
+  const float4 *rec;
+  uint32_t n;
+  const float *queries;
+  const uint32_t *qperm;  // nullable: input order
+  uint32_t m;
+  float r2;
+  int32_t *counts;
+  const int64_t *offsets;
+  int32_t *indices;
+  int64_t capacity;
+  int32_t *buf;  // 1P row buffers [m][bs]
+  int bs;
+  uint32_t *ovf_list;  // 1P queries with more than bs results
+  uint32_t *ovf_count;
+  const uint32_t *m_dev;  // nullable: device-side query count
+  uint32_t *err;
+  int stack_smem;
+  unsigned long long *stats;
+};
+
 // counts[j] (j in original query order) = number of primitives within r2
 void launch_spatial_count(const float4 *rec, uint32_t n, const float *queries, const uint32_t *qperm, uint32_t m,
                           float r2, int32_t *counts, uint32_t *err, const TravCfg &cfg, cudaStream_t s);
-// fill rows at offsets[j]
+// fill rows at offsets[j]; m_dev (nullable) bounds the number of queries on the device
 void launch_spatial_fill(const float4 *rec, uint32_t n, const float *queries, const uint32_t *qperm, uint32_t m,
                          float r2, const int64_t *offsets, int32_t *indices, int64_t capacity, uint32_t *err,
-                         const TravCfg &cfg, cudaStream_t s);
+                         const TravCfg &cfg, cudaStream_t s, const uint32_t *m_dev = nullptr);
+// one pass: counts + the first bs results of each query in buf; overflowing queries listed
+void launch_spatial_buffered(const float4 *rec, uint32_t n, const float *queries, const uint32_t *qperm, uint32_t m,
+                             float r2, int32_t *counts, int32_t *buf, int bs, uint32_t *ovf_list, uint32_t *ovf_count,
+                             uint32_t *err, const TravCfg &cfg, cudaStream_t s);
+void launch_compact(const int32_t *buf, int bs, const int32_t *counts, const int64_t *offsets, uint32_t m,
+                    int32_t *indices, int64_t capacity, uint32_t *err, cudaStream_t s);
 // exclusive scan counts[m] -> offsets[m+1]; tmp holds scan_tmp_words(m) int64
 size_t scan_tmp_words(uint32_t m);
 void launch_scan(const int32_t *counts, uint32_t m, int64_t *offsets, int64_t *tmp, cudaStream_t s);

@@ -33,33 +33,55 @@ __device__ __forceinline__ bool pless(float d, int32_t i, float e, int32_t j) {
   return d < e || (d == e && i < j);
 }
 
-template <bool FILL>
-__global__ void __launch_bounds__(kMaxBlock) k_spatial(const float4 *__restrict__ rec, uint32_t n,
-                                                 const float *__restrict__ queries, const uint32_t *__restrict__ qperm,
-                                                 uint32_t m, float r2, int32_t *__restrict__ counts,
-                                                 const int64_t *__restrict__ offsets, int32_t *__restrict__ indices,
-                                                 int64_t capacity, uint32_t *__restrict__ err, int stack_smem,
-                                                 unsigned long long *__restrict__ stats) {
+// Queries flagged by a traversal (fewer than k hits inside a bound, or more
+// results than a row buffer holds): appended with one atomic per converged
+// group, in lane order (keeps the Morton order within a warp for the next pass).
+__device__ __forceinline__ void append_flagged(bool flag, uint32_t qi, uint32_t *list, uint32_t *count) {
+  const unsigned act = __activemask();
+  const unsigned bal = __ballot_sync(act, flag);
+  if (!bal) return;
+  const int leader = __ffs(act) - 1;
+  uint32_t base = 0;
+  if ((int)lane_id() == leader) base = atomicAdd(count, (uint32_t)__popc(bal));
+  base = __shfl_sync(act, base, leader);
+  if (flag) list[base + __popc(bal & lanemask_lt())] = qi;
+}
+
+// MODE kCount: counts[qi] = results.  MODE kFill: write the row at offsets[qi]
+// (2P second pass).  MODE kBuffered: count and keep the first `bs` results in
+// buf[qi * bs ...] (1P); queries with more than bs results are listed for a
+// fill pass.  m_dev (nullable) holds the number of queries on the device.
+enum : int { kCount = 0, kFill = 1, kBuffered = 2 };
+
+template <int MODE>
+__global__ void __launch_bounds__(kMaxBlock) k_spatial(const SpatialArgs a) {
   extern __shared__ int32_t s_stack[];
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t m = a.m_dev ? min(a.m, *a.m_dev) : a.m;
   if (t >= m) return;
-  const uint32_t qi = qperm ? __ldg(qperm + t) : t;
-  const float qx = __ldg(queries + 3 * (uint64_t)qi);
-  const float qy = __ldg(queries + 3 * (uint64_t)qi + 1);
-  const float qz = __ldg(queries + 3 * (uint64_t)qi + 2);
+  const float4 *__restrict__ rec = a.rec;
+  const uint32_t n = a.n;
+  const float r2 = a.r2;
+  const uint32_t qi = a.qperm ? __ldg(a.qperm + t) : t;
+  const float qx = __ldg(a.queries + 3 * (uint64_t)qi);
+  const float qy = __ldg(a.queries + 3 * (uint64_t)qi + 1);
+  const float qz = __ldg(a.queries + 3 * (uint64_t)qi + 2);
   int64_t base = 0;
-  if (FILL) base = __ldg(offsets + qi);
+  if (MODE == kFill) base = __ldg(a.offsets + qi);
+  if (MODE == kBuffered) base = (int64_t)qi * a.bs;
   uint32_t cnt = 0;
   uint32_t visited = 0;  // internal nodes loaded (statistics)
 
-#define ABX_EMIT(v)                                   \
-  do {                                                \
-    if (FILL) {                                       \
-      const int64_t pos_ = base + cnt;                \
-      if (pos_ < capacity) indices[pos_] = (v);       \
-      else set_err(err, ERR_CSR);                     \
-    }                                                 \
-    ++cnt;                                            \
+#define ABX_EMIT(v)                                       \
+  do {                                                    \
+    if (MODE == kFill) {                                  \
+      const int64_t pos_ = base + cnt;                    \
+      if (pos_ < a.capacity) a.indices[pos_] = (v);       \
+      else set_err(a.err, ERR_CSR);                       \
+    } else if (MODE == kBuffered) {                       \
+      if (cnt < (uint32_t)a.bs) a.buf[base + cnt] = (v);  \
+    }                                                     \
+    ++cnt;                                                \
   } while (0)
 
   if (n > 0 && finite3(qx, qy, qz)) {
@@ -71,12 +93,13 @@ __global__ void __launch_bounds__(kMaxBlock) k_spatial(const float4 *__restrict_
       } else {
         int32_t *my = s_stack + threadIdx.x;
         const int stride = blockDim.x;
+        const int stack_smem = a.stack_smem;
         int32_t spill[kSpill];
         int sp = 0;
         int node = e0;
         while (true) {
           if ((uint32_t)node >= n - 1) {  // corrupt tree: never read outside the records
-            set_err(err, ERR_STACK);
+            set_err(a.err, ERR_STACK);
             break;
           }
           const float4 *rp = rec + 4 + 4 * (uint64_t)node;
@@ -97,7 +120,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_spatial(const float4 *__restrict_
                 spill[sp - stack_smem] = er;
                 ++sp;
               } else {
-                set_err(err, ERR_STACK);  // cannot happen: capacity exceeds the deepest LBVH
+                set_err(a.err, ERR_STACK);  // cannot happen: capacity exceeds the deepest LBVH
               }
             }
             node = el;
@@ -113,8 +136,26 @@ __global__ void __launch_bounds__(kMaxBlock) k_spatial(const float4 *__restrict_
     }
   }
 #undef ABX_EMIT
-  if (!FILL) counts[qi] = (int32_t)cnt;
-  if (stats) atomicAdd(stats, (unsigned long long)visited);
+  if (MODE != kFill) a.counts[qi] = (int32_t)cnt;
+  if (MODE == kBuffered) append_flagged(cnt > (uint32_t)a.bs, qi, a.ovf_list, a.ovf_count);
+  if (a.stats) atomicAdd(a.stats, (unsigned long long)visited);
+}
+
+// Move buffered rows (those that fit) to their CSR place; one thread per slot.
+__global__ void __launch_bounds__(256) k_compact(const int32_t *__restrict__ buf, int bs,
+                                                const int32_t *__restrict__ counts,
+                                                const int64_t *__restrict__ offsets, uint32_t m,
+                                                int32_t *__restrict__ indices, int64_t capacity,
+                                                uint32_t *__restrict__ err) {
+  const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (uint64_t)m * bs) return;
+  const uint32_t qi = (uint32_t)(t / bs);
+  const int j = (int)(t - (uint64_t)qi * bs);
+  const int c = __ldg(counts + qi);
+  if (c > bs || j >= c) return;
+  const int64_t pos = __ldg(offsets + qi) + j;
+  if (pos < capacity) indices[pos] = __ldg(buf + t);
+  else set_err(err, ERR_CSR);
 }
 
 // ---------------------------------------------------------------- nearest
@@ -301,20 +342,6 @@ __device__ __forceinline__ void knn_traverse(const float4 *__restrict__ rec, uin
   }
 }
 
-// Queries whose bounded traversal found fewer than k candidates: appended with
-// one atomic per converged group, in lane order (keeps the Morton order within
-// a warp for the fallback pass).
-__device__ __forceinline__ void append_miss(bool miss, uint32_t qi, uint32_t *miss_list, uint32_t *miss_count) {
-  const unsigned act = __activemask();
-  const unsigned bal = __ballot_sync(act, miss);
-  if (!bal) return;
-  const int leader = __ffs(act) - 1;
-  uint32_t base = 0;
-  if ((int)lane_id() == leader) base = atomicAdd(miss_count, (uint32_t)__popc(bal));
-  base = __shfl_sync(act, base, leader);
-  if (miss) miss_list[base + __popc(bal & lanemask_lt())] = qi;
-}
-
 // Threads t <= m also write offsets[t] = t * kk (CSR view of the rows).
 template <int KC>
 __global__ void __launch_bounds__(kMaxBlock) k_nearest(const float4 *__restrict__ rec, uint32_t n,
@@ -345,7 +372,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_nearest(const float4 *__restrict_
     RegList<KC> L;
     L.init(b0, k);
     if (ok && n > 0) knn_traverse(rec, n, qx, qy, qz, L, k, s_node, s_dist, B, stack_smem, err, visited);
-    if (miss_list) append_miss(ok && L.bound_idx() == INT_MAX, qi, miss_list, miss_count);
+    if (miss_list) append_flagged(ok && L.bound_idx() == INT_MAX, qi, miss_list, miss_count);
     L.write(row, kk, out_idx, out_d2);
   } else {
     SmemHeap H;
@@ -355,7 +382,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_nearest(const float4 *__restrict_
     H.k = k;
     H.init(b0, k);
     if (ok && n > 0) knn_traverse(rec, n, qx, qy, qz, H, k, s_node, s_dist, B, stack_smem, err, visited);
-    if (miss_list) append_miss(ok && H.bound_idx() == INT_MAX, qi, miss_list, miss_count);
+    if (miss_list) append_flagged(ok && H.bound_idx() == INT_MAX, qi, miss_list, miss_count);
     H.write(row, kk, out_idx, out_d2);
   }
   if (stats) atomicAdd(stats, (unsigned long long)visited);
@@ -450,25 +477,68 @@ void launch_iota(uint32_t *out, uint32_t m, cudaStream_t s) {
   k_iota<<<ceil_div<uint32_t>(m, 256u), 256, 0, s>>>(out, m);
 }
 
+template <int MODE>
+static void spatial_launch(const SpatialArgs &args, int block, cudaStream_t s, const char *name) {
+  const size_t smem = (size_t)args.stack_smem * block * sizeof(int32_t);
+  prof::Scope ps(s, name);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k_spatial<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_spatial<MODE><<<ceil_div<uint32_t>(args.m, block), block, smem, s>>>(args);
+}
+
+static SpatialArgs spatial_args(const float4 *rec, uint32_t n, const float *queries, const uint32_t *qperm, uint32_t m,
+                                float r2, uint32_t *err, const TravCfg &cfg) {
+  SpatialArgs a{};
+  a.rec = rec;
+  a.n = n;
+  a.queries = queries;
+  a.qperm = qperm;
+  a.m = m;
+  a.r2 = r2;
+  a.err = err;
+  a.stack_smem = cfg.stack_smem;
+  a.stats = cfg.stats_nodes;
+  return a;
+}
+
 void launch_spatial_count(const float4 *rec, uint32_t n, const float *queries, const uint32_t *qperm, uint32_t m,
                           float r2, int32_t *counts, uint32_t *err, const TravCfg &cfg, cudaStream_t s) {
   if (m == 0) return;
-  const size_t smem = (size_t)cfg.stack_smem * cfg.block * sizeof(int32_t);
-  prof::Scope ps(s, "spatial_count");
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k_spatial<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_spatial<false><<<ceil_div<uint32_t>(m, cfg.block), cfg.block, smem, s>>>(
-      rec, n, queries, qperm, m, r2, counts, nullptr, nullptr, 0, err, cfg.stack_smem, cfg.stats_nodes);
+  SpatialArgs a = spatial_args(rec, n, queries, qperm, m, r2, err, cfg);
+  a.counts = counts;
+  spatial_launch<kCount>(a, cfg.block, s, "spatial_count");
 }
 
 void launch_spatial_fill(const float4 *rec, uint32_t n, const float *queries, const uint32_t *qperm, uint32_t m,
                          float r2, const int64_t *offsets, int32_t *indices, int64_t capacity, uint32_t *err,
-                         const TravCfg &cfg, cudaStream_t s) {
+                         const TravCfg &cfg, cudaStream_t s, const uint32_t *m_dev) {
   if (m == 0) return;
-  const size_t smem = (size_t)cfg.stack_smem * cfg.block * sizeof(int32_t);
-  prof::Scope ps(s, "spatial_fill");
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k_spatial<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_spatial<true><<<ceil_div<uint32_t>(m, cfg.block), cfg.block, smem, s>>>(
-      rec, n, queries, qperm, m, r2, nullptr, offsets, indices, capacity, err, cfg.stack_smem, cfg.stats_nodes);
+  SpatialArgs a = spatial_args(rec, n, queries, qperm, m, r2, err, cfg);
+  a.offsets = offsets;
+  a.indices = indices;
+  a.capacity = capacity;
+  a.m_dev = m_dev;
+  spatial_launch<kFill>(a, cfg.block, s, "spatial_fill");
+}
+
+void launch_spatial_buffered(const float4 *rec, uint32_t n, const float *queries, const uint32_t *qperm, uint32_t m,
+                             float r2, int32_t *counts, int32_t *buf, int bs, uint32_t *ovf_list, uint32_t *ovf_count,
+                             uint32_t *err, const TravCfg &cfg, cudaStream_t s) {
+  if (m == 0) return;
+  SpatialArgs a = spatial_args(rec, n, queries, qperm, m, r2, err, cfg);
+  a.counts = counts;
+  a.buf = buf;
+  a.bs = bs;
+  a.ovf_list = ovf_list;
+  a.ovf_count = ovf_count;
+  spatial_launch<kBuffered>(a, cfg.block, s, "spatial_buffered");
+}
+
+void launch_compact(const int32_t *buf, int bs, const int32_t *counts, const int64_t *offsets, uint32_t m,
+                    int32_t *indices, int64_t capacity, uint32_t *err, cudaStream_t s) {
+  const uint64_t slots = (uint64_t)m * bs;
+  if (slots == 0) return;
+  prof::Scope ps(s, "compact");
+  k_compact<<<(unsigned)((slots + 255) / 256), 256, 0, s>>>(buf, bs, counts, offsets, m, indices, capacity, err);
 }
 
 size_t scan_tmp_words(uint32_t m) { return (size_t)ceil_div<uint32_t>(m > 0 ? m : 1, (uint32_t)kScanTile) + 1; }

@@ -225,3 +225,46 @@ def test_lattice_closed_form_counts_and_knn27(side):
     want = np.sort(idx[interior, None] + off3[None, :], axis=1)
     assert np.array_equal(np.sort(host(kg)[interior], axis=1), want)
     assert np.array_equal(np.unique(host(dg)[interior]), np.array([0, 1, 2, 3], np.float32))
+
+
+@pytest.mark.parametrize("name", ["cube_1e4", "paper_hollow", "duplicates", "boxes"])
+@pytest.mark.parametrize("bs", [1, 4, 10, 32, 4096])
+def test_one_pass_spatial_matches_brute_force(name, bs):
+    # 1P: one traversal keeps up to bs results per query; overflowing rows are refilled by a
+    # second traversal; results equal the definition for any buffer estimate
+    ab = _ab()
+    p, q, r = CASES[name]()
+    bvh = ab.BVH(dev(p))
+    og, ig = bvh.query_spatial(dev(q), r, buffer_size=bs)
+    bvh.check()
+    oo, io = oracle.spatial_brute(p, q, r)
+    assert_spatial_equal(host(og), host(ig), oo, io)
+
+
+def test_one_pass_spatial_edge_cases():
+    ab = _ab()
+    import ctypes
+    import torch
+    p = datagen.cube(3000, 62)
+    q = np.concatenate([datagen.cube(500, 63), np.array([[np.nan, 0, 0]], np.float32)])
+    bvh = ab.BVH(dev(p))
+    for r in (0.0, 0.2, float("inf")):
+        og, ig = bvh.query_spatial(dev(q), r, buffer_size=8)
+        oo, io = oracle.spatial_brute(p, q, r)
+        assert_spatial_equal(host(og), host(ig), oo, io)
+    og, ig = bvh.query_spatial(torch.zeros((0, 3), device="cuda"), 0.1, buffer_size=8)
+    assert host(og).tolist() == [0] and ig.numel() == 0
+    L = ab.lib()
+    qd = dev(q)
+    off = torch.empty(len(q) + 1, dtype=torch.int64, device="cuda")
+    idx = torch.empty(10, dtype=torch.int32, device="cuda")
+    # a fill without its count call is refused
+    st = L.arborx_query_spatial_buffered_fill(bvh.handle, ctypes.c_void_p(qd.data_ptr()), len(q), ctypes.c_float(0.1),
+                                             None, ctypes.c_void_p(off.data_ptr()), ctypes.c_void_p(idx.data_ptr()), 10)
+    assert st == 6
+    nnz = ctypes.c_int64(0)
+    for bad in (0, 4097):
+        st = L.arborx_query_spatial_buffered_count(bvh.handle, ctypes.c_void_p(qd.data_ptr()), len(q),
+                                                   ctypes.c_float(0.1), bad, None, None,
+                                                   ctypes.c_void_p(off.data_ptr()), ctypes.byref(nnz))
+        assert st == 1
