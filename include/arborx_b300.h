@@ -269,16 +269,21 @@ ARBORX_API int arborx_mlp_grad(arborx_handle h, const float *d_params, const flo
 
 /* Train the regressor on mt training queries: labels log(max(d_k, 1e-30)) come from this tree's own
  * exact nearest traversal (k-th distance); then `epochs` passes of mini-batch Adam (beta 0.9 / 0.999,
- * eps 1e-8, learning rate lr) over batches of `batch` queries, each step one gradient kernel and
+ * eps 1e-8) over batches of `batch` queries, the learning rate following a cosine from lr at the
+ * first step to lr_final at the last (lr_final = lr: constant), each step one gradient kernel and
  * one update kernel.  d_params holds the initial parameters and receives the trained ones;
  * d_loss (NULL or device float[epochs]) receives the mean batch loss of each epoch. */
 ARBORX_API int arborx_mlp_train(arborx_handle h, const float *d_queries, int64_t mt, int32_t k, int32_t epochs,
-                                int32_t batch, float lr, void *stream, float *d_params, float *d_loss);
+                                int32_t batch, float lr, float lr_final, void *stream, float *d_params,
+                                float *d_loss);
 
 /* Nearest query seeded with a caller-supplied upper bound per query (for example the k-th distances
  * of the previous time step of a simulation): the traversal starts with d_bound2[j] as the k-th
- * squared distance of query j, and queries that find fewer than k primitives within their bound are
- * traversed again without it, so outputs equal those of arborx_query_nearest whatever the bounds.
+ * squared distance of query j; queries that find fewer than k primitives within their bound are
+ * traversed again with a bound taken from the finished rows of their neighbours in Morton order
+ * (the neighbour's k-th distance plus the distance between the two queries, which always holds k
+ * primitives), and without a bound if no neighbour provides one, so outputs equal those of
+ * arborx_query_nearest whatever the bounds.
  *   d_bound2     device float[m] (by query index; +inf = no bound)
  *   h_fallbacks  NULL, or host int64 receiving the number of second traversals (synchronises) */
 ARBORX_API int arborx_query_nearest_bounded(arborx_handle h, const float *d_queries, int64_t m, int32_t k,

@@ -84,7 +84,7 @@ def lib() -> ctypes.CDLL:
         L.arborx_query_order.argtypes = [vp, vp, i64, vp, vp]
         L.arborx_mlp_forward.argtypes = [vp, vp, vp, i64, i32, vp, vp]
         L.arborx_mlp_grad.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp]
-        L.arborx_mlp_train.argtypes = [vp, vp, i64, i32, i32, i32, ctypes.c_float, vp, vp, vp]
+        L.arborx_mlp_train.argtypes = [vp, vp, i64, i32, i32, i32, ctypes.c_float, ctypes.c_float, vp, vp, vp]
         L.arborx_query_spatial_buffered_count.argtypes = [vp, vp, i64, ctypes.c_float, i32, vp, vp, vp,
                                                           ctypes.POINTER(i64)]
         L.arborx_query_spatial_buffered_fill.argtypes = [vp, vp, i64, ctypes.c_float, vp, vp, vp, i64]
@@ -281,14 +281,15 @@ class BVH:
         return loss, grad
 
     def mlp_train(self, params: torch.Tensor, queries: torch.Tensor, k: int, epochs: int = 10, batch: int = 4096,
-                  lr: float = 1e-3) -> torch.Tensor:
+                  lr: float = 1e-3, lr_final: Optional[float] = None) -> torch.Tensor:
         """Train ``params`` (float32 [4481] CUDA tensor, updated in place); returns the loss per epoch."""
         q = _as_f32_cuda(queries, 3, "queries")
         if params.dtype != torch.float32 or params.numel() != MLP_PARAMS or not params.is_contiguous():
             raise ValueError("params must be a contiguous float32 tensor of 4481 values")
         loss = torch.empty(max(epochs, 1), dtype=torch.float32, device=q.device)
         _check(lib().arborx_mlp_train(self.handle, _ptr(q), q.shape[0], int(k), int(epochs), int(batch),
-                                      ctypes.c_float(lr), _stream(), _ptr(params), _ptr(loss)), "arborx_mlp_train")
+                                      ctypes.c_float(lr), ctypes.c_float(lr if lr_final is None else lr_final),
+                                      _stream(), _ptr(params), _ptr(loss)), "arborx_mlp_train")
         return loss[:epochs]
 
     def query_nearest_bounded(self, queries: torch.Tensor, k: int, bound2: torch.Tensor,

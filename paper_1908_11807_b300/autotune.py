@@ -1,0 +1,109 @@
+"""Autotuner for the query launch parameters.
+
+Picks, for a workload class, the traversal block size, the number of stack
+entries kept in shared memory, the row-buffer estimate of the one-pass spatial
+query (0 = two passes) and the margin of the learned bound, by timing the
+candidates with CUDA events on a sample of the caller's queries.  Choices are
+cached in JSON keyed by (log2 n bucket, k, distribution tag), in
+``$ARBORX_TUNE_CACHE`` or ``~/.cache/arborx_b300/tune.json``.
+
+Every candidate returns identical results (the launch parameters and the
+buffer estimate only change speed), so the tuner times nothing but speed.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+from typing import Dict, Iterable, Optional
+
+import torch
+
+from . import _binding as _b
+
+DEFAULT_BLOCKS = (64, 128, 256)
+DEFAULT_STACKS = (4, 8, 16)
+DEFAULT_BUFFERS = (0, 16, 24, 32)
+DEFAULT_MARGINS = (0.3, 0.5, 0.7, 1.0)
+
+
+def cache_path() -> str:
+    return os.environ.get("ARBORX_TUNE_CACHE",
+                          os.path.join(os.path.expanduser("~"), ".cache", "arborx_b300", "tune.json"))
+
+
+def cache_key(n: int, k: int, tag: str) -> str:
+    return f"n2^{int(round(math.log2(max(n, 1))))}/k{k}/{tag}"
+
+
+def _load() -> Dict[str, dict]:
+    try:
+        with open(cache_path()) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def _store(key: str, value: dict) -> None:
+    d = _load()
+    d[key] = value
+    p = cache_path()
+    os.makedirs(os.path.dirname(p), exist_ok=True)
+    tmp = p + ".tmp"
+    with open(tmp, "w") as f:
+        json.dump(d, f, indent=1, sort_keys=True)
+    os.replace(tmp, p)
+
+
+def _time(fn, reps: int = 3) -> float:
+    fn()
+    torch.cuda.synchronize()
+    best = float("inf")
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return best
+
+
+def tune(points: torch.Tensor, queries: torch.Tensor, radius: float, k: int, tag: str,
+         blocks: Iterable[int] = DEFAULT_BLOCKS, stacks: Iterable[int] = DEFAULT_STACKS,
+         buffers: Iterable[int] = DEFAULT_BUFFERS, params: Optional[torch.Tensor] = None,
+         margins: Iterable[float] = DEFAULT_MARGINS, use_cache: bool = True) -> dict:
+    """Return {"block_size", "stack_smem", "buffer_size", "margin", "ms"} for this workload
+    class, timing the candidates on (points, queries) unless the cache has them."""
+    key = cache_key(points.shape[0], k, tag)
+    if use_cache:
+        hit = _load().get(key)
+        if hit is not None:
+            return hit
+    best = None
+    for block in blocks:
+        for stack in stacks:
+            bvh = _b.BVH(points, block_size=block, stack_smem=stack)
+            order = bvh.query_order(queries)
+            ms_knn = _time(lambda: bvh.query_nearest(queries, k, order=order))
+            ms_sp = _time(lambda: bvh.query_spatial(queries, radius, order=order))
+            cand = (ms_knn + ms_sp, block, stack)
+            if best is None or cand < best:
+                best = cand
+            bvh.destroy()
+    _, block, stack = best
+    bvh = _b.BVH(points, block_size=block, stack_smem=stack)
+    order = bvh.query_order(queries)
+    buf_best = min((_time(lambda: bvh.query_spatial(queries, radius, order=order, buffer_size=bs)), bs)
+                   for bs in buffers)[1]
+    margin = None
+    if params is not None:
+        margin = min((_time(lambda: bvh.query_nearest_learned(queries, k, params, mg, order=order)), mg)
+                     for mg in margins)[1]
+    bvh.destroy()
+    out = {"block_size": block, "stack_smem": stack, "buffer_size": buf_best, "margin": margin,
+           "ms_queries": round(best[0], 4)}
+    if use_cache:
+        _store(key, out)
+    return out

@@ -135,6 +135,19 @@ TravCfg trav_cfg(const arborx_bvh_s *h, int which) {
   return c;
 }
 
+NearestArgs nearest_args(const arborx_bvh_s *h, const float *queries, const uint32_t *perm, int64_t m, int k) {
+  NearestArgs a{};
+  a.rec = h->rec;
+  a.n = (uint32_t)h->n;
+  a.queries = queries;
+  a.qperm = perm;
+  a.m = (uint32_t)m;
+  a.k = k;
+  a.bound_scale = 1.0f;
+  a.err = &h->meta->err;
+  return a;
+}
+
 bool opts_ok(const arborx_opts &o) {
   if (o.key_bits != 30 && o.key_bits != 63) return false;
   if (o.block_size != 0 && (o.block_size < 32 || o.block_size > 256 || o.block_size % 32)) return false;
@@ -500,9 +513,11 @@ int arborx_query_nearest(arborx_handle h, const float *d_queries, int64_t m, int
   const uint32_t *perm;
   st = order_queries(h, d_queries, m, s, q, &perm, d_order);
   if (st) return st;
-  if (launch_nearest(h->rec, (uint32_t)h->n, d_queries, perm, (uint32_t)m, k, d_offsets, d_indices, d_dist2, nullptr,
-                     nullptr, nullptr, &h->meta->err, trav_cfg(h, 1), s))
-    return ARBORX_EINVAL;
+  NearestArgs a = nearest_args(h, d_queries, perm, m, k);
+  a.offsets = d_offsets;
+  a.out_idx = d_indices;
+  a.out_d2 = d_dist2;
+  if (launch_nearest(a, trav_cfg(h, 1), s)) return ARBORX_EINVAL;
   h->stat_queries[1] += (uint64_t)m;
   return launch_status();
 }
@@ -595,9 +610,9 @@ int arborx_mlp_grad(arborx_handle h, const float *d_params, const float *d_queri
 }
 
 int arborx_mlp_train(arborx_handle h, const float *d_queries, int64_t mt, int32_t k, int32_t epochs, int32_t batch,
-                     float lr, void *stream, float *d_params, float *d_loss) {
+                     float lr, float lr_final, void *stream, float *d_params, float *d_loss) {
   if (!h || !d_queries || !d_params || mt < 1 || mt >= ARBORX_MAX_QUERIES || k < 1 || k > ARBORX_MAX_K ||
-      epochs < 0 || batch < 1 || batch > (1 << 20) || !(lr >= 0.f) || h->n < 1)
+      epochs < 0 || batch < 1 || batch > (1 << 20) || !(lr >= 0.f) || !(lr_final >= 0.f) || h->n < 1)
     return ARBORX_EINVAL;
   const cudaStream_t s = (cudaStream_t)stream;
   h->stream = s;
@@ -624,14 +639,18 @@ int arborx_mlp_train(arborx_handle h, const float *d_queries, int64_t mt, int32_
     cudaMemsetAsync(mom, 0, 2 * align_up((size_t)kMlpParams * sizeof(float)), s);
     if (d_loss && epochs > 0) cudaMemsetAsync(d_loss, 0, (size_t)epochs * sizeof(float), s);
     const int64_t steps = (mt + b - 1) / b;
+    const double total = (double)steps * epochs;
     const double b1 = 0.9, b2 = 0.999;
     int64_t t = 0;
     for (int e = 0; e < epochs; ++e) {
       const int64_t shift = ((int64_t)e * 7919) % mt;  // batches differ from epoch to epoch
       for (int64_t j = 0; j < steps; ++j) {
+        // cosine decay from lr (first step) to lr_final (last step)
+        const double frac = total > 1 ? (double)t / (total - 1) : 0.0;
+        const float lr_t = (float)(lr_final + (lr - lr_final) * 0.5 * (1.0 + std::cos(3.14159265358979323846 * frac)));
         ++t;
         launch_mlp_grad(d_params, d_queries, labels, mt, (shift + j * b) % mt, b, h->meta, partial, s);
-        launch_adam(d_params, mom, vel, partial, nblocks, lr, (float)b1, (float)b2, 1e-8f,
+        launch_adam(d_params, mom, vel, partial, nblocks, lr_t, (float)b1, (float)b2, 1e-8f,
                     (float)(1.0 - std::pow(b1, (double)t)), (float)(1.0 - std::pow(b2, (double)t)), nullptr,
                     d_loss ? d_loss + e : nullptr, 1.0f / (float)steps, s);
       }
@@ -644,22 +663,57 @@ int arborx_mlp_train(arborx_handle h, const float *d_queries, int64_t mt, int32_
 
 namespace {
 // Bounded nearest traversal seeded with per-query squared bounds (in `bound2`,
-// by query index; may alias the workspace), then the exact fallback pass over
-// the queries that found fewer than k primitives inside their bound.
+// by query index; may alias the workspace).  Queries that find fewer than k
+// primitives inside their bound run a second, still bounded, traversal whose
+// bound comes from the finished rows of their Morton neighbours (neighbour's
+// k-th distance plus the distance between the two queries: a guaranteed upper
+// bound); a third, unbounded pass is kept for the rare query whose neighbours
+// give no usable bound.
 int nearest_bounded(arborx_handle h, const float *d_queries, int64_t m, int32_t k, const float *bound2,
                     const uint32_t *perm, QueryWs &q, cudaStream_t s, int64_t *d_offsets, int32_t *d_indices,
                     float *d_dist2, int64_t *h_fallbacks) {
   uint32_t *miss = q.miss;
   uint32_t *miss_count = q.miss + m;
-  cudaMemsetAsync(miss_count, 0, sizeof(uint32_t), s);
-  TravCfg cfg = trav_cfg(h, 1);
-  if (launch_nearest(h->rec, (uint32_t)h->n, d_queries, perm, (uint32_t)m, k, d_offsets, d_indices, d_dist2, bound2,
-                     miss, miss_count, &h->meta->err, cfg, s))
-    return ARBORX_EINVAL;
-  launch_nearest(h->rec, (uint32_t)h->n, d_queries, miss, (uint32_t)m, k, nullptr, d_indices, d_dist2, nullptr,
-                 nullptr, nullptr, &h->meta->err, cfg, s, miss_count);
-  h->stat_queries[1] += (uint64_t)m;
-  int st = launch_status();
+  uint32_t *miss2 = perm == q.pB ? q.pA : q.pB;  // free once the order exists
+  uint32_t *miss2_count = q.miss + m + 1;
+  const int64_t kk = k < h->n ? k : h->n;
+  // the neighbour bound reads finished squared distances: keep them even if the caller does not
+  float *d2 = d_dist2;
+  const size_t d2_bytes = (size_t)m * kk * sizeof(float);
+  if (!d2) {
+    d2 = (float *)dev_alloc(h->opts, d2_bytes, s);
+    if (!d2) return ARBORX_ENOMEM;
+  }
+  cudaMemsetAsync(miss_count, 0, 2 * sizeof(uint32_t), s);
+  const TravCfg cfg = trav_cfg(h, 1);
+  NearestArgs a = nearest_args(h, d_queries, perm, m, k);
+  a.offsets = d_offsets;
+  a.out_idx = d_indices;
+  a.out_d2 = d2;
+  a.init_bound2 = bound2;
+  a.miss_list = miss;
+  a.miss_count = miss_count;
+  int st = launch_nearest(a, cfg, s) ? ARBORX_EINVAL : ARBORX_OK;
+  if (st == ARBORX_OK) {
+    NearestArgs b = nearest_args(h, d_queries, perm, m, k);
+    b.out_idx = d_indices;
+    b.out_d2 = d2;
+    b.pos_list = miss;
+    b.m_dev = miss_count;
+    b.nbr_bound = 1;
+    b.miss_list = miss2;
+    b.miss_count = miss2_count;
+    launch_nearest(b, cfg, s);
+    NearestArgs c = nearest_args(h, d_queries, perm, m, k);
+    c.out_idx = d_indices;
+    c.out_d2 = d2;
+    c.pos_list = miss2;
+    c.m_dev = miss2_count;
+    launch_nearest(c, cfg, s);
+    h->stat_queries[1] += (uint64_t)m;
+    st = launch_status();
+  }
+  if (d2 != d_dist2) dev_free(h->opts, d2, d2_bytes, s);
   if (st == ARBORX_OK && h_fallbacks) {
     uint32_t cnt = 0;
     if (cudaMemcpyAsync(&cnt, miss_count, sizeof cnt, cudaMemcpyDeviceToHost, s) != cudaSuccess ||

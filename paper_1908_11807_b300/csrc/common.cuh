@@ -81,6 +81,7 @@ __device__ __forceinline__ uint32_t atom_add_acq_rel_gpu(uint32_t *p, uint32_t v
 }
 // L1-bypassing vector load (data written by another block of the same kernel)
 __device__ __forceinline__ float4 ld_cg_f4(const float4 *p) { return __ldcg(p); }
+__device__ __forceinline__ float ld_cg_f32(const float *p) { return __ldcg(p); }
 
 __device__ __forceinline__ void set_err(uint32_t *err, uint32_t bit) {
   if (err) atomicOr(err, bit);

@@ -67,13 +67,29 @@ size_t scan_tmp_words(uint32_t m);
 void launch_scan(const int32_t *counts, uint32_t m, int64_t *offsets, int64_t *tmp, cudaStream_t s);
 
 // nearest: rows of kk = min(k, n) (index, d2) in (d2, index) order.
-// init_bound2 (nullable, by original query index): initial k-th bound; rows that
-// end with fewer than kk real hits are appended to miss_list (if non-null).
-// m_dev (nullable): device word holding the number of queries to process (<= m).
-int launch_nearest(const float4 *rec, uint32_t n, const float *queries, const uint32_t *qperm, uint32_t m, int k,
-                   int64_t *offsets, int32_t *out_idx, float *out_d2, const float *init_bound2,
-                   uint32_t *miss_list, uint32_t *miss_count, uint32_t *err, const TravCfg &cfg, cudaStream_t s,
-                   const uint32_t *m_dev = nullptr);
+struct NearestArgs {
+  const float4 *rec;
+  uint32_t n;
+  const float *queries;
+  const uint32_t *qperm;     // sorted position -> query index (nullable: identity)
+  const uint32_t *pos_list;  // nullable: thread -> sorted position (second passes)
+  uint32_t m;                // number of queries (sorted positions 0..m-1)
+  const uint32_t *m_dev;     // nullable: number of threads to run, produced on the device
+  int k;
+  int kk;                    // set by launch_nearest
+  int64_t *offsets;          // nullable: offsets[t] = t * kk
+  int32_t *out_idx;
+  float *out_d2;             // nullable unless nbr_bound
+  const float *init_bound2;  // nullable: initial k-th squared distance by query index, times bound_scale
+  float bound_scale;
+  int nbr_bound;             // also bound by the finished rows of the sorted neighbours (needs out_d2)
+  uint32_t *miss_list;       // nullable: sorted positions of queries with fewer than k hits in their bound
+  uint32_t *miss_count;
+  uint32_t *err;
+  int stack_smem;            // set by launch_nearest
+  unsigned long long *stats; // set by launch_nearest
+};
+int launch_nearest(NearestArgs a, const TravCfg &cfg, cudaStream_t s);
 
 // ---- learned k-th-distance regressor (mlp.cu)
 constexpr int kMlpParams = 4481;  // W1 64x3, b1 64, W2 64x64, b2 64, w3 64, b3 1

@@ -46,7 +46,7 @@ __device__ __forceinline__ void block_excl_scan2(uint32_t a, uint32_t b, uint32_
 }
 
 template <typename K, bool FIRST>
-__global__ void __launch_bounds__(kSortThreads) k_onesweep(const K *__restrict__ kin, const uint32_t *__restrict__ vin,
+__global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(const K *__restrict__ kin, const uint32_t *__restrict__ vin,
                                                           K *__restrict__ kout, uint32_t *__restrict__ vout,
                                                           uint32_t n, int shift, const uint32_t *__restrict__ hist,
                                                           uint32_t *__restrict__ status,
@@ -84,18 +84,22 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(const K *__restrict__
     }
   }
 
-  // warp-level ranking in input order (item-major, lane-minor)
-  const uint32_t lt = lanemask_lt(), gt = lanemask_gt();
+  // warp-level ranking in input order (item-major, lane-minor): the lowest lane
+  // of each group of equal digits adds the group size to the warp's counter
+  // and hands the previous count to its peers; the warp's shared-memory
+  // atomics execute in program order, so item i is counted before item i + 1
+  const uint32_t lt = lanemask_lt();
 #pragma unroll
   for (int i = 0; i < ITEMS; ++i) {
     const uint32_t pos = wbase + i * 32 + lane;
-    const uint32_t d = pos < n ? (uint32_t)(k[i] >> shift) & (kRadix - 1) : (uint32_t)kRadix;
+    const bool valid = pos < n;
+    const uint32_t d = valid ? (uint32_t)(k[i] >> shift) & (kRadix - 1) : (uint32_t)kRadix;
     const uint32_t peers = __match_any_sync(0xffffffffu, d);
-    const uint32_t prev = d < (uint32_t)kRadix ? s_whist[warp][d] : 0u;
-    rk[i] = prev + __popc(peers & lt);
-    __syncwarp();
-    if (d < (uint32_t)kRadix && (peers & gt) == 0) s_whist[warp][d] = prev + __popc(peers);
-    __syncwarp();
+    const int leader = __ffs(peers) - 1;
+    uint32_t old = 0;
+    if (valid && (int)lane == leader) old = atomicAdd(&s_whist[warp][d], (uint32_t)__popc(peers));
+    old = __shfl_sync(0xffffffffu, old, leader);
+    rk[i] = old + __popc(peers & lt);
   }
   __syncthreads();
 

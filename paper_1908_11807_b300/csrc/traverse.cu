@@ -342,38 +342,55 @@ __device__ __forceinline__ void knn_traverse(const float4 *__restrict__ rec, uin
   }
 }
 
-// Threads t <= m also write offsets[t] = t * kk (CSR view of the rows).
+// Upper bound on the k-th squared distance of query q taken from a finished row
+// of its Morton neighbour q': the neighbour's k primitives lie within
+// d_k(q') + |q - q'| of q (triangle inequality).  Inflated by 2^-10 relative
+// to cover FP32 rounding; +inf when the neighbour's row is not finished.
+__device__ __forceinline__ float neighbour_bound2(const NearestArgs &a, uint32_t pos_n, float qx, float qy, float qz) {
+  const uint32_t qn = a.qperm ? __ldg(a.qperm + pos_n) : pos_n;
+  const float d2n = ld_cg_f32(a.out_d2 + (int64_t)qn * a.kk + a.kk - 1);  // written by other blocks
+  if (!(d2n < __int_as_float(0x7f800000))) return __int_as_float(0x7f800000);
+  const float dx = __fsub_rn(qx, __ldg(a.queries + 3 * (uint64_t)qn));
+  const float dy = __fsub_rn(qy, __ldg(a.queries + 3 * (uint64_t)qn + 1));
+  const float dz = __fsub_rn(qz, __ldg(a.queries + 3 * (uint64_t)qn + 2));
+  const float e = sqrtf(dx * dx + dy * dy + dz * dz);
+  const float b = (sqrtf(d2n) + e) * (1.0f + 0x1p-10f);
+  return b * b;  // NaN for a non-finite neighbour: ignored by fminf
+}
+
+// Threads t <= m also write offsets[t] = t * kk (CSR view of the rows).  Thread
+// t serves sorted position pos = pos_list ? pos_list[t] : t, query qperm[pos].
 template <int KC>
-__global__ void __launch_bounds__(kMaxBlock) k_nearest(const float4 *__restrict__ rec, uint32_t n,
-                                                 const float *__restrict__ queries, const uint32_t *__restrict__ qperm,
-                                                 uint32_t m, int k, int kk, int64_t *__restrict__ offsets,
-                                                 int32_t *__restrict__ out_idx, float *__restrict__ out_d2,
-                                                 const float *__restrict__ init_bound2, uint32_t *__restrict__ miss_list,
-                                                 uint32_t *__restrict__ miss_count, uint32_t *__restrict__ err,
-                                                 int stack_smem, unsigned long long *__restrict__ stats,
-                                                 const uint32_t *__restrict__ m_dev) {
+__global__ void __launch_bounds__(kMaxBlock) k_nearest(const NearestArgs a) {
   extern __shared__ unsigned char s_raw[];
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (offsets && t <= m) offsets[t] = (int64_t)t * kk;
-  if (m_dev) m = min(m, *m_dev);  // query count produced on the device (fallback pass)
+  const int kk = a.kk, k = a.k, stack_smem = a.stack_smem;
+  if (a.offsets && t <= a.m) a.offsets[t] = (int64_t)t * kk;
+  const uint32_t m = a.m_dev ? min(a.m, *a.m_dev) : a.m;  // count produced on the device (fallback passes)
   if (t >= m) return;
   const int B = blockDim.x;
   int32_t *s_node = reinterpret_cast<int32_t *>(s_raw) + threadIdx.x;
   float *s_dist = reinterpret_cast<float *>(s_raw) + (size_t)stack_smem * B + threadIdx.x;
-  const uint32_t qi = qperm ? __ldg(qperm + t) : t;
-  const float qx = __ldg(queries + 3 * (uint64_t)qi);
-  const float qy = __ldg(queries + 3 * (uint64_t)qi + 1);
-  const float qz = __ldg(queries + 3 * (uint64_t)qi + 2);
-  const float b0 = init_bound2 ? __ldg(init_bound2 + qi) : __int_as_float(0x7f800000);
+  const uint32_t pos = a.pos_list ? __ldg(a.pos_list + t) : t;
+  const uint32_t qi = a.qperm ? __ldg(a.qperm + pos) : pos;
+  const float qx = __ldg(a.queries + 3 * (uint64_t)qi);
+  const float qy = __ldg(a.queries + 3 * (uint64_t)qi + 1);
+  const float qz = __ldg(a.queries + 3 * (uint64_t)qi + 2);
+  float b0 = a.init_bound2 ? __ldg(a.init_bound2 + qi) * a.bound_scale : __int_as_float(0x7f800000);
+  if (a.nbr_bound) {
+    if (pos > 0) b0 = fminf(b0, neighbour_bound2(a, pos - 1, qx, qy, qz));
+    if (pos + 1 < a.m) b0 = fminf(b0, neighbour_bound2(a, pos + 1, qx, qy, qz));
+  }
   const bool ok = finite3(qx, qy, qz);
   const int64_t row = (int64_t)qi * kk;
+  const uint32_t n = a.n;
   uint32_t visited = 0;
   if constexpr (KC > 0) {
     RegList<KC> L;
     L.init(b0, k);
-    if (ok && n > 0) knn_traverse(rec, n, qx, qy, qz, L, k, s_node, s_dist, B, stack_smem, err, visited);
-    if (miss_list) append_flagged(ok && L.bound_idx() == INT_MAX, qi, miss_list, miss_count);
-    L.write(row, kk, out_idx, out_d2);
+    if (ok && n > 0) knn_traverse(a.rec, n, qx, qy, qz, L, k, s_node, s_dist, B, stack_smem, a.err, visited);
+    if (a.miss_list) append_flagged(ok && L.bound_idx() == INT_MAX, pos, a.miss_list, a.miss_count);
+    L.write(row, kk, a.out_idx, a.out_d2);
   } else {
     SmemHeap H;
     H.hd = reinterpret_cast<float *>(s_raw) + (size_t)2 * stack_smem * B + threadIdx.x;
@@ -381,11 +398,11 @@ __global__ void __launch_bounds__(kMaxBlock) k_nearest(const float4 *__restrict_
     H.s = B;
     H.k = k;
     H.init(b0, k);
-    if (ok && n > 0) knn_traverse(rec, n, qx, qy, qz, H, k, s_node, s_dist, B, stack_smem, err, visited);
-    if (miss_list) append_flagged(ok && H.bound_idx() == INT_MAX, qi, miss_list, miss_count);
-    H.write(row, kk, out_idx, out_d2);
+    if (ok && n > 0) knn_traverse(a.rec, n, qx, qy, qz, H, k, s_node, s_dist, B, stack_smem, a.err, visited);
+    if (a.miss_list) append_flagged(ok && H.bound_idx() == INT_MAX, pos, a.miss_list, a.miss_count);
+    H.write(row, kk, a.out_idx, a.out_d2);
   }
-  if (stats) atomicAdd(stats, (unsigned long long)visited);
+  if (a.stats) atomicAdd(a.stats, (unsigned long long)visited);
 }
 
 // ------------------------------------------------------------------- scan
@@ -556,22 +573,18 @@ void launch_scan(const int32_t *counts, uint32_t m, int64_t *offsets, int64_t *t
 }
 
 template <int KC>
-static void nearest_kc(dim3 grid, int block, size_t smem, cudaStream_t s, const float4 *rec, uint32_t n,
-                       const float *queries, const uint32_t *qperm, uint32_t m, int k, int kk, int64_t *offsets,
-                       int32_t *out_idx, float *out_d2, const float *init_bound2, uint32_t *miss_list,
-                       uint32_t *miss_count, uint32_t *err, int stack_smem, unsigned long long *stats,
-                       const uint32_t *m_dev) {
+static void nearest_kc(dim3 grid, int block, size_t smem, cudaStream_t s, const NearestArgs &a) {
   prof::Scope ps(s, "nearest");
   if (smem > 48 * 1024) cudaFuncSetAttribute(k_nearest<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_nearest<KC><<<grid, block, smem, s>>>(rec, n, queries, qperm, m, k, kk, offsets, out_idx, out_d2, init_bound2,
-                                          miss_list, miss_count, err, stack_smem, stats, m_dev);
+  k_nearest<KC><<<grid, block, smem, s>>>(a);
 }
 
-int launch_nearest(const float4 *rec, uint32_t n, const float *queries, const uint32_t *qperm, uint32_t m, int k,
-                   int64_t *offsets, int32_t *out_idx, float *out_d2, const float *init_bound2, uint32_t *miss_list,
-                   uint32_t *miss_count, uint32_t *err, const TravCfg &cfg, cudaStream_t s, const uint32_t *m_dev) {
-  const int kk = (int)std::min<int64_t>(k, n);
-  const uint32_t threads = m + 1;
+int launch_nearest(NearestArgs a, const TravCfg &cfg, cudaStream_t s) {
+  a.kk = (int)std::min<int64_t>(a.k, a.n);
+  a.stack_smem = cfg.stack_smem;
+  a.stats = cfg.stats_nodes;
+  const int k = a.k;
+  const uint32_t threads = a.m + 1;
   int block = cfg.block;
   size_t smem = (size_t)2 * cfg.stack_smem * block * sizeof(int32_t);
   if (k > 32) {
@@ -584,18 +597,14 @@ int launch_nearest(const float4 *rec, uint32_t n, const float *queries, const ui
     if (smem > 227 * 1024) return -1;
   }
   const dim3 grid(ceil_div<uint32_t>(threads, (uint32_t)block));
-#define ABX_NEAREST(KC)                                                                                           \
-  nearest_kc<KC>(grid, block, smem, s, rec, n, queries, qperm, m, k, kk, offsets, out_idx, out_d2, init_bound2, \
-                 miss_list, miss_count, err, cfg.stack_smem, cfg.stats_nodes, m_dev)
-  if (k <= 1) ABX_NEAREST(1);
-  else if (k <= 2) ABX_NEAREST(2);
-  else if (k <= 4) ABX_NEAREST(4);
-  else if (k <= 8) ABX_NEAREST(8);
-  else if (k <= 10) ABX_NEAREST(10);
-  else if (k <= 16) ABX_NEAREST(16);
-  else if (k <= 32) ABX_NEAREST(32);
-  else ABX_NEAREST(0);
-#undef ABX_NEAREST
+  if (k <= 1) nearest_kc<1>(grid, block, smem, s, a);
+  else if (k <= 2) nearest_kc<2>(grid, block, smem, s, a);
+  else if (k <= 4) nearest_kc<4>(grid, block, smem, s, a);
+  else if (k <= 8) nearest_kc<8>(grid, block, smem, s, a);
+  else if (k <= 10) nearest_kc<10>(grid, block, smem, s, a);
+  else if (k <= 16) nearest_kc<16>(grid, block, smem, s, a);
+  else if (k <= 32) nearest_kc<32>(grid, block, smem, s, a);
+  else nearest_kc<0>(grid, block, smem, s, a);
   return 0;
 }
 
