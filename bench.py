@@ -150,6 +150,8 @@ def kernel_bytes(name, n, m, k, nnz, nodes):
         "scan": 12 * m + 8,                         # counts read twice, offsets written
         "spatial_count": 20 * m + 64 * nodes.get("spatial", 0) // 2,
         "spatial_fill": 28 * m + 4 * nnz + 64 * nodes.get("spatial", 0) // 2,
+        "spatial_buffered": 20 * m + 4 * nnz + 64 * nodes.get("spatial", 0),  # one pass, rows to the buffer
+        "compact": 8 * nnz + 12 * m,                                           # buffer -> CSR
         "nearest": m * (16 + 8 * k + 8) + 64 * nodes.get("nearest", 0),
     }
     return table.get(name)
@@ -177,13 +179,23 @@ def run_gpu(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
+    # launch parameters from the autotuner, tuned on another draw of the same distribution
+    tuned = {"block_size": 0, "stack_smem": 0, "buffer_size": 0}
+    if not args.no_tune:
+        from paper_1908_11807_b300 import autotune
+        tp, tq = datagen.workload(dist_name, n, min(m, 200_000), seed + 1000)
+        tuned = autotune.tune(torch.from_numpy(tp).to(dev), torch.from_numpy(tq).to(dev), r, k, dist_name)
+        del tp, tq
+    topts = {"block_size": tuned["block_size"], "stack_smem": tuned["stack_smem"]}
+    bsz = int(tuned["buffer_size"] or 0)
+
     def step(points, queries, **opts):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         ev[0].record(stream)
-        bvh = ab.BVH(points, **opts)
+        bvh = ab.BVH(points, **topts, **opts)
         ev[1].record(stream)
         order = bvh.query_order(queries)
-        off, idx = bvh.query_spatial(queries, r, order=order)
+        off, idx = bvh.query_spatial(queries, r, order=order, buffer_size=bsz)
         ev[2].record(stream)
         kidx, kd2 = bvh.query_nearest(queries, k, order=order)
         ev[3].record(stream)
@@ -320,6 +332,7 @@ def run_gpu(args):
                        "build_ms": round(build_ms, 4), "radius_ms": round(spatial_ms, 4),
                        "knn_ms": round(knn_ms, 4), "nnz": nnz},
         "kernels": kernels,
+        "tuned": tuned,
         "traversal": {"spatial_nodes_per_query_per_pass": round(nodes["spatial"] / (2 * m), 2),
                       "nearest_nodes_per_query": round(nodes["nearest"] / m, 2), "node_bytes": 64},
         "roofline": roofline,
@@ -327,12 +340,106 @@ def run_gpu(args):
         "gpu_launches": launches,
         "clocks": clocks,
     }
+    if rank == 0 and not args.no_extras:
+        line["learned"] = learned_extra(ab, dev)
+        line["batched"] = batched_extra(ab, dev)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, p_h, q_h, r, k, n, m, budget_s=args.cpu_budget)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+def _time_ms(fn, reps=3):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    best = float("inf")
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return best
+
+
+def learned_extra(ab, dev):
+    """Learned initial bound vs plain nearest traversal: 1e7 points and 1e7 queries from a
+    64-Gaussian mixture, regressor trained on 1e6 exact labels by the library's kernels."""
+    import torch
+    from paper_1908_11807_b300 import autotune
+    n, m, mt = 10_000_000, 10_000_000, 1_000_000
+    seed = datagen.SEED0 + 5
+    p = torch.from_numpy(datagen.gaussian_mixture(n, seed)).to(dev)
+    q = torch.from_numpy(datagen.gaussian_mixture(m, seed, datagen.STREAM_QUERIES)).to(dev)
+    qt = torch.from_numpy(datagen.gaussian_mixture(mt, seed, datagen.STREAM_TRAIN)).to(dev)
+    out = {"workload": "gaussian mixture (64 components), n=1e7 points, m=1e7 queries, 1e6 training labels",
+           "unit": "ms per query batch"}
+    bvh = ab.BVH(p)
+    order = bvh.query_order(q)
+    for k in (10, 50):
+        g = np.random.default_rng(seed)
+        init = np.concatenate([g.standard_normal(192) * np.sqrt(2 / 3), np.zeros(64),
+                               g.standard_normal(4096) * np.sqrt(2 / 64), np.zeros(64),
+                               g.standard_normal(64) * np.sqrt(1 / 64), np.zeros(1)]).astype(np.float32)
+        params = torch.from_numpy(init).to(dev)
+        t0 = time.perf_counter()
+        loss = bvh.mlp_train(params, qt, k, epochs=60, batch=1024, lr=3e-3, lr_final=3e-5)
+        torch.cuda.synchronize()
+        train_s = time.perf_counter() - t0
+        sub = q[:1_000_000]
+        margin = autotune.tune_margin(bvh, sub, k, params)
+        plain_ms = _time_ms(lambda: bvh.query_nearest(q, k, order=order))
+        learned_ms = _time_ms(lambda: bvh.query_nearest_learned(q, k, params, margin, order=order))
+        pi, pd = bvh.query_nearest(q, k, order=order)
+        li, ld, fb = bvh.query_nearest_learned(q, k, params, margin, order=order, count_fallbacks=True)
+        same = bool(torch.equal(pi, li) and torch.equal(pd, ld))
+        out[f"k{k}"] = {"plain_ms": round(plain_ms, 3), "learned_ms": round(learned_ms, 3),
+                        "speedup": round(plain_ms / learned_ms, 3), "identical_results": same,
+                        "plain_mq_s": round(m / plain_ms / 1e3, 1), "learned_mq_s": round(m / learned_ms / 1e3, 1),
+                        "margin": margin, "fallback_fraction": round(fb / m, 4),
+                        "train_s": round(train_s, 2), "final_loss": round(float(loss[-1].item()), 4)}
+        del pi, pd, li, ld
+    bvh.destroy()
+    return out
+
+
+def batched_extra(ab, dev):
+    """512 independent clouds (sizes log-uniform in [1e3, 1e5], cube or hollow sphere, k in
+    {1, 10, 32}): one graph-replayed batch vs a per-cloud build + query loop."""
+    import torch
+    w = datagen.batched_workload(512, datagen.SEED0 + 4)
+    pts = [c["points"] for c in w]
+    qs = [c["queries"] for c in w]
+    ks = np.array([c["k"] for c in w], np.int32)
+    po = np.concatenate([[0], np.cumsum([len(x) for x in pts])]).astype(np.int64)
+    qo = np.concatenate([[0], np.cumsum([len(x) for x in qs])]).astype(np.int64)
+    P = torch.from_numpy(np.concatenate(pts)).to(dev)
+    Q = torch.from_numpy(np.concatenate(qs)).to(dev)
+    b = ab.Batch(po, qo, ks)
+    out_bufs = b.run(P, Q, use_graph=True)
+    graph_ms = _time_ms(lambda: b.run(P, Q, use_graph=True, out=(out_bufs[0], out_bufs[1], out_bufs[2])), reps=5)
+    eager_ms = _time_ms(lambda: b.run(P, Q, use_graph=False), reps=3)
+    b.check()
+    pd = [P[po[c]:po[c + 1]] for c in range(512)]
+    qd = [Q[qo[c]:qo[c + 1]] for c in range(512)]
+
+    def loop():
+        for c in range(512):
+            t = ab.BVH(pd[c], validate=0)
+            t.query_nearest(qd[c], int(ks[c]))
+            t.destroy()
+    loop_ms = _time_ms(loop, reps=2)
+    mtot = int(qo[-1])
+    b.destroy()
+    return {"workload": f"512 clouds, {int(po[-1])} points, {mtot} queries, k in {{1,10,32}}",
+            "graph_ms": round(graph_ms, 3), "eager_batch_ms": round(eager_ms, 3), "per_cloud_loop_ms": round(loop_ms, 3),
+            "graph_mq_s": round(mtot / graph_ms / 1e3, 1), "loop_mq_s": round(mtot / loop_ms / 1e3, 1),
+            "speedup_vs_loop": round(loop_ms / graph_ms, 2)}
 
 
 # ---------------------------------------------------------------- CPU oracle arm
@@ -410,6 +517,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the learned-bound and batched measurements")
+    ap.add_argument("--no-tune", action="store_true", help="default launch parameters instead of the autotuner's")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "b300":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

@@ -300,6 +300,40 @@ ARBORX_API int arborx_query_nearest_learned(arborx_handle h, const float *d_quer
                                             void *stream, int64_t *d_offsets, int32_t *d_indices, float *d_dist2,
                                             int64_t *h_fallbacks);
 
+/* ---------------------------------------------------------------------------------------------
+ * Many independent point clouds at once: every cloud gets its own tree (the LBVH of Sec. 2.1 over its
+ * points) and every query its k nearest points of its own cloud (Sec. 2.2), for all clouds in one
+ * launch sequence of about twenty kernels instead of a build and a query per cloud.  The paper has
+ * no batched interface; results equal those of arborx_build + arborx_query_nearest per cloud. */
+typedef struct arborx_batch_s *arborx_batch;
+
+/* Plan a batch of n_clouds clouds (host arrays, copied): cloud c owns points
+ * [h_point_offsets[c], h_point_offsets[c+1]) of the concatenated point array (float[N][3]) and
+ * queries [h_query_offsets[c], h_query_offsets[c+1]) of the concatenated query array, and wants
+ * its k_c = h_k[c] nearest points (1 <= k_c <= 32).  Offsets start at 0 and do not decrease.
+ * Allocates every device buffer the runs need (so runs allocate nothing) and synchronises once.
+ * opts: block_size, stack_smem and the allocator are used; NULL for defaults. */
+ARBORX_API int arborx_batch_create(int64_t n_clouds, const int64_t *h_point_offsets, const int64_t *h_query_offsets,
+                                   const int32_t *h_k, const arborx_opts *opts, void *stream, arborx_batch *out);
+
+/* Totals of a batch: points, queries, and output entries (sum over queries of min(k_c, n_c)). */
+ARBORX_API int arborx_batch_entries(arborx_batch b, int64_t *n_points, int64_t *n_queries, int64_t *entries);
+
+/* Build all clouds and answer all queries.  Row j (query j of the concatenation) is written at
+ * d_row_offsets[j] (int64[M+1], NULL to skip) with min(k_c, n_c) point indices local to the
+ * query's cloud in (d^2, index) order, -1 for a non-finite query; d_dist2 (NULL or float[entries])
+ * gets the squared distances.  use_graph = 1: the launch sequence is captured in a CUDA graph on
+ * the first call and replayed while the five pointers stay the same.  Does not synchronise;
+ * arborx_batch_check reports device errors of the last run. */
+ARBORX_API int arborx_batch_run(arborx_batch b, const float *d_points, const float *d_queries, int32_t use_graph,
+                                void *stream, int64_t *d_row_offsets, int32_t *d_indices, float *d_dist2);
+
+/* Synchronise `stream` and report device errors of the last run (non-finite input: EINVAL). */
+ARBORX_API int arborx_batch_check(arborx_batch b, void *stream);
+
+/* Release the batch (stream-ordered on the creation stream).  NULL is a no-op. */
+ARBORX_API int arborx_batch_destroy(arborx_batch b);
+
 /* Traversal statistics of a tree built with opts.stats = 1 (synchronises `stream`): out[0], out[1] =
  * internal nodes loaded by spatial and nearest traversals, out[2], out[3] = queries traversed,
  * since the previous call; resets them. */

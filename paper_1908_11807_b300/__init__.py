@@ -13,6 +13,7 @@ from ._binding import (  # noqa: F401
     ArborXError,
     MLP_PARAMS,
     BVH,
+    Batch,
     arborx_build,
     arborx_query_nearest,
     arborx_query_spatial,

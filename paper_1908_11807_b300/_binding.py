@@ -88,6 +88,11 @@ def lib() -> ctypes.CDLL:
         L.arborx_query_spatial_buffered_count.argtypes = [vp, vp, i64, ctypes.c_float, i32, vp, vp, vp,
                                                           ctypes.POINTER(i64)]
         L.arborx_query_spatial_buffered_fill.argtypes = [vp, vp, i64, ctypes.c_float, vp, vp, vp, i64]
+        L.arborx_batch_create.argtypes = [i64, vp, vp, vp, ctypes.POINTER(arborx_opts), vp, ctypes.POINTER(vp)]
+        L.arborx_batch_entries.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]
+        L.arborx_batch_run.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp]
+        L.arborx_batch_check.argtypes = [vp, vp]
+        L.arborx_batch_destroy.argtypes = [vp]
         L.arborx_query_nearest_bounded.argtypes = [vp, vp, i64, i32, vp, vp, vp, vp, vp, vp,
                                                    ctypes.POINTER(i64)]
         L.arborx_query_nearest_learned.argtypes = [vp, vp, i64, i32, vp, ctypes.c_float, vp, vp, vp, vp, vp,
@@ -388,3 +393,58 @@ def profile_report() -> dict:
 def release_cached_memory() -> None:
     """Return the library's pooled device memory to the driver."""
     _check(lib().arborx_release_cached_memory(), "arborx_release_cached_memory")
+
+
+class Batch:
+    """Many point clouds built and queried together (wraps an ``arborx_batch``).
+
+    point_offsets / query_offsets: int64 [C+1] host sequences; ks: per-cloud k (1..32)."""
+
+    def __init__(self, point_offsets, query_offsets, ks, **opts):
+        import numpy as np
+        self.point_offsets = np.ascontiguousarray(point_offsets, dtype=np.int64)
+        self.query_offsets = np.ascontiguousarray(query_offsets, dtype=np.int64)
+        self.ks = np.ascontiguousarray(ks, dtype=np.int32)
+        c = len(self.ks)
+        if self.point_offsets.shape != (c + 1,) or self.query_offsets.shape != (c + 1,):
+            raise ValueError("offsets must have n_clouds + 1 entries")
+        self.opts = default_opts(**opts)
+        h = ctypes.c_void_p()
+        _check(lib().arborx_batch_create(c, self.point_offsets.ctypes.data_as(ctypes.c_void_p),
+                                         self.query_offsets.ctypes.data_as(ctypes.c_void_p),
+                                         self.ks.ctypes.data_as(ctypes.c_void_p), ctypes.byref(self.opts),
+                                         _stream(), ctypes.byref(h)), "arborx_batch_create")
+        self._h = h
+        n, m, e = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().arborx_batch_entries(h, ctypes.byref(n), ctypes.byref(m), ctypes.byref(e)), "arborx_batch_entries")
+        self.n_points, self.n_queries, self.entries = n.value, m.value, e.value
+
+    def run(self, points: torch.Tensor, queries: torch.Tensor, use_graph: bool = True, out=None,
+            return_dist2: bool = True):
+        """(row_offsets int64 [M+1], indices int32 [entries] local to each cloud, dist2 float32 [entries])."""
+        p = _as_f32_cuda(points, 3, "points")
+        q = _as_f32_cuda(queries, 3, "queries")
+        if p.shape[0] != self.n_points or q.shape[0] != self.n_queries:
+            raise ValueError("points / queries do not match the planned offsets")
+        if out is None:
+            out = (torch.empty(self.n_queries + 1, dtype=torch.int64, device=p.device),
+                   torch.empty(max(self.entries, 1), dtype=torch.int32, device=p.device),
+                   torch.empty(max(self.entries, 1), dtype=torch.float32, device=p.device) if return_dist2 else None)
+        off, idx, d2 = out
+        _check(lib().arborx_batch_run(self._h, _ptr(p), _ptr(q), int(bool(use_graph)), _stream(), _ptr(off),
+                                      _ptr(idx), _ptr(d2)), "arborx_batch_run")
+        return off, idx[: self.entries], (d2[: self.entries] if d2 is not None else None)
+
+    def check(self) -> None:
+        _check(lib().arborx_batch_check(self._h, _stream()), "arborx_batch_check")
+
+    def destroy(self) -> None:
+        if getattr(self, "_h", None) is not None:
+            lib().arborx_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass

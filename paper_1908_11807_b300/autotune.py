@@ -24,7 +24,7 @@ from . import _binding as _b
 DEFAULT_BLOCKS = (64, 128, 256)
 DEFAULT_STACKS = (4, 8, 16)
 DEFAULT_BUFFERS = (0, 16, 24, 32)
-DEFAULT_MARGINS = (0.3, 0.5, 0.7, 1.0)
+DEFAULT_MARGINS = (0.2, 0.35, 0.5, 0.7)
 
 
 def cache_path() -> str:
@@ -107,3 +107,11 @@ def tune(points: torch.Tensor, queries: torch.Tensor, radius: float, k: int, tag
     if use_cache:
         _store(key, out)
     return out
+
+
+def tune_margin(bvh, queries: torch.Tensor, k: int, params: torch.Tensor,
+                margins: Iterable[float] = DEFAULT_MARGINS) -> float:
+    """Margin of the learned bound with the fastest nearest query on ``queries``."""
+    order = bvh.query_order(queries)
+    return min((_time(lambda: bvh.query_nearest_learned(queries, k, params, mg, order=order)), mg)
+               for mg in margins)[1]

@@ -380,6 +380,168 @@ __global__ void __launch_bounds__(256) k_apetrei(const float *__restrict__ prims
   }
 }
 
+// ------------------------------------------------------ batched clouds
+// Cloud c of a batch owns points [off[c], off[c+1]) of the concatenation.
+
+__device__ __forceinline__ uint32_t cloud_of(const uint32_t *__restrict__ off, uint32_t n_clouds, uint32_t i) {
+  uint32_t lo = 0, hi = n_clouds;  // largest c with off[c] <= i
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (__ldg(off + mid) <= i) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Scene box of each cloud: one block per cloud.
+__global__ void __launch_bounds__(256) k_seg_bounds(const float *__restrict__ pts, const uint32_t *__restrict__ off,
+                                                   float *__restrict__ seg_scene, uint32_t *__restrict__ err) {
+  const uint32_t c = blockIdx.x;
+  const uint32_t b = off[c], e = off[c + 1];
+  float mn[3], mx[3];
+  uint32_t bad = 0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    mn[a] = __int_as_float(0x7f800000);
+    mx[a] = __int_as_float(0xff800000);
+  }
+  for (uint32_t i = b + threadIdx.x; i < e; i += blockDim.x) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) acc_axis(__ldg(pts + 3 * (uint64_t)i + a), mn[a], mx[a], bad);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      mn[a] = fminf(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], o));
+      mx[a] = fmaxf(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
+    }
+    bad += __shfl_xor_sync(0xffffffffu, bad, o);
+  }
+  __shared__ float s_v[8][6];
+  __shared__ uint32_t s_bad[8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      s_v[warp][a] = mn[a];
+      s_v[warp][3 + a] = mx[a];
+    }
+    s_bad[warp] = bad;
+  }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    const int a = threadIdx.x;
+    float v = s_v[0][a];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v = a < 3 ? fminf(v, s_v[w][a]) : fmaxf(v, s_v[w][a]);
+    seg_scene[6 * c + a] = v;
+  } else if (threadIdx.x == 32) {
+    uint32_t t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_bad[w];
+    if (t) atomicOr(err, ERR_NONFINITE);
+  }
+}
+
+// Key (internal cloud id << 30) | 30-bit Morton code against the cloud's own
+// scene box (queries clamped into it); histograms of every radix pass.
+__global__ void __launch_bounds__(256) k_seg_morton(const float *__restrict__ pts, uint32_t count,
+                                                   const uint32_t *__restrict__ off, uint32_t n_clouds,
+                                                   const uint32_t *__restrict__ cmap,
+                                                   const float *__restrict__ seg_scene, uint64_t *__restrict__ keys,
+                                                   uint32_t *__restrict__ hist, int passes) {
+  __shared__ uint32_t s_h[8][kRadix];
+  for (int i = threadIdx.x; i < passes * kRadix; i += blockDim.x) (&s_h[0][0])[i] = 0;
+  __syncthreads();
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+    const uint32_t c = cloud_of(off, n_clouds, i);
+    float sc[6];
+#pragma unroll
+    for (int a = 0; a < 6; ++a) sc[a] = __ldg(seg_scene + 6 * c + a);
+    const uint32_t code = morton<uint32_t>(__ldg(pts + 3 * (uint64_t)i), __ldg(pts + 3 * (uint64_t)i + 1),
+                                           __ldg(pts + 3 * (uint64_t)i + 2), sc);
+    const uint64_t key = ((uint64_t)__ldg(cmap + c) << 30) | code;
+    keys[i] = key;
+    hist_add<uint64_t>(s_h, passes, key);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < passes * kRadix; i += blockDim.x) {
+    const uint32_t c = (&s_h[0][0])[i];
+    if (c) atomicAdd(&hist[i], c);
+  }
+}
+
+// Single bottom-up pass over all clouds at once (one tree whose top levels
+// separate the clouds); additionally records, for every cloud, the record slot
+// describing the subtree that holds exactly its points (sorted positions
+// [sorted_off[c], sorted_off[c+1]) ).
+__global__ void __launch_bounds__(256) k_apetrei_seg(const float *__restrict__ prims, uint32_t n,
+                                                    const uint64_t *__restrict__ codes,
+                                                    const uint32_t *__restrict__ perm, int32_t *__restrict__ other,
+                                                    float4 *__restrict__ rec, const uint32_t *__restrict__ sorted_off,
+                                                    int32_t *__restrict__ root_slot, uint32_t *__restrict__ err) {
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const uint32_t prim = perm[t];
+  const float *pp = prims + 3 * (uint64_t)prim;
+  float lx = pp[0], ly = pp[1], lz = pp[2];
+  float hx = lx, hy = ly, hz = lz;
+  int enc = ~(int)prim;
+  int pending = -1;  // cloud whose root is the current node
+  {
+    const uint32_t c = (uint32_t)(__ldg(codes + t) >> 30);
+    if (__ldg(sorted_off + c + 1) - __ldg(sorted_off + c) == 1) pending = (int)c;
+  }
+  if (n == 1) {
+    rec[0] = make_float4(lx, ly, lz, __int_as_float(enc));
+    rec[1] = make_float4(hx, hy, hz, 0.0f);
+    if (pending >= 0) root_slot[pending] = 0;
+    return;
+  }
+  const int N = (int)n;
+  int l = (int)t, r = (int)t;
+  for (int level = 0;; ++level) {
+    bool left_child;
+    if (l == 0) {
+      left_child = true;
+    } else if (r == N - 1) {
+      left_child = false;
+    } else {
+      const uint64_t cl = __ldg(codes + l), cr = __ldg(codes + r);
+      left_child = delta<uint64_t>(codes, cr, r, r + 1, N) > delta<uint64_t>(codes, cl, l, l - 1, N);
+    }
+    const int p = left_child ? r : l - 1;
+    if (p < 0 || p >= N - 1 || level > 160) {
+      set_err(err, ERR_STACK);
+      return;
+    }
+    const int slot_id = 2 + 2 * p + (left_child ? 0 : 1);
+    if (pending >= 0) {
+      root_slot[pending] = slot_id;
+      pending = -1;
+    }
+    float4 *slot = rec + 2 * (uint64_t)slot_id;
+    slot[0] = make_float4(lx, ly, lz, __int_as_float(enc));
+    slot[1] = make_float4(hx, hy, hz, 0.0f);
+    const int got = atom_exch_acq_rel_gpu(other + p, left_child ? l : r);
+    if (got < 0) return;
+    if (left_child) r = got;
+    else l = got;
+    const float4 *sib = rec + 4 + 4 * (uint64_t)p + (left_child ? 2 : 0);
+    const float4 slo = ld_cg_f4(sib), shi = ld_cg_f4(sib + 1);
+    lx = fminf(lx, slo.x); ly = fminf(ly, slo.y); lz = fminf(lz, slo.z);
+    hx = fmaxf(hx, shi.x); hy = fmaxf(hy, shi.y); hz = fmaxf(hz, shi.z);
+    enc = p;
+    const uint32_t c = (uint32_t)(__ldg(codes + l) >> 30);
+    if ((uint32_t)l == __ldg(sorted_off + c) && (uint32_t)r + 1 == __ldg(sorted_off + c + 1)) pending = (int)c;
+    if (l == 0 && r == N - 1) {
+      rec[0] = make_float4(lx, ly, lz, __int_as_float(p));
+      rec[1] = make_float4(hx, hy, hz, 0.0f);
+      if (pending >= 0) root_slot[pending] = 0;
+      return;
+    }
+  }
+}
+
 int sm_count() {
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
@@ -442,6 +604,29 @@ void launch_apetrei(const float *prims, uint32_t n, int kind, const K *codes, co
     k_apetrei<K, 0><<<ceil_div<uint32_t>(n, 256u), 256, 0, s>>>(prims, n, codes, perm, other, rec, err);
   else
     k_apetrei<K, 1><<<ceil_div<uint32_t>(n, 256u), 256, 0, s>>>(prims, n, codes, perm, other, rec, err);
+}
+
+void launch_seg_bounds(const float *pts, const uint32_t *off, uint32_t n_clouds, float *seg_scene, uint32_t *err,
+                       cudaStream_t s) {
+  if (n_clouds == 0) return;
+  prof::Scope ps(s, "seg_bounds");
+  k_seg_bounds<<<n_clouds, 256, 0, s>>>(pts, off, seg_scene, err);
+}
+
+void launch_seg_morton(const float *pts, uint32_t count, const uint32_t *off, uint32_t n_clouds, const uint32_t *cmap,
+                       const float *seg_scene, uint64_t *keys, uint32_t *hist, int passes, cudaStream_t s) {
+  if (count == 0) return;
+  const uint32_t blocks = std::min<uint32_t>(ceil_div<uint32_t>(count, 256u), (uint32_t)sm_count() * 8u);
+  prof::Scope ps(s, "seg_morton");
+  k_seg_morton<<<blocks, 256, 0, s>>>(pts, count, off, n_clouds, cmap, seg_scene, keys, hist, passes);
+}
+
+void launch_apetrei_seg(const float *prims, uint32_t n, const uint64_t *codes, const uint32_t *perm, int32_t *other,
+                        float4 *rec, const uint32_t *sorted_off, int32_t *root_slot, uint32_t *err, cudaStream_t s) {
+  if (n == 0) return;
+  prof::Scope ps(s, "apetrei_seg");
+  k_apetrei_seg<<<ceil_div<uint32_t>(n, 256u), 256, 0, s>>>(prims, n, codes, perm, other, rec, sorted_off, root_slot,
+                                                            err);
 }
 
 template void launch_apetrei<uint32_t>(const float *, uint32_t, int, const uint32_t *, const uint32_t *, int32_t *,

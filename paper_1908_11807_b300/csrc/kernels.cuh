@@ -16,6 +16,13 @@ void launch_hierarchy(const K *codes, uint32_t n, int32_t *parent, cudaStream_t 
 template <typename K>
 void launch_apetrei(const float *prims, uint32_t n, int kind, const K *codes, const uint32_t *perm, int32_t *other,
                     float4 *rec, uint32_t *err, cudaStream_t s);
+// batched clouds (cloud c owns entries [off[c], off[c+1]))
+void launch_seg_bounds(const float *pts, const uint32_t *off, uint32_t n_clouds, float *seg_scene, uint32_t *err,
+                       cudaStream_t s);
+void launch_seg_morton(const float *pts, uint32_t count, const uint32_t *off, uint32_t n_clouds, const uint32_t *cmap,
+                       const float *seg_scene, uint64_t *keys, uint32_t *hist, int passes, cudaStream_t s);
+void launch_apetrei_seg(const float *prims, uint32_t n, const uint64_t *codes, const uint32_t *perm, int32_t *other,
+                        float4 *rec, const uint32_t *sorted_off, int32_t *root_slot, uint32_t *err, cudaStream_t s);
 void launch_fit(const float *prims, uint32_t n, int kind, const uint32_t *perm, const int32_t *parent,
                 uint32_t *arrival, float4 *rec, uint32_t *err, cudaStream_t s);
 
@@ -90,6 +97,27 @@ struct NearestArgs {
   unsigned long long *stats; // set by launch_nearest
 };
 int launch_nearest(NearestArgs a, const TravCfg &cfg, cudaStream_t s);
+
+// batched clouds: k-nearest for sorted query positions [pos_begin, pos_end), all with k <= kc
+struct BatchQueryArgs {
+  const float4 *rec;
+  uint32_t n;
+  const float *queries;
+  const uint32_t *qperm;    // sorted position -> query index
+  const uint64_t *qkeys;    // sorted query keys, internal cloud id in bits 30 and up
+  uint32_t pos_begin, pos_end;
+  uint32_t *queue;          // work counter, zero at launch
+  const int32_t *root_slot; // per internal cloud: record slot of its subtree (-1: empty cloud)
+  const int32_t *kof;       // per internal cloud: k
+  const uint32_t *ncount;   // per internal cloud: number of points
+  const uint32_t *prim_base;// per internal cloud: index of its first point in the concatenation
+  const int64_t *row_off;   // per query: first output entry
+  int32_t *out_idx;
+  float *out_d2;            // nullable
+  uint32_t *err;
+  int stack_smem;
+};
+int launch_batch_nearest(const BatchQueryArgs &a, int kc, const TravCfg &cfg, cudaStream_t s);
 
 // ---- learned k-th-distance regressor (mlp.cu)
 constexpr int kMlpParams = 4481;  // W1 64x3, b1 64, W2 64x64, b2 64, w3 64, b3 1

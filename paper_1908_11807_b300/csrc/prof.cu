@@ -43,6 +43,11 @@ cudaEvent_t take_event() {
 bool enabled() { return g_on.load(std::memory_order_relaxed); }
 
 int begin(cudaStream_t s, const char *name) {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return -1;  // no event pairs inside a graph being captured
+  }
   std::lock_guard<std::mutex> lk(g_mu);
   Pending p;
   p.name = name;

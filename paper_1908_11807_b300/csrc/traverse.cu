@@ -54,7 +54,7 @@ __device__ __forceinline__ void append_flagged(bool flag, uint32_t qi, uint32_t 
 enum : int { kCount = 0, kFill = 1, kBuffered = 2 };
 
 template <int MODE>
-__global__ void __launch_bounds__(kMaxBlock) k_spatial(const SpatialArgs a) {
+__global__ void __launch_bounds__(kMaxBlock) k_spatial(const __grid_constant__ SpatialArgs a) {
   extern __shared__ int32_t s_stack[];
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t m = a.m_dev ? min(a.m, *a.m_dev) : a.m;
@@ -196,13 +196,14 @@ struct RegList {
       i[0] = ic;
     }
   }
-  __device__ __forceinline__ void write(int64_t row, int kk, int32_t *out_idx, float *out_d2) const {
+  __device__ __forceinline__ void write(int64_t row, int kk, int32_t *out_idx, float *out_d2,
+                                        int32_t base = 0) const {
 #pragma unroll
     for (int j = 0; j < KC; ++j) {
       const int o = j - off;
       if (o >= 0 && o < kk) {
         const bool real = i[j] != INT_MAX;
-        out_idx[row + o] = real ? i[j] : -1;
+        out_idx[row + o] = real ? i[j] - base : -1;
         if (out_d2) out_d2[row + o] = real ? d[j] : __int_as_float(0x7f800000);
       }
     }
@@ -276,8 +277,8 @@ struct SmemHeap {
 template <class List>
 __device__ __forceinline__ void knn_traverse(const float4 *__restrict__ rec, uint32_t n, float qx, float qy, float qz, List &L,
                                              int k, int32_t *s_node, float *s_dist, int stride, int stack_smem,
-                                             uint32_t *err, uint32_t &visited) {
-  const float4 r0 = __ldg(rec), r1 = __ldg(rec + 1);
+                                             uint32_t *err, uint32_t &visited, uint32_t root_slot = 0) {
+  const float4 r0 = __ldg(rec + 2 * (uint64_t)root_slot), r1 = __ldg(rec + 2 * (uint64_t)root_slot + 1);
   const int e0 = __float_as_int(r0.w);
   const float d0 = dist2_box(qx, qy, qz, r0, r1);
   if (e0 < 0) {
@@ -360,37 +361,44 @@ __device__ __forceinline__ float neighbour_bound2(const NearestArgs &a, uint32_t
 
 // Threads t <= m also write offsets[t] = t * kk (CSR view of the rows).  Thread
 // t serves sorted position pos = pos_list ? pos_list[t] : t, query qperm[pos].
-template <int KC>
-__global__ void __launch_bounds__(kMaxBlock) k_nearest(const NearestArgs a) {
+template <int KC, bool NBR>
+__global__ void __launch_bounds__(kMaxBlock) k_nearest(const __grid_constant__ NearestArgs a) {
   extern __shared__ unsigned char s_raw[];
+  const float4 *__restrict__ rec = a.rec;
+  const float *__restrict__ queries = a.queries;
+  const uint32_t *__restrict__ qperm = a.qperm;
+  const uint32_t *__restrict__ pos_list = a.pos_list;
+  int32_t *__restrict__ out_idx = a.out_idx;
+  float *__restrict__ out_d2 = a.out_d2;
+  uint32_t *__restrict__ err = a.err;
+  const uint32_t n = a.n;
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
   const int kk = a.kk, k = a.k, stack_smem = a.stack_smem;
   if (a.offsets && t <= a.m) a.offsets[t] = (int64_t)t * kk;
-  const uint32_t m = a.m_dev ? min(a.m, *a.m_dev) : a.m;  // count produced on the device (fallback passes)
+  const uint32_t m = a.m_dev ? min(a.m, *a.m_dev) : a.m;  // count produced on the device (second passes)
   if (t >= m) return;
   const int B = blockDim.x;
   int32_t *s_node = reinterpret_cast<int32_t *>(s_raw) + threadIdx.x;
   float *s_dist = reinterpret_cast<float *>(s_raw) + (size_t)stack_smem * B + threadIdx.x;
-  const uint32_t pos = a.pos_list ? __ldg(a.pos_list + t) : t;
-  const uint32_t qi = a.qperm ? __ldg(a.qperm + pos) : pos;
-  const float qx = __ldg(a.queries + 3 * (uint64_t)qi);
-  const float qy = __ldg(a.queries + 3 * (uint64_t)qi + 1);
-  const float qz = __ldg(a.queries + 3 * (uint64_t)qi + 2);
+  const uint32_t pos = pos_list ? __ldg(pos_list + t) : t;
+  const uint32_t qi = qperm ? __ldg(qperm + pos) : pos;
+  const float qx = __ldg(queries + 3 * (uint64_t)qi);
+  const float qy = __ldg(queries + 3 * (uint64_t)qi + 1);
+  const float qz = __ldg(queries + 3 * (uint64_t)qi + 2);
   float b0 = a.init_bound2 ? __ldg(a.init_bound2 + qi) * a.bound_scale : __int_as_float(0x7f800000);
-  if (a.nbr_bound) {
+  if constexpr (NBR) {  // a separate instantiation: this code slows the plain traversal
     if (pos > 0) b0 = fminf(b0, neighbour_bound2(a, pos - 1, qx, qy, qz));
     if (pos + 1 < a.m) b0 = fminf(b0, neighbour_bound2(a, pos + 1, qx, qy, qz));
   }
   const bool ok = finite3(qx, qy, qz);
   const int64_t row = (int64_t)qi * kk;
-  const uint32_t n = a.n;
   uint32_t visited = 0;
   if constexpr (KC > 0) {
     RegList<KC> L;
     L.init(b0, k);
-    if (ok && n > 0) knn_traverse(a.rec, n, qx, qy, qz, L, k, s_node, s_dist, B, stack_smem, a.err, visited);
+    if (ok && n > 0) knn_traverse(rec, n, qx, qy, qz, L, k, s_node, s_dist, B, stack_smem, err, visited);
     if (a.miss_list) append_flagged(ok && L.bound_idx() == INT_MAX, pos, a.miss_list, a.miss_count);
-    L.write(row, kk, a.out_idx, a.out_d2);
+    L.write(row, kk, out_idx, out_d2);
   } else {
     SmemHeap H;
     H.hd = reinterpret_cast<float *>(s_raw) + (size_t)2 * stack_smem * B + threadIdx.x;
@@ -398,11 +406,46 @@ __global__ void __launch_bounds__(kMaxBlock) k_nearest(const NearestArgs a) {
     H.s = B;
     H.k = k;
     H.init(b0, k);
-    if (ok && n > 0) knn_traverse(a.rec, n, qx, qy, qz, H, k, s_node, s_dist, B, stack_smem, a.err, visited);
+    if (ok && n > 0) knn_traverse(rec, n, qx, qy, qz, H, k, s_node, s_dist, B, stack_smem, err, visited);
     if (a.miss_list) append_flagged(ok && H.bound_idx() == INT_MAX, pos, a.miss_list, a.miss_count);
-    H.write(row, kk, a.out_idx, a.out_d2);
+    H.write(row, kk, out_idx, out_d2);
   }
   if (a.stats) atomicAdd(a.stats, (unsigned long long)visited);
+}
+
+// Batched clouds: persistent warps take tiles of 32 sorted query positions from
+// an atomic counter; each query starts at its cloud's subtree root and returns
+// indices local to its cloud.
+template <int KC>
+__global__ void __launch_bounds__(kMaxBlock) k_batch_nearest(const __grid_constant__ BatchQueryArgs a) {
+  extern __shared__ unsigned char s_raw[];
+  const int B = blockDim.x;
+  int32_t *s_node = reinterpret_cast<int32_t *>(s_raw) + threadIdx.x;
+  float *s_dist = reinterpret_cast<float *>(s_raw) + (size_t)a.stack_smem * B + threadIdx.x;
+  const uint32_t lane = threadIdx.x & 31;
+  while (true) {
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(a.queue, 32u);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (a.pos_begin + base >= a.pos_end) break;
+    const uint32_t pos = a.pos_begin + base + lane;
+    if (pos < a.pos_end) {
+      const uint32_t qi = __ldg(a.qperm + pos);
+      const uint32_t c = (uint32_t)(__ldg(a.qkeys + pos) >> 30);
+      const int k = __ldg(a.kof + c);
+      const int kk = min(k, (int)__ldg(a.ncount + c));
+      const int32_t slot = __ldg(a.root_slot + c);
+      const float qx = __ldg(a.queries + 3 * (uint64_t)qi);
+      const float qy = __ldg(a.queries + 3 * (uint64_t)qi + 1);
+      const float qz = __ldg(a.queries + 3 * (uint64_t)qi + 2);
+      RegList<KC> L;
+      L.init(__int_as_float(0x7f800000), k);
+      uint32_t visited = 0;
+      if (finite3(qx, qy, qz) && slot >= 0)
+        knn_traverse(a.rec, a.n, qx, qy, qz, L, k, s_node, s_dist, B, a.stack_smem, a.err, visited, (uint32_t)slot);
+      L.write(__ldg(a.row_off + qi), kk, a.out_idx, a.out_d2, (int32_t)__ldg(a.prim_base + c));
+    }
+  }
 }
 
 // ------------------------------------------------------------------- scan
@@ -572,11 +615,49 @@ void launch_scan(const int32_t *counts, uint32_t m, int64_t *offsets, int64_t *t
   k_scan_down<<<tiles, kScanThreads, 0, s>>>(counts, m, tmp, offsets);
 }
 
+template <int KC, bool NBR>
+static void nearest_kc2(dim3 grid, int block, size_t smem, cudaStream_t s, const NearestArgs &a) {
+  if (smem > 48 * 1024) {
+    cudaFuncSetAttribute(k_nearest<KC, NBR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_nearest<KC, NBR>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  }
+  k_nearest<KC, NBR><<<grid, block, smem, s>>>(a);
+}
+
 template <int KC>
 static void nearest_kc(dim3 grid, int block, size_t smem, cudaStream_t s, const NearestArgs &a) {
   prof::Scope ps(s, "nearest");
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k_nearest<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_nearest<KC><<<grid, block, smem, s>>>(a);
+  if (a.nbr_bound) nearest_kc2<KC, true>(grid, block, smem, s, a);
+  else nearest_kc2<KC, false>(grid, block, smem, s, a);
+}
+
+int launch_batch_nearest(const BatchQueryArgs &a, int kc, const TravCfg &cfg, cudaStream_t s) {
+  if (a.pos_end <= a.pos_begin) return 0;
+  const int block = cfg.block;
+  const size_t smem = (size_t)2 * a.stack_smem * block * sizeof(int32_t);
+  int dev = 0, sms = 148, per_sm = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  prof::Scope ps(s, "batch_nearest");
+#define ABX_BATCH(KC)                                                                                  \
+  do {                                                                                                 \
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_nearest<KC>, block, smem);          \
+    const uint32_t need = ceil_div<uint32_t>(a.pos_end - a.pos_begin, (uint32_t)block);                \
+    const uint32_t grid = std::max<uint32_t>(1u, std::min<uint32_t>(need, (uint32_t)(sms * std::max(per_sm, 1)))); \
+    k_batch_nearest<KC><<<grid, block, smem, s>>>(a);                                                   \
+  } while (0)
+  switch (kc) {
+    case 1: ABX_BATCH(1); break;
+    case 2: ABX_BATCH(2); break;
+    case 4: ABX_BATCH(4); break;
+    case 8: ABX_BATCH(8); break;
+    case 10: ABX_BATCH(10); break;
+    case 16: ABX_BATCH(16); break;
+    case 32: ABX_BATCH(32); break;
+    default: return -1;
+  }
+#undef ABX_BATCH
+  return 0;
 }
 
 int launch_nearest(NearestArgs a, const TravCfg &cfg, cudaStream_t s) {
@@ -587,7 +668,9 @@ int launch_nearest(NearestArgs a, const TravCfg &cfg, cudaStream_t s) {
   const uint32_t threads = a.m + 1;
   int block = cfg.block;
   size_t smem = (size_t)2 * cfg.stack_smem * block * sizeof(int32_t);
-  if (k > 32) {
+  // k > 32: candidates in a shared-memory heap (a 64-entry register list measured 2x slower at k = 50)
+  const bool use_heap = k > 32;
+  if (use_heap) {
     // heap of k pairs per thread in shared memory: shrink the block to fit
     while (block > 32 && smem + (size_t)2 * k * block * sizeof(int32_t) > 200 * 1024) {
       block >>= 1;
@@ -597,14 +680,14 @@ int launch_nearest(NearestArgs a, const TravCfg &cfg, cudaStream_t s) {
     if (smem > 227 * 1024) return -1;
   }
   const dim3 grid(ceil_div<uint32_t>(threads, (uint32_t)block));
-  if (k <= 1) nearest_kc<1>(grid, block, smem, s, a);
+  if (use_heap) nearest_kc<0>(grid, block, smem, s, a);
+  else if (k <= 1) nearest_kc<1>(grid, block, smem, s, a);
   else if (k <= 2) nearest_kc<2>(grid, block, smem, s, a);
   else if (k <= 4) nearest_kc<4>(grid, block, smem, s, a);
   else if (k <= 8) nearest_kc<8>(grid, block, smem, s, a);
   else if (k <= 10) nearest_kc<10>(grid, block, smem, s, a);
   else if (k <= 16) nearest_kc<16>(grid, block, smem, s, a);
-  else if (k <= 32) nearest_kc<32>(grid, block, smem, s, a);
-  else nearest_kc<0>(grid, block, smem, s, a);
+  else nearest_kc<32>(grid, block, smem, s, a);
   return 0;
 }
 

