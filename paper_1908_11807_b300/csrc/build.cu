@@ -314,39 +314,38 @@ __global__ void __launch_bounds__(256) k_fit(const float *__restrict__ prims, ui
 
 // Single bottom-up pass (Apetrei 2014): hierarchy and boxes together.  Internal
 // node p is the node whose split lies between sorted leaves p and p + 1.  A
-// thread starts at leaf t with range [t, t] and climbs: the parent of a node
-// covering [l, r] splits at r (node is its left child) when the augmented keys
-// share a longer prefix across r | r+1 than across l-1 | l, else at l - 1 (node
-// is its right child).  Each child writes its box record into the parent's
-// slot and exchanges its outer range end through `other[p]`; the first
-// arriver stops, the second learns the parent's full range, merges the two
-// boxes and continues.  Same binary radix tree as the top-down split rule.
-template <typename K, int KIND>
-__global__ void __launch_bounds__(256) k_apetrei(const float *__restrict__ prims, uint32_t n,
-                                                const K *__restrict__ codes, const uint32_t *__restrict__ perm,
-                                                int32_t *__restrict__ other, float4 *__restrict__ rec,
-                                                uint32_t *__restrict__ err) {
-  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n) return;
-  const uint32_t prim = perm[t];
-  float lx, ly, lz, hx, hy, hz;
-  if (KIND == 0) {
-    const float *p = prims + 3 * (uint64_t)prim;
-    lx = hx = p[0]; ly = hy = p[1]; lz = hz = p[2];
-  } else {
-    const float *p = prims + 6 * (uint64_t)prim;
-    lx = p[0]; ly = p[1]; lz = p[2]; hx = p[3]; hy = p[4]; hz = p[5];
-  }
-  int enc = ~(int)prim;
-  if (n == 1) {
-    rec[0] = make_float4(lx, ly, lz, __int_as_float(enc));
-    rec[1] = make_float4(hx, hy, hz, 0.0f);
-    return;
-  }
-  const int N = (int)n;
-  int l = (int)t, r = (int)t;
+// climb starts at leaf t with range [t, t]: the parent of a node covering
+// [l, r] splits at r (node is its left child) when the augmented keys share a
+// longer prefix across r | r+1 than across l-1 | l, else at l - 1 (node is its
+// right child).  Each child writes its box record into the parent's slot and
+// exchanges its outer range end; the first arriver stops, the second learns
+// the parent's full range, merges the two boxes and continues.  Same binary
+// radix tree as the top-down split rule.
+//
+// Two kernels.  k_apetrei_local: block b owns the sorted leaves [c0, c0 + C)
+// and the inner splits c0 .. c0 + C - 2; climbs exchange through shared memory
+// (box and range end in shared arrays, block-scope atomics, no GPU-scope
+// fence).  A climb stops when its parent is a boundary split (c0 - 1 or
+// c0 + C - 1): that node goes to the block's frontier list (at most one per
+// side).  An inner split that saw one local arrival (its other child crosses a
+// chunk boundary) stores the arriver's range end in other[p] as a completed
+// first arrival; one that saw none stores -1.  k_apetrei_top then climbs from
+// every frontier node with the GPU-scope exchange on other[]; crossing nodes
+// are few (about ten per chunk), so the chain of acq_rel exchanges no longer
+// holds blocks of the leaf work.  Each node still sees exactly two arrivals.
+
+struct Frontier {
+  float4 lo;  // w: enc
+  float4 hi;
+  int32_t l, r, pad0, pad1;  // l < 0: empty
+};
+
+template <typename K>
+__device__ __forceinline__ void apetrei_climb_global(const K *__restrict__ codes, int N, int32_t *__restrict__ other,
+                                                     float4 *__restrict__ rec, uint32_t *__restrict__ err, int l,
+                                                     int r, float4 lo, float4 hi) {
   for (int level = 0;; ++level) {
-    bool left_child;  // true: parent splits at r
+    bool left_child;
     if (l == 0) {
       left_child = true;
     } else if (r == N - 1) {
@@ -361,23 +360,141 @@ __global__ void __launch_bounds__(256) k_apetrei(const float *__restrict__ prims
       return;
     }
     float4 *slot = rec + 4 + 4 * (uint64_t)p + (left_child ? 0 : 2);
-    slot[0] = make_float4(lx, ly, lz, __int_as_float(enc));
-    slot[1] = make_float4(hx, hy, hz, 0.0f);
+    slot[0] = lo;
+    slot[1] = hi;
     const int got = atom_exch_acq_rel_gpu(other + p, left_child ? l : r);
     if (got < 0) return;  // sibling not done yet
     if (left_child) r = got;
     else l = got;
     const float4 *sib = rec + 4 + 4 * (uint64_t)p + (left_child ? 2 : 0);
     const float4 slo = ld_cg_f4(sib), shi = ld_cg_f4(sib + 1);
-    lx = fminf(lx, slo.x); ly = fminf(ly, slo.y); lz = fminf(lz, slo.z);
-    hx = fmaxf(hx, shi.x); hy = fmaxf(hy, shi.y); hz = fmaxf(hz, shi.z);
-    enc = p;
+    lo = make_float4(fminf(lo.x, slo.x), fminf(lo.y, slo.y), fminf(lo.z, slo.z), __int_as_float(p));
+    hi = make_float4(fmaxf(hi.x, shi.x), fmaxf(hi.y, shi.y), fmaxf(hi.z, shi.z), 0.0f);
     if (l == 0 && r == N - 1) {
-      rec[0] = make_float4(lx, ly, lz, __int_as_float(p));
-      rec[1] = make_float4(hx, hy, hz, 0.0f);
+      rec[0] = lo;
+      rec[1] = hi;
       return;
     }
   }
+}
+
+constexpr int kApBlock = 256;
+constexpr int kApChunk = kApBlock;  // sorted leaves per block of k_apetrei_local
+
+template <typename K, int KIND>
+__global__ void __launch_bounds__(kApBlock) k_apetrei_local(const float *__restrict__ prims, uint32_t n,
+                                                           const K *__restrict__ codes,
+                                                           const uint32_t *__restrict__ perm,
+                                                           int32_t *__restrict__ other, float4 *__restrict__ rec,
+                                                           Frontier *__restrict__ front, uint32_t *__restrict__ err) {
+  constexpr int C = kApChunk;
+  __shared__ K s_code[C + 2];        // codes of positions c0 - 1 .. c0 + C
+  __shared__ int32_t s_other[C];     // inner split c0 + i: -1 none, >= 0 first range end, -2 done
+  __shared__ float4 s_box[C][2][2];  // inner split c0 + i: box record of its child on each side
+  __shared__ Frontier s_front[2];    // children of the boundary splits c0 - 1 and c0 + C - 1
+  const int N = (int)n;
+  const int c0 = (int)blockIdx.x * C;
+  const int cend = min(c0 + C, N) - 1;  // last leaf of the chunk
+  const int tid = (int)threadIdx.x;
+  if (N == 1) {
+    if (tid == 0) {
+      const uint32_t prim = perm[0];
+      const float *q = prims + (KIND == 0 ? 3 : 6) * (uint64_t)prim;
+      rec[0] = make_float4(q[0], q[1], q[2], __int_as_float(~(int)prim));
+      rec[1] = KIND == 0 ? make_float4(q[0], q[1], q[2], 0.0f) : make_float4(q[3], q[4], q[5], 0.0f);
+      front[0].l = front[1].l = -1;
+    }
+    return;
+  }
+  for (int i = tid; i < C + 2; i += kApBlock) {
+    const int x = c0 - 1 + i;
+    if (x >= 0 && x < N) s_code[i] = codes[x];
+  }
+  for (int i = tid; i < C; i += kApBlock) s_other[i] = -1;
+  if (tid < 2) s_front[tid].l = -1;
+  __syncthreads();
+  auto dl = [&](int i, int j) -> int {  // both positions in [c0 - 1, cend + 1] and in [0, N)
+    const K ci = s_code[i - c0 + 1], cj = s_code[j - c0 + 1];
+    if (ci != cj) return clz_key<K>(ci ^ cj);
+    return (int)(8 * sizeof(K)) + __clz((uint32_t)(i ^ j));
+  };
+  const int t = c0 + tid;
+  if (t <= cend) {
+    const uint32_t prim = perm[t];
+    float4 lo, hi;
+    if (KIND == 0) {
+      const float *q = prims + 3 * (uint64_t)prim;
+      lo = make_float4(q[0], q[1], q[2], __int_as_float(~(int)prim));
+      hi = make_float4(q[0], q[1], q[2], 0.0f);
+    } else {
+      const float *q = prims + 6 * (uint64_t)prim;
+      lo = make_float4(q[0], q[1], q[2], __int_as_float(~(int)prim));
+      hi = make_float4(q[3], q[4], q[5], 0.0f);
+    }
+    int l = t, r = t;
+    for (int level = 0;; ++level) {
+      bool left_child;
+      if (l == 0) left_child = true;
+      else if (r == N - 1) left_child = false;
+      else left_child = dl(r, r + 1) > dl(l - 1, l);
+      const int p = left_child ? r : l - 1;
+      const int side = left_child ? 0 : 1;
+      float4 *slot = rec + 4 + 4 * (uint64_t)p + 2 * side;
+      slot[0] = lo;
+      slot[1] = hi;
+      if (p < c0 || p >= cend) {  // boundary split: the sibling lies in another chunk
+        Frontier &f = s_front[p < c0 ? 0 : 1];
+        f.lo = lo;
+        f.hi = hi;
+        f.r = r;
+        f.l = l;
+        break;
+      }
+      if (level > 128) {
+        set_err(err, ERR_STACK);
+        break;
+      }
+      const int i = p - c0;
+      s_box[i][side][0] = lo;
+      s_box[i][side][1] = hi;
+      __threadfence_block();
+      const int got = atomicExch(&s_other[i], left_child ? l : r);
+      if (got < 0) break;  // sibling not done yet (here, or crossing the chunk)
+      __threadfence_block();
+      s_other[i] = -2;
+      if (left_child) r = got;
+      else l = got;
+      const float4 slo = s_box[i][1 - side][0], shi = s_box[i][1 - side][1];
+      lo = make_float4(fminf(lo.x, slo.x), fminf(lo.y, slo.y), fminf(lo.z, slo.z), __int_as_float(p));
+      hi = make_float4(fmaxf(hi.x, shi.x), fmaxf(hi.y, shi.y), fmaxf(hi.z, shi.z), 0.0f);
+      if (l == 0 && r == N - 1) {
+        rec[0] = lo;
+        rec[1] = hi;
+        break;
+      }
+    }
+  }
+  __syncthreads();
+  // inner splits not completed here: record the local first arrival (or none) for the top kernel
+  for (int i = tid; i < cend - c0; i += kApBlock) {
+    const int v = s_other[i];
+    if (v != -2) other[c0 + i] = v;
+  }
+  if (tid == 0 && c0 > 0) other[c0 - 1] = -1;
+  if (tid < 2) front[2 * blockIdx.x + tid] = s_front[tid];
+}
+
+// One thread per frontier entry: continue the climb with the GPU-scope protocol.
+template <typename K>
+__global__ void __launch_bounds__(256) k_apetrei_top(const K *__restrict__ codes, uint32_t n,
+                                                    int32_t *__restrict__ other, float4 *__restrict__ rec,
+                                                    const Frontier *__restrict__ front, uint32_t n_front,
+                                                    uint32_t *__restrict__ err) {
+  const uint32_t f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= n_front) return;
+  const Frontier e = front[f];
+  if (e.l < 0) return;
+  apetrei_climb_global<K>(codes, (int)n, other, rec, err, e.l, e.r, e.lo, e.hi);
 }
 
 // ------------------------------------------------------ batched clouds
@@ -595,15 +712,22 @@ void launch_fit(const float *prims, uint32_t n, int kind, const uint32_t *perm, 
     k_fit<1><<<ceil_div<uint32_t>(n, 256u), 256, 0, s>>>(prims, n, perm, parent, arrival, rec, err);
 }
 
+size_t apetrei_front_bytes(uint32_t n) { return (size_t)2 * ceil_div<uint32_t>(std::max(n, 1u), kApChunk) * sizeof(Frontier); }
+
 template <typename K>
 void launch_apetrei(const float *prims, uint32_t n, int kind, const K *codes, const uint32_t *perm, int32_t *other,
-                    float4 *rec, uint32_t *err, cudaStream_t s) {
+                    float4 *rec, void *front_ws, uint32_t *err, cudaStream_t s) {
   if (n == 0) return;
   prof::Scope ps(s, "apetrei");
+  const uint32_t chunks = ceil_div<uint32_t>(n, (uint32_t)kApChunk);
+  Frontier *front = static_cast<Frontier *>(front_ws);
   if (kind == 0)
-    k_apetrei<K, 0><<<ceil_div<uint32_t>(n, 256u), 256, 0, s>>>(prims, n, codes, perm, other, rec, err);
+    k_apetrei_local<K, 0><<<chunks, kApBlock, 0, s>>>(prims, n, codes, perm, other, rec, front, err);
   else
-    k_apetrei<K, 1><<<ceil_div<uint32_t>(n, 256u), 256, 0, s>>>(prims, n, codes, perm, other, rec, err);
+    k_apetrei_local<K, 1><<<chunks, kApBlock, 0, s>>>(prims, n, codes, perm, other, rec, front, err);
+  if (chunks > 1)
+    k_apetrei_top<K><<<ceil_div<uint32_t>(2 * chunks, 256u), 256, 0, s>>>(codes, n, other, rec, front, 2 * chunks,
+                                                                          err);
 }
 
 void launch_seg_bounds(const float *pts, const uint32_t *off, uint32_t n_clouds, float *seg_scene, uint32_t *err,
@@ -630,9 +754,9 @@ void launch_apetrei_seg(const float *prims, uint32_t n, const uint64_t *codes, c
 }
 
 template void launch_apetrei<uint32_t>(const float *, uint32_t, int, const uint32_t *, const uint32_t *, int32_t *,
-                                       float4 *, uint32_t *, cudaStream_t);
+                                       float4 *, void *, uint32_t *, cudaStream_t);
 template void launch_apetrei<uint64_t>(const float *, uint32_t, int, const uint64_t *, const uint32_t *, int32_t *,
-                                       float4 *, uint32_t *, cudaStream_t);
+                                       float4 *, void *, uint32_t *, cudaStream_t);
 template void launch_morton<uint32_t>(const float *, uint32_t, int, DevMeta *, uint32_t *, uint32_t *, int, bool,
                                       cudaStream_t);
 template void launch_morton<uint64_t>(const float *, uint32_t, int, DevMeta *, uint64_t *, uint32_t *, int, bool,

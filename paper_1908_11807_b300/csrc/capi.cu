@@ -203,14 +203,16 @@ int build_impl(arborx_bvh_s *h, const float *d_prims, cudaStream_t s) {
     if (nonfinite) return ARBORX_EINVAL;
   }
 
-  // scratch: keys A/B, vals A/B, parent links (Karras) or range ends
-  // (Apetrei, preset to -1), then the zero-initialised region
+  // scratch: keys A/B, vals A/B, parent links (Karras, preset to -1) or range
+  // ends (Apetrei), the Apetrei frontier list, then the zero-initialised region
   const bool karras = h->opts.build_method == ARBORX_BUILD_KARRAS;
   const size_t ws_words = sort_ws_words<K>(n, key_bits);
-  const size_t zero_bytes = align_up((size_t)n_int * sizeof(uint32_t)) + align_up(ws_words * sizeof(uint32_t));
+  const size_t arrival_words = karras ? (size_t)n_int : 0;  // Karras fit's arrival counters
+  const size_t zero_bytes = align_up(arrival_words * sizeof(uint32_t)) + align_up(ws_words * sizeof(uint32_t));
   const size_t link_words = karras ? (size_t)(2 * n - 1) : (size_t)n_int;
+  const size_t front_bytes = karras ? 0 : align_up(apetrei_front_bytes(un));
   const size_t scratch_bytes = 2 * align_up((size_t)n * sizeof(K)) + 2 * align_up((size_t)n * sizeof(uint32_t)) +
-                               align_up(link_words * sizeof(int32_t)) + zero_bytes;
+                               align_up(link_words * sizeof(int32_t)) + front_bytes + zero_bytes;
   void *scratch = dev_alloc(h->opts, scratch_bytes, s);
   if (!scratch) return ARBORX_ENOMEM;
   Carver c(scratch);
@@ -219,11 +221,12 @@ int build_impl(arborx_bvh_s *h, const float *d_prims, cudaStream_t s) {
   uint32_t *vA = c.take<uint32_t>(n);
   uint32_t *vB = c.take<uint32_t>(n);
   int32_t *links = c.take<int32_t>(link_words);
+  void *front = karras ? nullptr : static_cast<void *>(c.take<char>(front_bytes));
   char *zero_base = c.base + c.off;
-  uint32_t *arrival = c.take<uint32_t>(n_int);
+  uint32_t *arrival = c.take<uint32_t>(arrival_words);
   uint32_t *wsbase = c.take<uint32_t>(ws_words);
   cudaMemsetAsync(zero_base, 0, zero_bytes, s);
-  cudaMemsetAsync(links, 0xff, link_words * sizeof(int32_t), s);  // unset links read as -1
+  if (karras) cudaMemsetAsync(links, 0xff, link_words * sizeof(int32_t), s);  // unset links read as -1
   const SortWs ws = sort_ws_carve<K>(wsbase, n, key_bits);
 
   launch_morton<K>(d_prims, un, h->kind, h->meta, kA, ws.hist, passes, true, s);
@@ -234,7 +237,7 @@ int build_impl(arborx_bvh_s *h, const float *d_prims, cudaStream_t s) {
     launch_hierarchy<K>(skeys, un, links, s);
     launch_fit(d_prims, un, h->kind, perm, links, arrival, h->rec, &h->meta->err, s);
   } else {
-    launch_apetrei<K>(d_prims, un, h->kind, skeys, perm, links, h->rec, &h->meta->err, s);
+    launch_apetrei<K>(d_prims, un, h->kind, skeys, perm, links, h->rec, front, &h->meta->err, s);
   }
   st = launch_status();
   if (st == ARBORX_OK && h->opts.keep_order) {

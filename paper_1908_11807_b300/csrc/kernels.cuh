@@ -13,9 +13,12 @@ void launch_morton(const float *prims, uint32_t n, int kind, DevMeta *meta, K *c
                    bool write_scene, cudaStream_t s);
 template <typename K>
 void launch_hierarchy(const K *codes, uint32_t n, int32_t *parent, cudaStream_t s);
+// bytes of the frontier list of launch_apetrei for n leaves
+size_t apetrei_front_bytes(uint32_t n);
+// other: n - 1 words, no initialisation needed; front_ws: apetrei_front_bytes(n)
 template <typename K>
 void launch_apetrei(const float *prims, uint32_t n, int kind, const K *codes, const uint32_t *perm, int32_t *other,
-                    float4 *rec, uint32_t *err, cudaStream_t s);
+                    float4 *rec, void *front_ws, uint32_t *err, cudaStream_t s);
 // batched clouds (cloud c owns entries [off[c], off[c+1]))
 void launch_seg_bounds(const float *pts, const uint32_t *off, uint32_t n_clouds, float *seg_scene, uint32_t *err,
                        cudaStream_t s);

@@ -31,6 +31,11 @@ CLOUDS = {
     "tiny_2": lambda: datagen.cube(2, 11),
     "tiny_3": lambda: datagen.cube(3, 12),
     "boxes_2e4": lambda: datagen.boxes(20_000, datagen.SEED0 + 2),
+    # runs of 1000 equal codes: subtrees made only of index bits span several 256-leaf chunks
+    "dup_runs_1000": lambda: np.repeat(datagen.cube(60, 13), 1000, axis=0),
+    "chunk_256": lambda: datagen.cube(256, 14),
+    "chunk_257": lambda: datagen.cube(257, 15),
+    "chunk_1023": lambda: datagen.cube(1023, 16),
 }
 
 
@@ -138,10 +143,11 @@ def test_sort_pairs_u64_matches_stable_argsort(n, key_bits):
     assert np.array_equal(host(sk).view(np.uint64), keys[want])
 
 
-def test_apetrei_and_karras_build_the_same_tree():
+@pytest.mark.parametrize("n", [50_000, 255, 512, 513, 65_539, 400_000])
+def test_apetrei_and_karras_build_the_same_tree(n):
     # same binary radix tree up to node numbering: identical sets of (range, box)
     ab = _ab()
-    p = datagen.gaussian_mixture(50_000, 77)
+    p = datagen.gaussian_mixture(n, 77)
     trees = []
     for method in (0, 1):
         bvh = ab.BVH(dev(p), keep_order=1, build_method=method)
