@@ -323,16 +323,21 @@ __global__ void __launch_bounds__(256) k_fit(const float *__restrict__ prims, ui
 // radix tree as the top-down split rule.
 //
 // Two kernels.  k_apetrei_local: block b owns the sorted leaves [c0, c0 + C)
-// and the inner splits c0 .. c0 + C - 2; climbs exchange through shared memory
-// (box and range end in shared arrays, block-scope atomics, no GPU-scope
-// fence).  A climb stops when its parent is a boundary split (c0 - 1 or
-// c0 + C - 1): that node goes to the block's frontier list (at most one per
-// side).  An inner split that saw one local arrival (its other child crosses a
-// chunk boundary) stores the arriver's range end in other[p] as a completed
-// first arrival; one that saw none stores -1.  k_apetrei_top then climbs from
-// every frontier node with the GPU-scope exchange on other[]; crossing nodes
-// are few (about ten per chunk), so the chain of acq_rel exchanges no longer
-// holds blocks of the leaf work.  Each node still sees exactly two arrivals.
+// and the inner splits c0 .. c0 + C - 2.  With d_i the common-prefix length of
+// the augmented keys at i | i+1, the node split at p covers [l, r] where l - 1
+// and r are the nearest positions on either side with d < d_p (the binary
+// radix tree is the Cartesian tree of d); its box is the union of the leaf
+// boxes l..r; its parent splits at r if d_r > d_(l-1), else at l - 1 (the
+// same rule the climb uses).  The block finds these nearest smaller values in
+// a shared-memory minimum table of d and the unions in shared-memory prefix /
+// suffix / segment tables, one leaf and one split per thread, with no climb,
+// atomic or fence.  A split whose nearest smaller value lies outside the chunk
+// on some side is a crossing node: it records in other[p] the outer end of
+// its local child if it has one (a completed first arrival), else -1.  A node
+// or leaf whose parent is a boundary split (c0 - 1 or c0 + C - 1) goes to the
+// block's frontier list (at most one per side).  k_apetrei_top then climbs
+// from every frontier node with the GPU-scope exchange on other[]; crossing
+// nodes are few (about ten per chunk).  Each node sees exactly two arrivals.
 
 struct Frontier {
   float4 lo;  // w: enc
@@ -379,7 +384,16 @@ __device__ __forceinline__ void apetrei_climb_global(const K *__restrict__ codes
 }
 
 constexpr int kApBlock = 256;
-constexpr int kApChunk = kApBlock;  // sorted leaves per block of k_apetrei_local
+constexpr int kApChunk = kApBlock;  // sorted leaves (and threads) per block of k_apetrei_local
+constexpr int kApLevels = 9;        // minimum table levels: 2^8 <= kApChunk + 1 entries
+constexpr int kApSeg = 16;          // leaves per union segment
+constexpr int kApSegs = kApChunk / kApSeg;
+constexpr int kApSegLevels = 5;     // 2^4 = kApSegs
+
+__device__ __forceinline__ void box_union(float4 &lo, float4 &hi, const float4 a, const float4 b) {
+  lo.x = fminf(lo.x, a.x); lo.y = fminf(lo.y, a.y); lo.z = fminf(lo.z, a.z);
+  hi.x = fmaxf(hi.x, b.x); hi.y = fmaxf(hi.y, b.y); hi.z = fmaxf(hi.z, b.z);
+}
 
 template <typename K, int KIND>
 __global__ void __launch_bounds__(kApBlock) k_apetrei_local(const float *__restrict__ prims, uint32_t n,
@@ -388,13 +402,16 @@ __global__ void __launch_bounds__(kApBlock) k_apetrei_local(const float *__restr
                                                            int32_t *__restrict__ other, float4 *__restrict__ rec,
                                                            Frontier *__restrict__ front, uint32_t *__restrict__ err) {
   constexpr int C = kApChunk;
-  __shared__ K s_code[C + 2];        // codes of positions c0 - 1 .. c0 + C
-  __shared__ int32_t s_other[C];     // inner split c0 + i: -1 none, >= 0 first range end, -2 done
-  __shared__ float4 s_box[C][2][2];  // inner split c0 + i: box record of its child on each side
-  __shared__ Frontier s_front[2];    // children of the boundary splits c0 - 1 and c0 + C - 1
+  __shared__ K s_code[C + 2];                          // codes of positions c0 - 1 .. c0 + C
+  __shared__ int32_t s_dmin[kApLevels][C + 1];         // [j][x]: min d over positions c0-1+x .. +2^j-1
+  __shared__ float4 s_leaf[2][C];                      // leaf boxes (lo, hi)
+  __shared__ float4 s_pre[2][C], s_suf[2][C];          // unions from segment start to t / t to segment end
+  __shared__ float4 s_seg[kApSegLevels][2][kApSegs];   // [j][.][s]: union of segments s .. s + 2^j - 1
+  __shared__ Frontier s_front[2];                      // children of the boundary splits c0 - 1, c0 + C - 1
   const int N = (int)n;
   const int c0 = (int)blockIdx.x * C;
   const int cend = min(c0 + C, N) - 1;  // last leaf of the chunk
+  const int last = cend - c0 + 1;       // largest valid index into s_dmin[0]
   const int tid = (int)threadIdx.x;
   if (N == 1) {
     if (tid == 0) {
@@ -410,78 +427,145 @@ __global__ void __launch_bounds__(kApBlock) k_apetrei_local(const float *__restr
     const int x = c0 - 1 + i;
     if (x >= 0 && x < N) s_code[i] = codes[x];
   }
-  for (int i = tid; i < C; i += kApBlock) s_other[i] = -1;
   if (tid < 2) s_front[tid].l = -1;
-  __syncthreads();
-  auto dl = [&](int i, int j) -> int {  // both positions in [c0 - 1, cend + 1] and in [0, N)
-    const K ci = s_code[i - c0 + 1], cj = s_code[j - c0 + 1];
-    if (ci != cj) return clz_key<K>(ci ^ cj);
-    return (int)(8 * sizeof(K)) + __clz((uint32_t)(i ^ j));
-  };
-  const int t = c0 + tid;
-  if (t <= cend) {
-    const uint32_t prim = perm[t];
-    float4 lo, hi;
+  const int t = c0 + tid;  // this thread's leaf, and split t (between t and t + 1)
+  const bool has_leaf = t <= cend;
+  uint32_t prim = 0;
+  float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;
+  if (has_leaf) {
+    prim = perm[t];
     if (KIND == 0) {
       const float *q = prims + 3 * (uint64_t)prim;
-      lo = make_float4(q[0], q[1], q[2], __int_as_float(~(int)prim));
-      hi = make_float4(q[0], q[1], q[2], 0.0f);
+      lo = make_float4(q[0], q[1], q[2], 0.0f);
+      hi = lo;
     } else {
       const float *q = prims + 6 * (uint64_t)prim;
-      lo = make_float4(q[0], q[1], q[2], __int_as_float(~(int)prim));
+      lo = make_float4(q[0], q[1], q[2], 0.0f);
       hi = make_float4(q[3], q[4], q[5], 0.0f);
     }
-    int l = t, r = t;
-    for (int level = 0;; ++level) {
-      bool left_child;
-      if (l == 0) left_child = true;
-      else if (r == N - 1) left_child = false;
-      else left_child = dl(r, r + 1) > dl(l - 1, l);
-      const int p = left_child ? r : l - 1;
-      const int side = left_child ? 0 : 1;
-      float4 *slot = rec + 4 + 4 * (uint64_t)p + 2 * side;
-      slot[0] = lo;
-      slot[1] = hi;
-      if (p < c0 || p >= cend) {  // boundary split: the sibling lies in another chunk
-        Frontier &f = s_front[p < c0 ? 0 : 1];
-        f.lo = lo;
-        f.hi = hi;
-        f.r = r;
-        f.l = l;
-        break;
-      }
-      if (level > 128) {
-        set_err(err, ERR_STACK);
-        break;
-      }
-      const int i = p - c0;
-      s_box[i][side][0] = lo;
-      s_box[i][side][1] = hi;
-      __threadfence_block();
-      const int got = atomicExch(&s_other[i], left_child ? l : r);
-      if (got < 0) break;  // sibling not done yet (here, or crossing the chunk)
-      __threadfence_block();
-      s_other[i] = -2;
-      if (left_child) r = got;
-      else l = got;
-      const float4 slo = s_box[i][1 - side][0], shi = s_box[i][1 - side][1];
-      lo = make_float4(fminf(lo.x, slo.x), fminf(lo.y, slo.y), fminf(lo.z, slo.z), __int_as_float(p));
-      hi = make_float4(fmaxf(hi.x, shi.x), fmaxf(hi.y, shi.y), fmaxf(hi.z, shi.z), 0.0f);
-      if (l == 0 && r == N - 1) {
-        rec[0] = lo;
-        rec[1] = hi;
-        break;
-      }
+  }
+  // unions within 16-leaf segments (lanes of one half-warp), before and after each leaf
+  {
+    float4 plo = lo, phi = hi, slo = lo, shi = hi;
+    const int sl = tid & (kApSeg - 1);
+    const int valid_to = has_leaf ? kApSeg - 1 : -1;  // beyond the last leaf: contribute nothing
+    const int seg_last = min(kApSeg - 1, cend - (c0 + (tid & ~(kApSeg - 1))));
+#pragma unroll
+    for (int o = 1; o < kApSeg; o <<= 1) {
+      float4 a, b;
+      a.x = __shfl_up_sync(0xffffffffu, plo.x, o, kApSeg); a.y = __shfl_up_sync(0xffffffffu, plo.y, o, kApSeg);
+      a.z = __shfl_up_sync(0xffffffffu, plo.z, o, kApSeg); b.x = __shfl_up_sync(0xffffffffu, phi.x, o, kApSeg);
+      b.y = __shfl_up_sync(0xffffffffu, phi.y, o, kApSeg); b.z = __shfl_up_sync(0xffffffffu, phi.z, o, kApSeg);
+      if (sl >= o) box_union(plo, phi, a, b);
+      a.x = __shfl_down_sync(0xffffffffu, slo.x, o, kApSeg); a.y = __shfl_down_sync(0xffffffffu, slo.y, o, kApSeg);
+      a.z = __shfl_down_sync(0xffffffffu, slo.z, o, kApSeg); b.x = __shfl_down_sync(0xffffffffu, shi.x, o, kApSeg);
+      b.y = __shfl_down_sync(0xffffffffu, shi.y, o, kApSeg); b.z = __shfl_down_sync(0xffffffffu, shi.z, o, kApSeg);
+      if (sl + o <= seg_last) box_union(slo, shi, a, b);
+    }
+    (void)valid_to;
+    s_leaf[0][tid] = lo;
+    s_leaf[1][tid] = hi;
+    s_pre[0][tid] = plo;
+    s_pre[1][tid] = phi;
+    s_suf[0][tid] = slo;
+    s_suf[1][tid] = shi;
+    if (sl == 0) {
+      s_seg[0][0][tid / kApSeg] = slo;
+      s_seg[0][1][tid / kApSeg] = shi;
     }
   }
   __syncthreads();
-  // inner splits not completed here: record the local first arrival (or none) for the top kernel
-  for (int i = tid; i < cend - c0; i += kApBlock) {
-    const int v = s_other[i];
-    if (v != -2) other[c0 + i] = v;
+  // d at positions c0 - 1 + x (-1 outside [0, N - 2])
+  auto dl = [&](int pos) -> int {
+    if (pos < 0 || pos >= N - 1) return -1;
+    const K ci = s_code[pos - c0 + 1], cj = s_code[pos - c0 + 2];
+    if (ci != cj) return clz_key<K>(ci ^ cj);
+    return (int)(8 * sizeof(K)) + __clz((uint32_t)(pos ^ (pos + 1)));
+  };
+  for (int x = tid; x <= last; x += kApBlock) s_dmin[0][x] = dl(c0 - 1 + x);
+  __syncthreads();
+#pragma unroll 1
+  for (int j = 1; j < kApLevels; ++j) {
+    const int h = 1 << (j - 1);
+    if (tid + 2 * h - 1 <= last) s_dmin[j][tid] = min(s_dmin[j - 1][tid], s_dmin[j - 1][tid + h]);
+    if (j < kApSegLevels && tid + 2 * h <= kApSegs) {
+      float4 a = s_seg[j - 1][0][tid], b = s_seg[j - 1][1][tid];
+      box_union(a, b, s_seg[j - 1][0][tid + h], s_seg[j - 1][1][tid + h]);
+      s_seg[j][0][tid] = a;
+      s_seg[j][1][tid] = b;
+    }
+    __syncthreads();
   }
+  auto D = [&](int pos) -> int { return s_dmin[0][pos - c0 + 1]; };
+  // write node [l, r] (box lo/hi, enc in lo.w) into its parent's slot, or as the root
+  auto emit = [&](int l, int r, float4 blo, float4 bhi) {
+    if (l == 0 && r == N - 1) {
+      rec[0] = blo;
+      rec[1] = bhi;
+      return;
+    }
+    const bool left_child = D(r) > D(l - 1);
+    const int p = left_child ? r : l - 1;
+    float4 *slot = rec + 4 + 4 * (uint64_t)p + (left_child ? 0 : 2);
+    slot[0] = blo;
+    slot[1] = bhi;
+    if (p < c0 || p >= cend) {  // boundary split: continued by the top kernel
+      Frontier &f = s_front[p < c0 ? 0 : 1];
+      f.lo = blo;
+      f.hi = bhi;
+      f.r = r;
+      f.l = l;
+    }
+  };
+  if (has_leaf) {
+    lo.w = __int_as_float(~(int)prim);
+    emit(t, t, lo, hi);
+  }
+  if (t < cend) {
+    const int xp = tid + 1;  // index of d_t
+    const int dp = s_dmin[0][xp];
+    int y = xp;  // smallest y with d >= dp on [y, xp - 1]
+#pragma unroll
+    for (int j = kApLevels - 1; j >= 0; --j)
+      if (y >= (1 << j) && s_dmin[j][y - (1 << j)] >= dp) y -= 1 << j;
+    const bool found_l = y > 0;
+    const int l = c0 - 1 + y;  // valid when found_l
+    int z = xp + 1;  // largest z - 1 with d >= dp on [xp + 1, z - 1]
+#pragma unroll
+    for (int j = kApLevels - 1; j >= 0; --j)
+      if (z + (1 << j) - 1 <= last && s_dmin[j][z] >= dp) z += 1 << j;
+    const bool found_r = z <= last;
+    const int r = c0 - 1 + z;  // valid when found_r
+    if (found_l && found_r) {
+      const int a = l - c0, b = r - c0;
+      const int sa = a / kApSeg, sb = b / kApSeg;
+      float4 blo, bhi;
+      if (sa == sb) {
+        blo = s_leaf[0][a];
+        bhi = s_leaf[1][a];
+        for (int i = a + 1; i <= b; ++i) box_union(blo, bhi, s_leaf[0][i], s_leaf[1][i]);
+      } else {
+        blo = s_suf[0][a];
+        bhi = s_suf[1][a];
+        box_union(blo, bhi, s_pre[0][b], s_pre[1][b]);
+        if (sb - sa >= 2) {
+          const int s0 = sa + 1, s1 = sb - 1;
+          const int j = 31 - __clz(s1 - s0 + 1);
+          box_union(blo, bhi, s_seg[j][0][s0], s_seg[j][1][s0]);
+          box_union(blo, bhi, s_seg[j][0][s1 - (1 << j) + 1], s_seg[j][1][s1 - (1 << j) + 1]);
+        }
+      }
+      blo.w = __int_as_float(t);
+      bhi.w = 0.0f;
+      emit(l, r, blo, bhi);
+    } else {
+      other[t] = found_l ? l : (found_r ? r : -1);  // local child's outer end: a completed first arrival
+    }
+  }
+  __syncthreads();
   if (tid == 0 && c0 > 0) other[c0 - 1] = -1;
   if (tid < 2) front[2 * blockIdx.x + tid] = s_front[tid];
+  (void)err;
 }
 
 // One thread per frontier entry: continue the climb with the GPU-scope protocol.

@@ -12,7 +12,7 @@ constexpr uint32_t kFlagAgg = 1u << 30;   // tile's own digit count published
 constexpr uint32_t kFlagPre = 2u << 30;   // inclusive prefix over tiles 0..t published
 constexpr uint32_t kValMask = (1u << 30) - 1u;
 constexpr uint32_t kSpinCap = 1u << 21;   // look-back give-up bound (~1 s)
-constexpr int kWin = 16;                  // predecessors loaded per look-back round trip
+constexpr int kWin = 4;                   // predecessors loaded per look-back round trip
 
 // Exclusive scans over the 256 threads of a block, two values at once.
 __device__ __forceinline__ void block_excl_scan2(uint32_t a, uint32_t b, uint32_t &a_ex, uint32_t &b_ex,
@@ -119,6 +119,21 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(const K *__restric
   block_excl_scan2(cnt, hist[d], cnt_ex, h_ex, s_scan);
   s_dstart[d] = cnt_ex;
 
+  __syncthreads();  // s_dstart and the warp offsets are complete
+
+  // stage in digit order (needs only tile-local offsets, so it runs before the
+  // look-back and gives the predecessors time to publish)
+#pragma unroll
+  for (int i = 0; i < ITEMS; ++i) {
+    const uint32_t pos = wbase + i * 32 + lane;
+    if (pos < n) {
+      const uint32_t dd = (uint32_t)(k[i] >> shift) & (kRadix - 1);
+      const uint32_t p = s_dstart[dd] + s_whist[warp][dd] + rk[i];
+      s_k[p] = k[i];
+      s_v[p] = v[i];
+    }
+  }
+
   // decoupled look-back over a window of kWin predecessors at a time (independent
   // loads, one round trip per window); stops at the first inclusive prefix
   uint32_t excl = 0;
@@ -157,27 +172,18 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(const K *__restric
   s_gofs[d] = h_ex + excl - cnt_ex;
   __syncthreads();
 
-  // stage in digit order
+  // write runs (unrolled: the shared-memory loads of all items are independent)
+  const uint32_t tn = min((uint32_t)TILE, n - tbase);
 #pragma unroll
   for (int i = 0; i < ITEMS; ++i) {
-    const uint32_t pos = wbase + i * 32 + lane;
-    if (pos < n) {
-      const uint32_t dd = (uint32_t)(k[i] >> shift) & (kRadix - 1);
-      const uint32_t p = s_dstart[dd] + s_whist[warp][dd] + rk[i];
-      s_k[p] = k[i];
-      s_v[p] = v[i];
+    const uint32_t j = tid + i * kSortThreads;
+    if (j < tn) {
+      const K key = s_k[j];
+      const uint32_t dd = (uint32_t)(key >> shift) & (kRadix - 1);
+      const uint32_t dst = s_gofs[dd] + j;
+      kout[dst] = key;
+      vout[dst] = s_v[j];
     }
-  }
-  __syncthreads();
-
-  // write runs
-  const uint32_t tn = min((uint32_t)TILE, n - tbase);
-  for (uint32_t j = tid; j < tn; j += kSortThreads) {
-    const K key = s_k[j];
-    const uint32_t dd = (uint32_t)(key >> shift) & (kRadix - 1);
-    const uint32_t dst = s_gofs[dd] + j;
-    kout[dst] = key;
-    vout[dst] = s_v[j];
   }
 }
 
