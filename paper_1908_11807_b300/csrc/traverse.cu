@@ -141,21 +141,47 @@ __global__ void __launch_bounds__(kMaxBlock) k_spatial(const __grid_constant__ S
   if (a.stats) atomicAdd(a.stats, (unsigned long long)visited);
 }
 
-// Move buffered rows (those that fit) to their CSR place; one thread per slot.
+// Move buffered rows (those that fit) to their CSR place.  A thread takes
+// kCompactPer slots a block width apart and issues all their loads (row
+// count, row offset, buffered value) before any store, so the dependent
+// latencies of a thread overlap instead of adding up.
+constexpr int kCompactPer = 8;
+
+template <typename IDX>
 __global__ void __launch_bounds__(256) k_compact(const int32_t *__restrict__ buf, int bs,
                                                 const int32_t *__restrict__ counts,
                                                 const int64_t *__restrict__ offsets, uint32_t m,
                                                 int32_t *__restrict__ indices, int64_t capacity,
                                                 uint32_t *__restrict__ err) {
-  const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (uint64_t)m * bs) return;
-  const uint32_t qi = (uint32_t)(t / bs);
-  const int j = (int)(t - (uint64_t)qi * bs);
-  const int c = __ldg(counts + qi);
-  if (c > bs || j >= c) return;
-  const int64_t pos = __ldg(offsets + qi) + j;
-  if (pos < capacity) indices[pos] = __ldg(buf + t);
-  else set_err(err, ERR_CSR);
+  const IDX total = (IDX)m * (IDX)bs;
+  const IDX base = (IDX)blockIdx.x * (IDX)(blockDim.x * kCompactPer) + threadIdx.x;
+  int32_t c[kCompactPer], j[kCompactPer], v[kCompactPer];
+  int64_t o[kCompactPer];
+#pragma unroll
+  for (int k = 0; k < kCompactPer; ++k) {
+    const IDX t = base + (IDX)k * blockDim.x;
+    c[k] = -1;
+    j[k] = 0;
+    if (t < total) {
+      const IDX qi = t / (IDX)bs;
+      j[k] = (int32_t)(t - qi * (IDX)bs);
+      c[k] = __ldg(counts + qi);
+      o[k] = __ldg(offsets + qi);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kCompactPer; ++k) {
+    const IDX t = base + (IDX)k * blockDim.x;
+    if (c[k] <= bs && j[k] < c[k]) v[k] = __ldg(buf + t);
+  }
+#pragma unroll
+  for (int k = 0; k < kCompactPer; ++k) {
+    if (c[k] <= bs && j[k] < c[k]) {
+      const int64_t pos = o[k] + j[k];
+      if (pos < capacity) indices[pos] = v[k];
+      else set_err(err, ERR_CSR);
+    }
+  }
 }
 
 // ---------------------------------------------------------------- nearest
@@ -598,7 +624,11 @@ void launch_compact(const int32_t *buf, int bs, const int32_t *counts, const int
   const uint64_t slots = (uint64_t)m * bs;
   if (slots == 0) return;
   prof::Scope ps(s, "compact");
-  k_compact<<<(unsigned)((slots + 255) / 256), 256, 0, s>>>(buf, bs, counts, offsets, m, indices, capacity, err);
+  const uint64_t blocks = (slots + 256 * kCompactPer - 1) / (256 * kCompactPer);
+  if (slots + 256 * kCompactPer < (1ull << 32))  // 32-bit slot arithmetic cannot wrap
+    k_compact<uint32_t><<<(unsigned)blocks, 256, 0, s>>>(buf, bs, counts, offsets, m, indices, capacity, err);
+  else
+    k_compact<uint64_t><<<(unsigned)blocks, 256, 0, s>>>(buf, bs, counts, offsets, m, indices, capacity, err);
 }
 
 size_t scan_tmp_words(uint32_t m) { return (size_t)ceil_div<uint32_t>(m > 0 ? m : 1, (uint32_t)kScanTile) + 1; }
