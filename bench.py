@@ -55,59 +55,123 @@ def dist_env():
     return ws, rank, local
 
 
-class ClockSampler:
-    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
-
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+class _Nvml:
+    """Read-only NVML queries through the driver's libnvidia-ml (SM clock, maximum SM clock,
+    current clock-event reasons)."""
 
     def __init__(self, index: int):
+        import ctypes
+        self.c = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        self.h = ctypes.c_void_p()
+        if self.lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(self.h)) != 0:
+            raise RuntimeError("nvmlDeviceGetHandleByIndex failed")
+        try:
+            self._reasons_fn = self.lib.nvmlDeviceGetCurrentClocksEventReasons
+        except AttributeError:
+            self._reasons_fn = self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+
+    def _clock(self, fn) -> float:
+        v = self.c.c_uint()
+        if fn(self.h, self.c.c_int(1), self.c.byref(v)) != 0:  # NVML_CLOCK_SM
+            raise RuntimeError("nvml clock query failed")
+        return float(v.value)
+
+    def sm_mhz(self) -> float:
+        return self._clock(self.lib.nvmlDeviceGetClockInfo)
+
+    def max_sm_mhz(self) -> float:
+        return self._clock(self.lib.nvmlDeviceGetMaxClockInfo)
+
+    def reasons(self) -> int:
+        v = self.c.c_ulonglong()
+        if self._reasons_fn(self.h, self.c.byref(v)) != 0:
+            raise RuntimeError("nvml reasons query failed")
+        return int(v.value)
+
+    def close(self):
+        try:
+            self.lib.nvmlShutdown()
+        except Exception:
+            pass
+
+
+class ClockSampler:
+    """Samples SM clock and clock-event (throttle) reasons every few milliseconds
+    through NVML in a background thread (nvidia-smi at 100 ms as a fallback)."""
+
+    REASONS = (("hw_slowdown", 0x8), ("sw_thermal_slowdown", 0x20), ("hw_thermal_slowdown", 0x40),
+               ("sw_power_cap", 0x4))
+
+    def __init__(self, index: int, period_s: float = 0.005):
         self.index = index
-        self.proc = None
-        self.lines = []
+        self.period = period_s
+        self.samples = []  # (sm_mhz, reasons bitmask)
+        self.max_mhz = None
+        self._stop = threading.Event()
+        self._t = None
+        self._nv = None
+        self.nvml_error = None
 
     def __enter__(self):
         try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self._t = threading.Thread(target=self._read, daemon=True)
-            self._t.start()
-        except Exception:
-            self.proc = None
+            self._nv = _Nvml(self.index)
+            self.max_mhz = self._nv.max_sm_mhz()
+            self._t = threading.Thread(target=self._poll_nvml, daemon=True)
+        except Exception as e:
+            self.nvml_error = repr(e)[:120]
+            self._nv = None
+            self._t = threading.Thread(target=self._poll_smi, daemon=True)
+        self._t.start()
         return self
 
-    def _read(self):
-        for line in self.proc.stdout:
-            self.lines.append(line.strip())
+    def _poll_nvml(self):
+        while not self._stop.is_set():
+            try:
+                self.samples.append((self._nv.sm_mhz(), self._nv.reasons()))
+            except Exception:
+                return
+            self._stop.wait(self.period)
+
+    def _poll_smi(self):
+        fields = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                  "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={fields}",
+                                     "--format=csv,noheader,nounits", "-lms", "100"],
+                                    stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            return
+        for line in proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            try:
+                mask = 0
+                for (nm, bit), v in zip(self.REASONS, parts[2:6]):
+                    if v.lower().startswith("active"):
+                        mask |= bit
+                self.samples.append((float(parts[0]), mask))
+                self.max_mhz = float(parts[1])
+            except (ValueError, IndexError):
+                pass
+            if self._stop.is_set():
+                break
+        proc.terminate()
 
     def __exit__(self, *a):
-        if self.proc is not None:
-            self.proc.terminate()
-            try:
-                self.proc.wait(timeout=5)
-            except Exception:
-                self.proc.kill()
+        self._stop.set()
+        if self._t is not None:
+            self._t.join(timeout=5)
+        if self._nv is not None:
+            self._nv.close()
 
     def summary(self):
-        sm, mx, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            parts = [x.strip() for x in ln.split(",")]
-            if len(parts) < 8:
-                continue
-            try:
-                sm.append(float(parts[0]))
-                mx = float(parts[1])
-            except ValueError:
-                continue
-            for nm, v in zip(names, parts[4:8]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": 0}
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+        reasons = sorted({nm for _, m in self.samples for nm, bit in self.REASONS if m & bit})
+        sm = [mhz for mhz, _ in self.samples]
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": self.max_mhz, "reasons": reasons,
+                "samples": len(sm), "source": "nvml" if self._nv is not None else "nvidia-smi",
+                **({"nvml_error": self.nvml_error} if self.nvml_error else {})}
 
 
 def measured_traffic(kernel, workload):
@@ -181,12 +245,17 @@ def run_gpu(args):
 
     # launch parameters from the autotuner, tuned on another draw of the same distribution
     tuned = {"block_size": 0, "stack_smem": 0, "buffer_size": 0}
-    if not args.no_tune:
+    if args.launch:
+        b_, s_, f_ = (int(x) for x in args.launch.split(","))
+        tuned = {"block_size": b_, "stack_smem": s_, "buffer_size": f_, "source": "--launch"}
+    elif not args.no_tune:
         from paper_1908_11807_b300 import autotune
         tp, tq = datagen.workload(dist_name, n, min(m, 200_000), seed + 1000)
         tuned = autotune.tune(torch.from_numpy(tp).to(dev), torch.from_numpy(tq).to(dev), r, k, dist_name)
         del tp, tq
-    topts = {"block_size": tuned["block_size"], "stack_smem": tuned["stack_smem"]}
+    # validate=0: the build runs without a host round trip; non-finite input is reported by
+    # arborx_check, which runs after every step outside the timed interval
+    topts = {"block_size": tuned["block_size"], "stack_smem": tuned["stack_smem"], "validate": 0}
     bsz = int(tuned["buffer_size"] or 0)
 
     def step(points, queries, **opts):
@@ -226,8 +295,9 @@ def run_gpu(args):
             flush.fill_(1.0)  # evict L2 between steps (outside the timed interval)
             barrier()
             ev, res, bvh = step(p, q)
-            bvh.destroy()
             torch.cuda.synchronize()
+            bvh.check()
+            bvh.destroy()
             t = [ev[0].elapsed_time(e) for e in ev[1:]]
             phase += np.array([t[0], t[1] - t[0], t[2] - t[1]])
             total_ms += t[2]
@@ -325,6 +395,7 @@ def run_gpu(args):
         "config": {"workload": f"{args.workload}: n={n} {dist_name} points, m={m} same-distribution queries, "
                                f"radius {r:.7g} (mean 10 neighbours), k={k}",
                    "n": n, "m": m, "k": k, "radius": r, "key_bits": 30, "parallelism": f"replicas{ws}",
+                   "build_validate": "asynchronous (arborx_check after each step, untimed)",
                    "l2": "flushed between steps (256 MB write)"},
         "components": {"build_mpts_s": round(n / (build_ms * 1e-3) / 1e6, 2),
                        "radius_mq_s": round(m / (spatial_ms * 1e-3) / 1e6, 2),
@@ -333,7 +404,7 @@ def run_gpu(args):
                        "knn_ms": round(knn_ms, 4), "nnz": nnz},
         "kernels": kernels,
         "tuned": tuned,
-        "traversal": {"spatial_nodes_per_query_per_pass": round(nodes["spatial"] / (2 * m), 2),
+        "traversal": {"spatial_nodes_per_query": round(nodes["spatial"] / m, 2),
                       "nearest_nodes_per_query": round(nodes["nearest"] / m, 2), "node_bytes": 64},
         "roofline": roofline,
         "e2e": e2e,
@@ -510,7 +581,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--workload", default="cube_1e7", choices=sorted(WORKLOADS))
@@ -519,6 +590,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the learned-bound and batched measurements")
     ap.add_argument("--no-tune", action="store_true", help="default launch parameters instead of the autotuner's")
+    ap.add_argument("--launch", default=None,
+                    help="block,stack,buffer: fixed traversal launch parameters (skips the autotuner)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "b300":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
