@@ -36,6 +36,7 @@ struct arborx_batch_s {
   uint32_t *vA, *vB, *qvA, *qvB;
   float4 *rec;
   int32_t *other;
+  void *front;  // frontier list of the chunked hierarchy build
   uint32_t *queue;
   void *zero_base;
   size_t zero_bytes;
@@ -59,11 +60,13 @@ namespace {
 constexpr size_t kAl = 256;
 size_t al(size_t x) { return (x + kAl - 1) & ~(kAl - 1); }
 
+// Query class of a cloud's k: the register-list width for k <= 16, else 0 (the
+// shared-memory heap of up to 32 entries, faster than a 32-entry register list)
 int kc_of(int k) {
-  const int widths[] = {1, 2, 4, 8, 10, 16, 32};
+  const int widths[] = {1, 2, 4, 8, 10, 16};
   for (int w : widths)
     if (k <= w) return w;
-  return -1;
+  return k <= 32 ? 0 : -1;
 }
 
 int status_of(cudaError_t e) { return e == cudaSuccess ? ARBORX_OK : ARBORX_ECUDA; }
@@ -72,7 +75,6 @@ void enqueue(arborx_batch_s *b, const float *pts, const float *qs, cudaStream_t 
              int32_t *d_idx, float *d_d2) {
   const uint32_t N = (uint32_t)b->N, M = (uint32_t)b->M, C = (uint32_t)b->C;
   cudaMemsetAsync(b->zero_base, 0, b->zero_bytes, s);
-  if (N > 1) cudaMemsetAsync(b->other, 0xff, (size_t)(N - 1) * sizeof(int32_t), s);
   cudaMemsetAsync(b->root_slot, 0xff, (size_t)C * sizeof(int32_t), s);
   const uint64_t *skeys = nullptr;
   const uint32_t *sperm = nullptr;
@@ -82,7 +84,10 @@ void enqueue(arborx_batch_s *b, const float *pts, const float *qs, cudaStream_t 
     const bool inA = launch_onesweep<uint64_t>(b->kA, b->kB, b->vA, b->vB, N, b->wsp, b->err, s);
     skeys = inA ? b->kA : b->kB;
     sperm = inA ? b->vA : b->vB;
-    launch_apetrei_seg(pts, N, skeys, sperm, b->other, b->rec, b->sorted_off, b->root_slot, b->err, s);
+    // one binary radix tree over the (cloud, code) keys: the cloud id in the high bits makes every
+    // cloud one subtree; its root slot is found afterwards
+    launch_apetrei<uint64_t>(pts, N, ARBORX_POINTS, skeys, sperm, b->other, b->rec, b->front, b->err, s);
+    launch_seg_roots(skeys, N, b->sorted_off, C, b->root_slot, s);
   }
   if (d_row_offsets)
     cudaMemcpyAsync(d_row_offsets, b->row_off, (size_t)(M + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
@@ -199,7 +204,8 @@ int arborx_batch_create(int64_t n_clouds, const int64_t *h_point_offsets, const 
                o_pb = take(C * 4), o_nc = take(C * 4), o_kof = take(C * 4), o_root = take(C * 4),
                o_row = take((M + 1) * 8), o_scene = take(C * 6 * 4), o_kA = take(N * 8), o_kB = take(N * 8),
                o_vA = take(N * 4), o_vB = take(N * 4), o_qkA = take(M * 8), o_qkB = take(M * 8), o_qvA = take(M * 4),
-               o_qvB = take(M * 4), o_rec = take(rec_f4 * 16), o_other = take((N > 1 ? N - 1 : 1) * 4);
+               o_qvB = take(M * 4), o_rec = take(rec_f4 * 16), o_other = take((N > 1 ? N - 1 : 1) * 4),
+               o_front = take(apetrei_front_bytes((uint32_t)N));
   const size_t o_zero = bytes;
   const size_t o_wsp = take(wsp_words * 4), o_wsq = take(wsq_words * 4), o_queue = take(nclass * 4),
                o_err = take(4);
@@ -233,6 +239,7 @@ int arborx_batch_create(int64_t n_clouds, const int64_t *h_point_offsets, const 
   b->qvB = (uint32_t *)(base + o_qvB);
   b->rec = (float4 *)(base + o_rec);
   b->other = (int32_t *)(base + o_other);
+  b->front = base + o_front;
   b->zero_base = base + o_zero;
   b->wsp = sort_ws_carve<uint64_t>((uint32_t *)(base + o_wsp), N, key_bits);
   b->wsq = sort_ws_carve<uint64_t>((uint32_t *)(base + o_wsq), M, key_bits);

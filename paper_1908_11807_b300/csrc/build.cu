@@ -671,76 +671,31 @@ __global__ void __launch_bounds__(256) k_seg_morton(const float *__restrict__ pt
   }
 }
 
-// Single bottom-up pass over all clouds at once (one tree whose top levels
-// separate the clouds); additionally records, for every cloud, the record slot
-// describing the subtree that holds exactly its points (sorted positions
-// [sorted_off[c], sorted_off[c+1]) ).
-__global__ void __launch_bounds__(256) k_apetrei_seg(const float *__restrict__ prims, uint32_t n,
-                                                    const uint64_t *__restrict__ codes,
-                                                    const uint32_t *__restrict__ perm, int32_t *__restrict__ other,
-                                                    float4 *__restrict__ rec, const uint32_t *__restrict__ sorted_off,
-                                                    int32_t *__restrict__ root_slot, uint32_t *__restrict__ err) {
-  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n) return;
-  const uint32_t prim = perm[t];
-  const float *pp = prims + 3 * (uint64_t)prim;
-  float lx = pp[0], ly = pp[1], lz = pp[2];
-  float hx = lx, hy = ly, hz = lz;
-  int enc = ~(int)prim;
-  int pending = -1;  // cloud whose root is the current node
-  {
-    const uint32_t c = (uint32_t)(__ldg(codes + t) >> 30);
-    if (__ldg(sorted_off + c + 1) - __ldg(sorted_off + c) == 1) pending = (int)c;
-  }
-  if (n == 1) {
-    rec[0] = make_float4(lx, ly, lz, __int_as_float(enc));
-    rec[1] = make_float4(hx, hy, hz, 0.0f);
-    if (pending >= 0) root_slot[pending] = 0;
+// Root slot of every cloud in the tree over the (cloud, code) keys: the cloud
+// owns sorted positions [a, b]; the node covering exactly that range hangs in
+// its parent's record at split b (left child) when the keys share a longer
+// prefix across b | b+1 than across a-1 | a, else at split a - 1 (right
+// child) -- the parent rule of the build.  The whole range [0, N - 1] is the
+// root (record slot 0).  Empty clouds get -1.
+__global__ void __launch_bounds__(256) k_seg_roots(const uint64_t *__restrict__ codes, uint32_t n,
+                                                  const uint32_t *__restrict__ sorted_off, uint32_t n_clouds,
+                                                  int32_t *__restrict__ root_slot) {
+  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_clouds) return;
+  const int a = (int)sorted_off[c], b = (int)sorted_off[c + 1] - 1, N = (int)n;
+  if (b < a) {
+    root_slot[c] = -1;
     return;
   }
-  const int N = (int)n;
-  int l = (int)t, r = (int)t;
-  for (int level = 0;; ++level) {
-    bool left_child;
-    if (l == 0) {
-      left_child = true;
-    } else if (r == N - 1) {
-      left_child = false;
-    } else {
-      const uint64_t cl = __ldg(codes + l), cr = __ldg(codes + r);
-      left_child = delta<uint64_t>(codes, cr, r, r + 1, N) > delta<uint64_t>(codes, cl, l, l - 1, N);
-    }
-    const int p = left_child ? r : l - 1;
-    if (p < 0 || p >= N - 1 || level > 160) {
-      set_err(err, ERR_STACK);
-      return;
-    }
-    const int slot_id = 2 + 2 * p + (left_child ? 0 : 1);
-    if (pending >= 0) {
-      root_slot[pending] = slot_id;
-      pending = -1;
-    }
-    float4 *slot = rec + 2 * (uint64_t)slot_id;
-    slot[0] = make_float4(lx, ly, lz, __int_as_float(enc));
-    slot[1] = make_float4(hx, hy, hz, 0.0f);
-    const int got = atom_exch_acq_rel_gpu(other + p, left_child ? l : r);
-    if (got < 0) return;
-    if (left_child) r = got;
-    else l = got;
-    const float4 *sib = rec + 4 + 4 * (uint64_t)p + (left_child ? 2 : 0);
-    const float4 slo = ld_cg_f4(sib), shi = ld_cg_f4(sib + 1);
-    lx = fminf(lx, slo.x); ly = fminf(ly, slo.y); lz = fminf(lz, slo.z);
-    hx = fmaxf(hx, shi.x); hy = fmaxf(hy, shi.y); hz = fmaxf(hz, shi.z);
-    enc = p;
-    const uint32_t c = (uint32_t)(__ldg(codes + l) >> 30);
-    if ((uint32_t)l == __ldg(sorted_off + c) && (uint32_t)r + 1 == __ldg(sorted_off + c + 1)) pending = (int)c;
-    if (l == 0 && r == N - 1) {
-      rec[0] = make_float4(lx, ly, lz, __int_as_float(p));
-      rec[1] = make_float4(hx, hy, hz, 0.0f);
-      if (pending >= 0) root_slot[pending] = 0;
-      return;
-    }
+  if (a == 0 && b == N - 1) {
+    root_slot[c] = 0;
+    return;
   }
+  const int dr = delta<uint64_t>(codes, codes[b], b, b + 1, N);
+  const int dl = a > 0 ? delta<uint64_t>(codes, codes[a - 1], a - 1, a, N) : -1;
+  const bool left_child = dr > dl;
+  const int p = left_child ? b : a - 1;
+  root_slot[c] = 2 + 2 * p + (left_child ? 0 : 1);
 }
 
 int sm_count() {
@@ -829,12 +784,11 @@ void launch_seg_morton(const float *pts, uint32_t count, const uint32_t *off, ui
   k_seg_morton<<<blocks, 256, 0, s>>>(pts, count, off, n_clouds, cmap, seg_scene, keys, hist, passes);
 }
 
-void launch_apetrei_seg(const float *prims, uint32_t n, const uint64_t *codes, const uint32_t *perm, int32_t *other,
-                        float4 *rec, const uint32_t *sorted_off, int32_t *root_slot, uint32_t *err, cudaStream_t s) {
-  if (n == 0) return;
-  prof::Scope ps(s, "apetrei_seg");
-  k_apetrei_seg<<<ceil_div<uint32_t>(n, 256u), 256, 0, s>>>(prims, n, codes, perm, other, rec, sorted_off, root_slot,
-                                                            err);
+void launch_seg_roots(const uint64_t *codes, uint32_t n, const uint32_t *sorted_off, uint32_t n_clouds,
+                      int32_t *root_slot, cudaStream_t s) {
+  if (n_clouds == 0 || n == 0) return;
+  prof::Scope ps(s, "seg_roots");
+  k_seg_roots<<<ceil_div<uint32_t>(n_clouds, 256u), 256, 0, s>>>(codes, n, sorted_off, n_clouds, root_slot);
 }
 
 template void launch_apetrei<uint32_t>(const float *, uint32_t, int, const uint32_t *, const uint32_t *, int32_t *,

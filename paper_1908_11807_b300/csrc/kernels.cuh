@@ -24,8 +24,9 @@ void launch_seg_bounds(const float *pts, const uint32_t *off, uint32_t n_clouds,
                        cudaStream_t s);
 void launch_seg_morton(const float *pts, uint32_t count, const uint32_t *off, uint32_t n_clouds, const uint32_t *cmap,
                        const float *seg_scene, uint64_t *keys, uint32_t *hist, int passes, cudaStream_t s);
-void launch_apetrei_seg(const float *prims, uint32_t n, const uint64_t *codes, const uint32_t *perm, int32_t *other,
-                        float4 *rec, const uint32_t *sorted_off, int32_t *root_slot, uint32_t *err, cudaStream_t s);
+// root record slot of every cloud in the tree over (cloud, code) keys (-1 for an empty cloud)
+void launch_seg_roots(const uint64_t *codes, uint32_t n, const uint32_t *sorted_off, uint32_t n_clouds,
+                      int32_t *root_slot, cudaStream_t s);
 void launch_fit(const float *prims, uint32_t n, int kind, const uint32_t *perm, const int32_t *parent,
                 uint32_t *arrival, float4 *rec, uint32_t *err, cudaStream_t s);
 

@@ -23,6 +23,15 @@ namespace {
 
 constexpr int kSpill = 96;     // local-memory stack entries beyond the shared part
 constexpr int kMaxBlock = 256;  // traversal block size limit (register budget)
+#ifndef ABX_HEAP_DEFER
+#define ABX_HEAP_DEFER 8
+#endif
+#ifndef ABX_HEAP_FROM
+#define ABX_HEAP_FROM 17
+#endif
+constexpr int kHeapDefer = ABX_HEAP_DEFER;  // deferred-insert buffer of the shared-memory heap path
+constexpr int kHeapFrom = ABX_HEAP_FROM;    // smallest k served by the shared-memory heap
+constexpr int kBatchHeapK = 32;             // largest k of the batched path (heap class)
 
 __device__ __forceinline__ bool finite3(float x, float y, float z) {
   return is_finite_bits(x) && is_finite_bits(y) && is_finite_bits(z);
@@ -286,13 +295,13 @@ struct SmemHeap {
     kd = hd[0];
     ki = hi[0];
   }
-  __device__ __forceinline__ void write(int64_t row, int kk, int32_t *out_idx, float *out_d2) {
+  __device__ __forceinline__ void write(int64_t row, int kk, int32_t *out_idx, float *out_d2, int32_t base = 0) {
     for (int j = k - 1; j >= 0; --j) {
       const float d = hd[0];
       const int32_t i = hi[0];
       if (j < kk) {
         const bool real = i != INT_MAX;
-        out_idx[row + j] = real ? i : -1;
+        out_idx[row + j] = real ? i - base : -1;
         if (out_d2) out_d2[row + j] = real ? d : __int_as_float(0x7f800000);
       }
       if (j > 0) sift(hd[j * s], hi[j * s], j);
@@ -300,7 +309,13 @@ struct SmemHeap {
   }
 };
 
-template <class List>
+// DEFER > 0: accepted leaf candidates wait in a DEFER-entry register buffer and
+// enter the list when some lane of the warp has a nearly full buffer, all
+// lanes together (and at the end).  Pruning meanwhile uses the list's bound,
+// which can only be larger than with every candidate inserted, so no node that
+// holds a result is skipped and every candidate still reaches the list once.
+// It pays for the shared-memory heap, whose data-dependent sift loop diverges.
+template <int DEFER, class List>
 __device__ __forceinline__ void knn_traverse(const float4 *__restrict__ rec, uint32_t n, float qx, float qy, float qz, List &L,
                                              int k, int32_t *s_node, float *s_dist, int stride, int stack_smem,
                                              uint32_t *err, uint32_t &visited, uint32_t root_slot = 0) {
@@ -316,6 +331,30 @@ __device__ __forceinline__ void knn_traverse(const float4 *__restrict__ rec, uin
   float spd[kSpill];
   int sp = 0;
   int node = e0;
+  constexpr int DB = DEFER > 0 ? DEFER : 1;
+  float bd[DB];
+  int32_t bi[DB];
+  int bc = 0;
+  auto offer = [&](float d, int32_t i) {
+    if constexpr (DEFER > 0) {
+#pragma unroll
+      for (int j = DB - 1; j > 0; --j) {
+        bd[j] = bd[j - 1];
+        bi[j] = bi[j - 1];
+      }
+      bd[0] = d;
+      bi[0] = i;
+      ++bc;
+    } else {
+      L.insert(d, i, k);
+    }
+  };
+  auto flush = [&]() {
+#pragma unroll
+    for (int j = 0; j < DB; ++j)
+      if (j < bc && L.accepts(bd[j], bi[j])) L.insert(bd[j], bi[j], k);
+    bc = 0;
+  };
   while (true) {
     if ((uint32_t)node >= n - 1) {  // corrupt tree: never read outside the records
       set_err(err, ERR_STACK);
@@ -327,8 +366,11 @@ __device__ __forceinline__ void knn_traverse(const float4 *__restrict__ rec, uin
     const float dl = dist2_box(qx, qy, qz, a0, a1);
     const float dr = dist2_box(qx, qy, qz, b0, b1);
     const int el = __float_as_int(a0.w), er = __float_as_int(b0.w);
-    if (el < 0 && L.accepts(dl, ~el)) L.insert(dl, ~el, k);
-    if (er < 0 && L.accepts(dr, ~er)) L.insert(dr, ~er, k);
+    if (el < 0 && L.accepts(dl, ~el)) offer(dl, ~el);
+    if (er < 0 && L.accepts(dr, ~er)) offer(dr, ~er);
+    if constexpr (DEFER > 0) {
+      if (__any_sync(__activemask(), bc > DB - 2)) flush();
+    }
     const bool gl = el >= 0 && dl <= L.bound();  // prune only when strictly farther than the k-th
     const bool gr = er >= 0 && dr <= L.bound();
     if (gl && gr) {
@@ -367,6 +409,7 @@ __device__ __forceinline__ void knn_traverse(const float4 *__restrict__ rec, uin
       if (node < 0) break;
     }
   }
+  if constexpr (DEFER > 0) flush();
 }
 
 // Upper bound on the k-th squared distance of query q taken from a finished row
@@ -422,7 +465,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_nearest(const __grid_constant__ N
   if constexpr (KC > 0) {
     RegList<KC> L;
     L.init(b0, k);
-    if (ok && n > 0) knn_traverse(rec, n, qx, qy, qz, L, k, s_node, s_dist, B, stack_smem, err, visited);
+    if (ok && n > 0) knn_traverse<0>(rec, n, qx, qy, qz, L, k, s_node, s_dist, B, stack_smem, err, visited);
     if (a.miss_list) append_flagged(ok && L.bound_idx() == INT_MAX, pos, a.miss_list, a.miss_count);
     L.write(row, kk, out_idx, out_d2);
   } else {
@@ -432,7 +475,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_nearest(const __grid_constant__ N
     H.s = B;
     H.k = k;
     H.init(b0, k);
-    if (ok && n > 0) knn_traverse(rec, n, qx, qy, qz, H, k, s_node, s_dist, B, stack_smem, err, visited);
+    if (ok && n > 0) knn_traverse<kHeapDefer>(rec, n, qx, qy, qz, H, k, s_node, s_dist, B, stack_smem, err, visited);
     if (a.miss_list) append_flagged(ok && H.bound_idx() == INT_MAX, pos, a.miss_list, a.miss_count);
     H.write(row, kk, out_idx, out_d2);
   }
@@ -441,7 +484,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_nearest(const __grid_constant__ N
 
 // Batched clouds: persistent warps take tiles of 32 sorted query positions from
 // an atomic counter; each query starts at its cloud's subtree root and returns
-// indices local to its cloud.
+// indices local to its cloud.  KC = 0: shared-memory heap for k up to kBatchHeapK.
 template <int KC>
 __global__ void __launch_bounds__(kMaxBlock) k_batch_nearest(const __grid_constant__ BatchQueryArgs a) {
   extern __shared__ unsigned char s_raw[];
@@ -464,12 +507,27 @@ __global__ void __launch_bounds__(kMaxBlock) k_batch_nearest(const __grid_consta
       const float qx = __ldg(a.queries + 3 * (uint64_t)qi);
       const float qy = __ldg(a.queries + 3 * (uint64_t)qi + 1);
       const float qz = __ldg(a.queries + 3 * (uint64_t)qi + 2);
-      RegList<KC> L;
-      L.init(__int_as_float(0x7f800000), k);
       uint32_t visited = 0;
-      if (finite3(qx, qy, qz) && slot >= 0)
-        knn_traverse(a.rec, a.n, qx, qy, qz, L, k, s_node, s_dist, B, a.stack_smem, a.err, visited, (uint32_t)slot);
-      L.write(__ldg(a.row_off + qi), kk, a.out_idx, a.out_d2, (int32_t)__ldg(a.prim_base + c));
+      const bool go = finite3(qx, qy, qz) && slot >= 0;
+      if constexpr (KC > 0) {
+        RegList<KC> L;
+        L.init(__int_as_float(0x7f800000), k);
+        if (go)
+          knn_traverse<0>(a.rec, a.n, qx, qy, qz, L, k, s_node, s_dist, B, a.stack_smem, a.err, visited,
+                          (uint32_t)slot);
+        L.write(__ldg(a.row_off + qi), kk, a.out_idx, a.out_d2, (int32_t)__ldg(a.prim_base + c));
+      } else {
+        SmemHeap H;
+        H.hd = reinterpret_cast<float *>(s_raw) + (size_t)2 * a.stack_smem * B + threadIdx.x;
+        H.hi = reinterpret_cast<int32_t *>(s_raw) + (size_t)(2 * a.stack_smem + kBatchHeapK) * B + threadIdx.x;
+        H.s = B;
+        H.k = k;
+        H.init(__int_as_float(0x7f800000), k);
+        if (go)
+          knn_traverse<kHeapDefer>(a.rec, a.n, qx, qy, qz, H, k, s_node, s_dist, B, a.stack_smem, a.err, visited,
+                                   (uint32_t)slot);
+        H.write(__ldg(a.row_off + qi), kk, a.out_idx, a.out_d2, (int32_t)__ldg(a.prim_base + c));
+      }
     }
   }
 }
@@ -663,8 +721,17 @@ static void nearest_kc(dim3 grid, int block, size_t smem, cudaStream_t s, const 
 
 int launch_batch_nearest(const BatchQueryArgs &a, int kc, const TravCfg &cfg, cudaStream_t s) {
   if (a.pos_end <= a.pos_begin) return 0;
-  const int block = cfg.block;
-  const size_t smem = (size_t)2 * a.stack_smem * block * sizeof(int32_t);
+  // the heap class runs 64-thread blocks at most (its shared heap limits the resident blocks)
+  const int block = kc == 0 ? std::min(cfg.block, 64) : cfg.block;
+  size_t smem = (size_t)2 * a.stack_smem * block * sizeof(int32_t);
+  if (kc == 0) {
+    smem += (size_t)2 * kBatchHeapK * block * sizeof(int32_t);
+    if (smem > 227 * 1024) return -1;
+    if (smem > 48 * 1024) {
+      cudaFuncSetAttribute(k_batch_nearest<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(k_batch_nearest<0>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    }
+  }
   int dev = 0, sms = 148, per_sm = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -677,13 +744,13 @@ int launch_batch_nearest(const BatchQueryArgs &a, int kc, const TravCfg &cfg, cu
     k_batch_nearest<KC><<<grid, block, smem, s>>>(a);                                                   \
   } while (0)
   switch (kc) {
+    case 0: ABX_BATCH(0); break;
     case 1: ABX_BATCH(1); break;
     case 2: ABX_BATCH(2); break;
     case 4: ABX_BATCH(4); break;
     case 8: ABX_BATCH(8); break;
     case 10: ABX_BATCH(10); break;
     case 16: ABX_BATCH(16); break;
-    case 32: ABX_BATCH(32); break;
     default: return -1;
   }
 #undef ABX_BATCH
@@ -698,8 +765,8 @@ int launch_nearest(NearestArgs a, const TravCfg &cfg, cudaStream_t s) {
   const uint32_t threads = a.m + 1;
   int block = cfg.block;
   size_t smem = (size_t)2 * cfg.stack_smem * block * sizeof(int32_t);
-  // k > 32: candidates in a shared-memory heap (a 64-entry register list measured 2x slower at k = 50)
-  const bool use_heap = k > 32;
+  // large k: candidates in a shared-memory heap (a 64-entry register list measured 2x slower at k = 50)
+  const bool use_heap = k >= kHeapFrom;
   if (use_heap) {
     // heap of k pairs per thread in shared memory: shrink the block to fit
     while (block > 32 && smem + (size_t)2 * k * block * sizeof(int32_t) > 200 * 1024) {
