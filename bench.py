@@ -199,7 +199,8 @@ def measured_peaks():
         return 6400.0, "fallback"
 
 
-# algorithmic bytes per unit of each kernel (the design doc states the derivation)
+# algorithmic bytes per unit of each kernel: compulsory reads and writes of one launch, plus
+# 64 bytes per internal node a traversal loads (counted by an instrumented untimed run)
 def kernel_bytes(name, n, m, k, nnz, nodes):
     """Algorithmic DRAM bytes of all launches of `name` in one step."""
     passes = 4  # 30-bit keys, 8-bit digits
@@ -210,7 +211,7 @@ def kernel_bytes(name, n, m, k, nnz, nodes):
         "onesweep_pass": sort_b(n) + sort_b(m),
         "hierarchy": 12 * n,                        # codes read, parent links written
         "fit": 52 * n + 76 * max(n - 1, 0),         # gather + leaf record, then per internal node
-        "apetrei": 48 * n + 80 * max(n - 1, 0),     # gather + leaf record, then per internal node
+        "apetrei": 52 * n + 32 * max(n - 1, 0),     # perm + code + gathered point + leaf slot; node slot
         "scan": 12 * m + 8,                         # counts read twice, offsets written
         "spatial_count": 20 * m + 64 * nodes.get("spatial", 0) // 2,
         "spatial_fill": 28 * m + 4 * nnz + 64 * nodes.get("spatial", 0) // 2,
