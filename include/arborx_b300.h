@@ -117,7 +117,7 @@ ARBORX_API int arborx_default_opts(arborx_opts *opts);
  * stable radix sort of (code, index) pairs, the binary radix-tree hierarchy
  * split at the highest differing bit of the index-augmented codes (Karras
  * 2012), and the bottom-up box fit in which the second thread to reach a node
- * continues (Sec. 2.1, "Calculate internal nodes bounding boxes").
+ * continues (Sec. 2.1, internal-node boxes).
  *   d_prims  device float[n][3] (ARBORX_POINTS) or float[n][6] (ARBORX_BOXES); read only during the
  *            build's stream work; may be freed once that work completes (the tree keeps its own copy
  *            of every primitive box)

@@ -98,8 +98,8 @@ def scene_box(prims: np.ndarray) -> Tuple[np.ndarray, int]:
 
 
 def morton(prims: np.ndarray, sb: np.ndarray, key_bits: int = 30) -> np.ndarray:
-    """Morton codes of the centroids scaled by the scene box (Sec. 2.1, "Assign
-    Morton codes"): 30-bit (10 bits / axis) or 63-bit (21 bits / axis), uint64."""
+    """Morton codes of the centroids scaled by the scene box (Sec. 2.1, Morton
+    code step): 30-bit (10 bits / axis) or 63-bit (21 bits / axis), uint64."""
     prims = _c(prims, np.float32)
     sb = _c(sb, np.float32)
     bits = {30: 10, 63: 21}[key_bits]

@@ -7,17 +7,18 @@
  * (no FMA contraction, so every float expression rounds exactly as written).
  *
  * What it computes (ArborX, arXiv 1908.11807):
- *   - scene bounding box: min / max over all box corners (Sec. 2.1, "Calculate
- *     the scene bounding box");
+ *   - scene bounding box: min / max over all box corners (Sec. 2.1, scene box
+ *     step);
  *   - Morton codes of box centroids scaled by the scene box into [0,1]^3,
  *     30-bit (10 bits per axis) and 63-bit (21 bits per axis), bits
- *     interleaved x-major (Sec. 2.1, "Assign Morton codes");
+ *     interleaved x-major (Sec. 2.1, Morton code step);
  *   - spatial query: every primitive whose AABB lies within distance r of the
  *     query point (Sec. 2.2, "Traversal for spatial queries"), read as the
  *     closed ball d^2 <= fl32(r*r);
  *   - nearest query: the min(k, n) primitives closest to the query point, ties
  *     broken by lower index, rows ordered by (d^2, index) (Sec. 2.2, "Traversal
- *     for nearest queries"; fewer than k when n < k, the paper's "purging").
+ *     for nearest queries"; fewer than k when n < k, as the paper drops missing
+ *     entries).
  *
  * Distance arithmetic (the reading used on both sides): per axis the gap
  * g = lo - q if q < lo, q - hi if q > hi, else 0 (for a point p: g = q - p);

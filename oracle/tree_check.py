@@ -4,17 +4,14 @@ Checks a tree exported by the library against what the paper's construction
 fixes (Sec. 2, Sec. 2.1), independently of how the tree was built:
 
 * a binary tree over n leaves has n - 1 internal nodes, every node reachable
-  from the root exactly once (Sec. 2, "number of internal nodes ... equal to
-  the number of leaf nodes decreased by one");
-* the root box is the scene box (Sec. 2, the root "corresponds to the bounding
-  volume around all objects");
+  from the root exactly once (Sec. 2: one internal node fewer than leaves);
+* the root box is the scene box (Sec. 2: the root bounds every object);
 * every node box is the union of its children's boxes, leaves hold their
-  primitive's box (Sec. 2.1, "Calculate internal nodes bounding boxes");
+  primitive's box (Sec. 2.1, the bottom-up box step);
 * leaves are ordered by Morton code, the codes of the leaves are
   non-decreasing, the permutation is a permutation, and each internal node
   covers a contiguous range of sorted leaves split at the highest differing
-  bit of the index-augmented code (Sec. 2.1, "Sort ...", "Generate the
-  bounding volume hierarchy").
+  bit of the index-augmented code (Sec. 2.1, sort and hierarchy steps).
 
 Exported layout being checked (the library's documented format): ``records``
 float32 [2 + 2 (n - 1)][8]; a record is (lo.x, lo.y, lo.z, enc, hi.x, hi.y,

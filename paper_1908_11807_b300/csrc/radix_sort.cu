@@ -84,20 +84,32 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(const K *__restric
     }
   }
 
-  // warp-level ranking in input order (item-major, lane-minor): the lowest lane
-  // of each group of equal digits adds the group size to the warp's counter
-  // and hands the previous count to its peers; the warp's shared-memory
-  // atomics execute in program order, so item i is counted before item i + 1
+  // warp-level ranking in input order (item-major, lane-minor): the lanes
+  // holding the same digit are found with one ballot per digit bit (cheaper
+  // than match.any when most of the 32 digits differ); the lowest lane of
+  // each group adds the group size to the warp's counter and hands the
+  // previous count to its peers; items are counted in order
   const uint32_t lt = lanemask_lt();
 #pragma unroll
   for (int i = 0; i < ITEMS; ++i) {
     const uint32_t pos = wbase + i * 32 + lane;
     const bool valid = pos < n;
     const uint32_t d = valid ? (uint32_t)(k[i] >> shift) & (kRadix - 1) : (uint32_t)kRadix;
-    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    uint32_t peers = __ballot_sync(0xffffffffu, valid);
+    if (!valid) peers = ~peers;
+#pragma unroll
+    for (int b = 0; b < kRadixBits; ++b) {
+      const bool bit = (d >> b) & 1u;
+      const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+      peers &= bit ? bal : ~bal;
+    }
     const int leader = __ffs(peers) - 1;
     uint32_t old = 0;
-    if (valid && (int)lane == leader) old = atomicAdd(&s_whist[warp][d], (uint32_t)__popc(peers));
+    if (valid && (int)lane == leader) {  // the warp's own counters, one leader per digit: no atomic needed
+      old = s_whist[warp][d];
+      s_whist[warp][d] = old + (uint32_t)__popc(peers);
+    }
+    __syncwarp();  // item i's counter update is visible to every lane before item i + 1 reads
     old = __shfl_sync(0xffffffffu, old, leader);
     rk[i] = old + __popc(peers & lt);
   }

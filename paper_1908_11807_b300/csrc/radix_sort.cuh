@@ -1,15 +1,15 @@
 // Onesweep LSD radix sort of (key, index) pairs -- the sort step of the LBVH
-// build (ArborX Sec. 2.1, "Sort the bounding boxes using their Morton code").
+// build (ArborX Sec. 2.1, the sort by Morton code).
 //
 // Design (B300): 8-bit digits; the digit histograms of all passes come from
 // one read of the keys (fused into the Morton-code kernel, or the standalone
 // histogram kernel); each pass is one kernel in which a block takes the next
-// tile id from an atomic counter, ranks its keys per warp with match.any,
+// tile id from an atomic counter, ranks its keys per warp with digit-bit ballots,
 // publishes its per-digit counts, obtains the counts of all earlier tiles by
 // decoupled look-back over 30-bit status words (bounded spin, error flag on
 // give-up), stages the tile in shared memory in digit order and writes it out
 // in runs.  Stable: ties keep input order, so equal codes end up ordered by
-// index -- the paper's "augmented with an index".
+// index, the paper's tie rule for equal codes.
 #pragma once
 
 #include "common.cuh"
