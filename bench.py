@@ -43,6 +43,7 @@ WORKLOADS = {
     "cube_1e7": ("cube", 10_000_000, 1_000_000, 10),
     "hollow_sphere_1e7": ("hollow_sphere", 10_000_000, 1_000_000, 10),
     "cube_1e6": ("cube", 1_000_000, 1_000_000, 10),
+    "cube_1e4": ("cube", 10_000, 10_000, 10),  # the small oracle-sized case (host tests)
 }
 
 
@@ -53,6 +54,17 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def max_over_ranks(x: float, ws: int, device) -> float:
+    """Largest value of x over all ranks (the slowest rank's time); x itself when ws == 1."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 class _Nvml:
@@ -307,11 +319,7 @@ def run_gpu(args):
     ab.profile_enable(False)
     clocks = clk.summary()
 
-    step_ms = total_ms / args.steps
-    if ws > 1:
-        tt = torch.tensor([step_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        step_ms = float(tt.item())
+    step_ms = max_over_ranks(total_ms / args.steps, ws, dev)
     value = ws * 2 * m / (step_ms * 1e-3) / 1e6
     build_ms, spatial_ms, knn_ms = phase / args.steps
 
@@ -355,11 +363,7 @@ def run_gpu(args):
             torch.cuda.synchronize()
             e2e_ms += e0.elapsed_time(e1)
             d2h = (m + 1) * 8 + got * 4 + m * kk * 8
-        e2e_ms /= args.steps
-        if ws > 1:
-            tt = torch.tensor([e2e_ms], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e2e_ms = float(tt.item())
+        e2e_ms = max_over_ranks(e2e_ms / args.steps, ws, dev)
         e2e_value = ws * 2 * m / (e2e_ms * 1e-3) / 1e6
 
         e2e = {"value": round(e2e_value, 3), "unit": UNIT, "ms_per_step": round(e2e_ms, 4),
