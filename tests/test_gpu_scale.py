@@ -32,6 +32,12 @@ def _sub_csr(off, idx, rows):
     return sub_off, sub_idx
 
 
+# the benchmark's step: fixed launch parameters (block 64, 16 shared stack entries), asynchronous
+# validation, one query order shared by a one-pass spatial query (32-slot rows) and the k-NN query
+BENCH_LAUNCH = dict(block_size=64, stack_smem=16, validate=0)
+BENCH_BUFFER = 32
+
+
 @pytest.mark.parametrize("dist,n", [("cube", 1_000_000), ("hollow_sphere", 1_000_000),
                                     ("cube", 10_000_000), ("hollow_sphere", 10_000_000)])
 def test_paper_scale_sampled_exact(dist, n):
@@ -39,10 +45,15 @@ def test_paper_scale_sampled_exact(dist, n):
     m = 1_000_000
     p, q = datagen.workload(dist, n, m, S2)
     r = datagen.radius_for_mean(n, dist)
-    bvh = ab.BVH(dev(p))
-    og, ig = bvh.query_spatial(dev(q), r)
-    kg, dg = bvh.query_nearest(dev(q), 10)
+    bvh = ab.BVH(dev(p), **BENCH_LAUNCH)
+    qd = dev(q)
+    order = bvh.query_order(qd)
+    og, ig = bvh.query_spatial(qd, r, order=order, buffer_size=BENCH_BUFFER)
+    kg, dg = bvh.query_nearest(qd, 10, order=order)
     bvh.check()
+    # the two-pass scheme returns the same CSR arrays (same traversal order)
+    og2, ig2 = bvh.query_spatial(qd, r, order=order)
+    assert bool((og2 == og).all()) and bool((ig2 == ig).all())
     og, ig, kg, dg = host(og), host(ig), host(kg), host(dg)
     # every row: CSR well formed, nearest rows sorted by (d2, index), distinct
     assert og[0] == 0 and np.all(np.diff(og) >= 0) and og[-1] == ig.size
@@ -141,3 +152,29 @@ def test_lattice_256_all_sites():
     bnd = np.nonzero(~interior)[0][:150]
     ko, do = oracle.nearest_brute(pts, q[bnd], 27)
     assert_nearest_equal(kg[bnd], dg[bnd], ko, do)
+
+
+def test_learned_full_size_sampled_exact():
+    # the learned-bound workload at its full point count (1e7 Gaussian-mixture points; 1e6 of the
+    # 1e7 queries), the regressor trained by the library on 1e5 labels: sampled rows exact
+    ab = _ab()
+    import torch
+    from oracle import mlp
+    n, m = 10_000_000, 1_000_000
+    seed = datagen.SEED0 + 5
+    p = datagen.gaussian_mixture(n, seed)
+    q = datagen.gaussian_mixture(m, seed, datagen.STREAM_QUERIES)
+    qt = datagen.gaussian_mixture(100_000, seed, datagen.STREAM_TRAIN)
+    bvh = ab.BVH(dev(p), **BENCH_LAUNCH)
+    params = dev(mlp.he_init(np.random.default_rng(5)).astype(np.float32))
+    bvh.mlp_train(params, dev(qt), 10, epochs=20, batch=1024, lr=3e-3, lr_final=3e-5)
+    qd = dev(q)
+    order = bvh.query_order(qd)
+    li, ld, fb = bvh.query_nearest_learned(qd, 10, params, 0.35, order=order, count_fallbacks=True)
+    pi, pd = bvh.query_nearest(qd, 10, order=order)
+    bvh.check()
+    assert torch.equal(li, pi) and torch.equal(ld, pd)
+    assert 0 < fb < m
+    rows = np.sort(np.random.default_rng(7).choice(m, 10_000, replace=False))
+    ko, do = oracle.CpuBVH(p).nearest(q[rows], 10)
+    assert_nearest_equal(host(li)[rows], host(ld)[rows], ko, do)
