@@ -464,7 +464,7 @@ def learned_extra(ab, dev):
                                g.standard_normal(64) * np.sqrt(1 / 64), np.zeros(1)]).astype(np.float32)
         params = torch.from_numpy(init).to(dev)
         t0 = time.perf_counter()
-        loss = bvh.mlp_train(params, qt, k, epochs=60, batch=1024, lr=3e-3, lr_final=3e-5)
+        loss = bvh.mlp_train(params, qt, k, epochs=400, batch=2048, lr=5e-3, lr_final=1e-5)
         torch.cuda.synchronize()
         train_s = time.perf_counter() - t0
         sub = q[:1_000_000]
