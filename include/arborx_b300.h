@@ -199,6 +199,21 @@ ARBORX_API int arborx_query_spatial_buffered_fill(arborx_handle h, const float *
                                                   void *stream, const int64_t *d_offsets, int32_t *d_indices,
                                                   int64_t capacity);
 
+/* One-pass spatial query in a single call with no host synchronisation (graph-capturable): the
+ * count traversal with the `buffer_size` row buffer, the scan, the compaction and the second
+ * traversal of the overflowing rows, all enqueued on `stream`.  d_offsets[m] receives the total
+ * on the device.  Rows are written into caller-owned d_indices of `capacity` entries; entries at
+ * positions >= capacity are not written and set the CSR-overflow error reported as
+ * ARBORX_EOVERFLOW by arborx_check (the offsets stay complete, so the caller can size a new
+ * buffer from d_offsets[m] and repeat).  Results equal those of arborx_query_spatial.
+ *   buffer_size  1 <= buffer_size <= ARBORX_MAX_BUFFER_SIZE
+ *   d_order      NULL or a traversal order from arborx_query_order
+ *   d_offsets    device int64[m + 1]
+ *   d_indices    device int32[capacity] (NULL when capacity == 0) */
+ARBORX_API int arborx_query_spatial_buffered(arborx_handle h, const float *d_queries, int64_t m, float radius,
+                                             int32_t buffer_size, const uint32_t *d_order, void *stream,
+                                             int64_t *d_offsets, int32_t *d_indices, int64_t capacity);
+
 /* Release memory returned by arborx_query_spatial (stream-ordered on `stream`). */
 ARBORX_API int arborx_free(arborx_handle h, void *d_ptr, size_t bytes, void *stream);
 

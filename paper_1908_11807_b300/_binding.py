@@ -88,6 +88,7 @@ def lib() -> ctypes.CDLL:
         L.arborx_query_spatial_buffered_count.argtypes = [vp, vp, i64, ctypes.c_float, i32, vp, vp, vp,
                                                           ctypes.POINTER(i64)]
         L.arborx_query_spatial_buffered_fill.argtypes = [vp, vp, i64, ctypes.c_float, vp, vp, vp, i64]
+        L.arborx_query_spatial_buffered.argtypes = [vp, vp, i64, ctypes.c_float, i32, vp, vp, vp, vp, i64]
         L.arborx_batch_create.argtypes = [i64, vp, vp, vp, ctypes.POINTER(arborx_opts), vp, ctypes.POINTER(vp)]
         L.arborx_batch_entries.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]
         L.arborx_batch_run.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp]
@@ -200,6 +201,28 @@ class BVH:
         _check(lib().arborx_stats(self.handle, _stream(), out), "arborx_stats")
         return {"spatial_nodes": out[0], "nearest_nodes": out[1], "spatial_queries": out[2],
                 "nearest_queries": out[3]}
+
+    def query_spatial_async(self, queries: torch.Tensor, radius: float, buffer_size: int = 32,
+                            order: Optional[torch.Tensor] = None, capacity: Optional[int] = None,
+                            indices: Optional[torch.Tensor] = None) -> Tuple[torch.Tensor, torch.Tensor]:
+        """One-pass spatial query with no host synchronisation: (offsets int64 [m+1], indices int32
+        [capacity]); the first offsets[-1] entries of ``indices`` are the CSR rows.  ``capacity``
+        defaults to m * buffer_size; rows beyond it are dropped and ``check()`` raises."""
+        q = _as_f32_cuda(queries, 3, "queries")
+        m = q.shape[0]
+        offsets = torch.empty(m + 1, dtype=torch.int64, device=q.device)
+        if indices is None:
+            cap = int(m * buffer_size if capacity is None else capacity)
+            indices = torch.empty(max(cap, 1), dtype=torch.int32, device=q.device)
+        else:
+            cap = indices.numel() if capacity is None else int(capacity)
+            if indices.dtype != torch.int32 or not indices.is_cuda or indices.numel() < cap:
+                raise ValueError("indices must be an int32 CUDA tensor of at least `capacity` entries")
+        _check(lib().arborx_query_spatial_buffered(self.handle, _ptr(q), m, ctypes.c_float(radius), int(buffer_size),
+                                                   _ptr(order), _stream(), _ptr(offsets), _ptr(indices), cap),
+               "arborx_query_spatial_buffered")
+        self._async_keep = (q, order)  # inputs stay alive while the stream works
+        return offsets, indices
 
     def query_spatial_count(self, queries: torch.Tensor, radius: float,
                             offsets: Optional[torch.Tensor] = None,

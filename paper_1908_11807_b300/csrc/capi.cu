@@ -838,6 +838,42 @@ int arborx_query_spatial_buffered_fill(arborx_handle h, const float *d_queries, 
   return launch_status();
 }
 
+int arborx_query_spatial_buffered(arborx_handle h, const float *d_queries, int64_t m, float radius,
+                                  int32_t buffer_size, const uint32_t *d_order, void *stream, int64_t *d_offsets,
+                                  int32_t *d_indices, int64_t capacity) {
+  if (!h || m < 0 || m >= ARBORX_MAX_QUERIES || !d_offsets || (m > 0 && !d_queries) || !finite_radius(radius) ||
+      buffer_size < 1 || buffer_size > ARBORX_MAX_BUFFER_SIZE || capacity < 0 || (capacity > 0 && !d_indices))
+    return ARBORX_EINVAL;
+  const cudaStream_t s = (cudaStream_t)stream;
+  h->stream = s;
+  h->count_valid = false;
+  h->buffered_valid = false;
+  QueryWs q;
+  int st = get_query_ws(h, m, s, &q);
+  if (st) return st;
+  const size_t need = (size_t)m * buffer_size * sizeof(int32_t);
+  if (need > h->sbuf_bytes) {
+    dev_free(h->opts, h->sbuf, h->sbuf_bytes, s);
+    h->sbuf = (int32_t *)dev_alloc(h->opts, need, s);
+    h->sbuf_bytes = h->sbuf ? need : 0;
+    if (!h->sbuf) return ARBORX_ENOMEM;
+  }
+  const uint32_t *perm;
+  st = order_queries(h, d_queries, m, s, q, &perm, d_order);
+  if (st) return st;
+  const float r2 = radius * radius;  // one IEEE single rounding
+  uint32_t *ovf_count = q.miss + m;
+  cudaMemsetAsync(ovf_count, 0, sizeof(uint32_t), s);
+  launch_spatial_buffered(h->rec, (uint32_t)h->n, d_queries, perm, (uint32_t)m, r2, q.counts, h->sbuf, buffer_size,
+                          q.miss, ovf_count, &h->meta->err, trav_cfg(h, 0), s);
+  launch_scan(q.counts, (uint32_t)m, d_offsets, q.scan_tmp, s);
+  launch_compact(h->sbuf, buffer_size, q.counts, d_offsets, (uint32_t)m, d_indices, capacity, &h->meta->err, s);
+  launch_spatial_fill(h->rec, (uint32_t)h->n, d_queries, q.miss, (uint32_t)m, r2, d_offsets, d_indices, capacity,
+                      &h->meta->err, trav_cfg(h, 0), s, ovf_count);
+  h->stat_queries[0] += (uint64_t)m;
+  return launch_status();
+}
+
 int arborx_query_order(arborx_handle h, const float *d_queries, int64_t m, void *stream, uint32_t *d_order) {
   if (!h || m < 0 || m >= ARBORX_MAX_QUERIES || (m > 0 && (!d_queries || !d_order))) return ARBORX_EINVAL;
   if (m == 0) return ARBORX_OK;

@@ -268,3 +268,57 @@ def test_one_pass_spatial_edge_cases():
                                                    ctypes.c_float(0.1), bad, None, None,
                                                    ctypes.c_void_p(off.data_ptr()), ctypes.byref(nnz))
         assert st == 1
+
+
+@pytest.mark.parametrize("name", ["cube_1e4", "paper_hollow", "duplicates", "boxes"])
+@pytest.mark.parametrize("bs", [1, 10, 32])
+def test_async_one_pass_spatial_matches(name, bs):
+    # single-call one-pass query (no host round trip): same CSR as the two-pass query
+    ab = _ab()
+    p, q, r = CASES[name]()
+    bvh = ab.BVH(dev(p))
+    qd = dev(q)
+    order = bvh.query_order(qd)
+    off, idx = bvh.query_spatial_async(qd, r, buffer_size=bs, order=order, capacity=len(q) * 64)
+    bvh.check()
+    og, ig = bvh.query_spatial(qd, r, order=order)
+    nnz = int(off[-1])
+    assert np.array_equal(host(off), host(og)) and np.array_equal(host(idx)[:nnz], host(ig))
+    oo, io = oracle.spatial_brute(p, q, r)
+    assert_spatial_equal(host(off), host(idx)[:nnz], oo, io)
+
+
+def test_async_one_pass_spatial_capacity_and_graph():
+    ab = _ab()
+    import torch
+    p, q, r = CASES["cube_1e4"]()
+    bvh = ab.BVH(dev(p))
+    qd = dev(q)
+    og, ig = bvh.query_spatial(qd, r)
+    nnz = int(ig.numel())
+    # too small a buffer: nothing past it is written, the overflow is reported, offsets stay complete
+    off, idx = bvh.query_spatial_async(qd, r, buffer_size=8, capacity=nnz - 1)
+    with pytest.raises(ab.ArborXError):
+        bvh.check()
+    assert np.array_equal(host(off), host(og))
+    # exact capacity
+    off, idx = bvh.query_spatial_async(qd, r, buffer_size=8, capacity=nnz)
+    bvh.check()
+    assert np.array_equal(host(idx)[:nnz], host(ig))
+    # empty query set
+    off0, _ = bvh.query_spatial_async(qd[:0], r, buffer_size=8, capacity=0)
+    assert host(off0).tolist() == [0]
+    # the call enqueues work only, so it can be captured in a CUDA graph and replayed
+    order = bvh.query_order(qd)
+    out_idx = torch.empty(len(q) * 16, dtype=torch.int32, device="cuda")
+    bvh.query_spatial_async(qd, r, buffer_size=16, order=order, indices=out_idx)  # size the workspaces
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        goff, _ = bvh.query_spatial_async(qd, r, buffer_size=16, order=order, indices=out_idx)
+    out_idx.fill_(-7)
+    g.replay()
+    torch.cuda.synchronize()
+    bvh.check()
+    assert np.array_equal(host(goff), host(og))
+    assert np.array_equal(host(out_idx)[:nnz], host(ig))
