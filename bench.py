@@ -343,16 +343,40 @@ def run_gpu(args):
         pd = torch.empty_like(p)
         qd = torch.empty_like(q)
 
+        cs = torch.cuda.Stream(device=dev)  # copy stream: overlaps transfers with the compute stream
+        nnz_pin = torch.empty(1, dtype=torch.int64).pin_memory()
+        ev_q = torch.cuda.Event()
+        ev_sp = torch.cuda.Event()
+
         def e2e_step():
-            pd.copy_(p_pin, non_blocking=True)
-            qd.copy_(q_pin, non_blocking=True)
-            ev, (off, idx, kidx, kd2), bvh = step(pd, qd)
-            bvh.destroy()
-            outs["off"].copy_(off, non_blocking=True)
+            pd.copy_(p_pin, non_blocking=True)  # compute stream: the build needs every point
+            cs.wait_stream(stream)
+            with torch.cuda.stream(cs):
+                qd.copy_(q_pin, non_blocking=True)  # uploads while the tree builds
+                ev_q.record(cs)
+            bvh = ab.BVH(pd, **topts)
+            stream.wait_event(ev_q)
+            order = bvh.query_order(qd)
+            if bsz > 0:
+                off, idx = bvh.query_spatial_async(qd, r, buffer_size=bsz, order=order, indices=idx_buf)
+            else:
+                off, idx = bvh.query_spatial(qd, r, order=order)
+            ev_sp.record(stream)
+            kidx, kd2 = bvh.query_nearest(qd, k, order=order)
+            with torch.cuda.stream(cs):
+                cs.wait_event(ev_sp)
+                off.record_stream(cs)
+                idx.record_stream(cs)
+                outs["off"].copy_(off, non_blocking=True)  # downloads while the k-NN kernel runs
+                nnz_pin.copy_(off[-1:], non_blocking=True)
+            cs.synchronize()  # the row total; the k-NN work is already queued on the compute stream
+            got = int(nnz_pin[0])
+            with torch.cuda.stream(cs):
+                idx_pin[:got].copy_(idx[:got], non_blocking=True)
             outs["kidx"].copy_(kidx, non_blocking=True)
             outs["kd2"].copy_(kd2, non_blocking=True)
-            got = int(off[-1].item())  # the row total, then exactly the rows
-            idx_pin[:got].copy_(idx[:got], non_blocking=True)
+            stream.wait_stream(cs)  # join the copies before the end event
+            bvh.destroy()
             return got
 
         for _ in range(max(1, args.warmup)):
@@ -375,7 +399,8 @@ def run_gpu(args):
         e2e_value = ws * 2 * m / (e2e_ms * 1e-3) / 1e6
 
         e2e = {"value": round(e2e_value, 3), "unit": UNIT, "ms_per_step": round(e2e_ms, 4),
-               "h2d_bytes_per_step": int(p_h.nbytes + q_h.nbytes), "d2h_bytes_per_step": int(d2h)}
+               "h2d_bytes_per_step": int(p_h.nbytes + q_h.nbytes), "d2h_bytes_per_step": int(d2h),
+               "overlap": "queries upload during the build, spatial rows download during the k-NN query"}
 
     # ---- roofline of the dominant kernel
     peak, peak_kind = measured_peaks()
