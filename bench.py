@@ -450,6 +450,7 @@ def run_gpu(args):
         "clocks": clocks,
     }
     if rank == 0 and not args.no_extras:
+        line["query_ordering"] = ordering_extra(ab, p, q, r, k, topts)
         line["learned"] = learned_extra(ab, dev)
         line["batched"] = batched_extra(ab, dev)
     if rank == 0 and not args.no_cpu_baseline:
@@ -474,6 +475,25 @@ def _time_ms(fn, reps=3):
         torch.cuda.synchronize()
         best = min(best, e0.elapsed_time(e1))
     return best
+
+
+def ordering_extra(ab, p, q, r, k, topts):
+    """Query ordering (Sec. 2.2.3): the same queries traversed in Morton order (the query sort
+    included in the time) and in input order, with the internal nodes loaded per query."""
+    out = {}
+    for name, sq in (("sorted", 1), ("unsorted", 0)):
+        bvh = ab.BVH(p, sort_queries=sq, stats=1, **topts)
+        knn_ms = _time_ms(lambda: bvh.query_nearest(q, k))
+        sp_ms = _time_ms(lambda: bvh.query_spatial(q, r))
+        bvh.stats()
+        bvh.query_nearest(q, k)
+        nodes = bvh.stats()["nearest_nodes"] / q.shape[0]
+        out[name] = {"knn_ms": round(knn_ms, 3), "spatial_2p_ms": round(sp_ms, 3),
+                     "knn_nodes_per_query": round(nodes, 1)}
+        bvh.destroy()
+    out["knn_speedup_from_ordering"] = round(out["unsorted"]["knn_ms"] / out["sorted"]["knn_ms"], 2)
+    out["spatial_speedup_from_ordering"] = round(out["unsorted"]["spatial_2p_ms"] / out["sorted"]["spatial_2p_ms"], 2)
+    return out
 
 
 def learned_extra(ab, dev):

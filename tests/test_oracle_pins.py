@@ -336,3 +336,19 @@ def test_strict_radius_reading_would_fail_lattice_pin():
         r_open = float(np.nextafter(np.float32(float(r)), np.float32(0)))
         off, _ = oracle.spatial_brute(pts, site, r_open)
         assert int(np.diff(off)[0]) == int(strict) != int(cnt) or int(strict) == int(cnt)
+
+
+def test_paper_shapes_count_statistics():
+    # sanity of the paper-shapes generator (Sec. 3.1), not a parity pin: with the radius for a mean
+    # of 10 neighbours in the filled cube, filled-sphere queries find about 10 on average (fewer
+    # near the cube faces, none beyond), while hollow-sphere queries against the hollow cube mostly
+    # find few points and a long tail near the face centres
+    import datagen
+    p = 10_000
+    r = datagen.paper_radius(p)
+    o, _ = oracle.spatial_brute(datagen.paper_shape(p, "filled_cube", 8), datagen.paper_shape(p, "filled_sphere", 9), r)
+    c = np.diff(o)
+    assert 9.5 < c.mean() < 10.5 and c.min() == 0 and 15 <= c.max() <= 40
+    o, _ = oracle.spatial_brute(datagen.paper_shape(p, "hollow_cube", 10), datagen.paper_shape(p, "hollow_sphere", 11), r)
+    c = np.diff(o)
+    assert 1.5 < c.mean() < 4.5 and c.min() == 0 and c.max() >= 8 * c.mean()
