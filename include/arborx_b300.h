@@ -140,8 +140,9 @@ ARBORX_API int arborx_size(arborx_handle h, int64_t *n, int32_t *kind);
  * clears them. */
 ARBORX_API int arborx_check(arborx_handle h, void *stream);
 
-/* Traversal order of a query set (Sec. 2.2, "Query ordering"): Morton codes of the query points
- * scaled by the tree's scene box (points outside clamped to it), stably sorted; d_order[i] is the
+/* Traversal order of a query set (Sec. 2.2, "Query ordering"): 30-bit Morton codes of the query
+ * points scaled by the tree's scene box (points outside clamped to it), stably sorted by their top
+ * 24 bits (8 per axis; the order only affects speed); d_order[i] is the
  * query traversed i-th.  Pass it to the query calls below to sort a query set once for several
  * queries.  A tree with n = 0 or m < 2 gives the identity.
  *   d_order  device uint32[m], written */

@@ -145,11 +145,13 @@ __device__ __forceinline__ void hist_add(uint32_t (*s_h)[kRadix], int passes, K 
 }
 
 // Morton code of each primitive's centroid (points: the point; boxes: the box
-// centre), scaled by the scene box in `meta`; histograms of every radix pass.
+// centre), scaled by the scene box in `meta`, without its `drop` lowest bits;
+// histograms of every radix pass.
 template <typename K, int KIND>
 __global__ void __launch_bounds__(256) k_morton(const float *__restrict__ prims, uint32_t n, bool vec,
                                                DevMeta *__restrict__ meta, K *__restrict__ codes,
-                                               uint32_t *__restrict__ hist, int passes, bool write_scene) {
+                                               uint32_t *__restrict__ hist, int passes, bool write_scene,
+                                               int drop) {
   __shared__ uint32_t s_h[8][kRadix];
   __shared__ float s_sc[6];
   for (int i = threadIdx.x; i < passes * kRadix; i += blockDim.x) (&s_h[0][0])[i] = 0;
@@ -181,7 +183,7 @@ __global__ void __launch_bounds__(256) k_morton(const float *__restrict__ prims,
         cy = __fmul_rn(__fadd_rn(v[6 * j + 1], v[6 * j + 4]), 0.5f);
         cz = __fmul_rn(__fadd_rn(v[6 * j + 2], v[6 * j + 5]), 0.5f);
       }
-      out[j] = morton<K>(cx, cy, cz, sc);
+      out[j] = morton<K>(cx, cy, cz, sc) >> drop;
       hist_add<K>(s_h, passes, out[j]);
     }
 #pragma unroll
@@ -197,7 +199,7 @@ __global__ void __launch_bounds__(256) k_morton(const float *__restrict__ prims,
       cy = __fmul_rn(__fadd_rn(p[1], p[4]), 0.5f);
       cz = __fmul_rn(__fadd_rn(p[2], p[5]), 0.5f);
     }
-    const K code = morton<K>(cx, cy, cz, sc);
+    const K code = morton<K>(cx, cy, cz, sc) >> drop;
     codes[i] = code;
     hist_add<K>(s_h, passes, code);
   }
@@ -721,7 +723,7 @@ void launch_bounds(const float *prims, int64_t n, int kind, DevMeta *meta, cudaS
 
 template <typename K>
 void launch_morton(const float *prims, uint32_t n, int kind, DevMeta *meta, K *codes, uint32_t *hist, int passes,
-                   bool write_scene, cudaStream_t s) {
+                   bool write_scene, cudaStream_t s, int drop) {
   if (n == 0) return;
   const bool vec = (reinterpret_cast<uintptr_t>(prims) & 15u) == 0;
   const uint32_t per_thread = kind == 0 ? 4 : 2;
@@ -729,9 +731,9 @@ void launch_morton(const float *prims, uint32_t n, int kind, DevMeta *meta, K *c
                                         (uint32_t)sm_count() * 8u);
   prof::Scope ps(s, "morton");
   if (kind == 0)
-    k_morton<K, 0><<<blocks, 256, 0, s>>>(prims, n, vec, meta, codes, hist, passes, write_scene);
+    k_morton<K, 0><<<blocks, 256, 0, s>>>(prims, n, vec, meta, codes, hist, passes, write_scene, drop);
   else
-    k_morton<K, 1><<<blocks, 256, 0, s>>>(prims, n, vec, meta, codes, hist, passes, write_scene);
+    k_morton<K, 1><<<blocks, 256, 0, s>>>(prims, n, vec, meta, codes, hist, passes, write_scene, drop);
 }
 
 template <typename K>
@@ -796,9 +798,9 @@ template void launch_apetrei<uint32_t>(const float *, uint32_t, int, const uint3
 template void launch_apetrei<uint64_t>(const float *, uint32_t, int, const uint64_t *, const uint32_t *, int32_t *,
                                        float4 *, void *, uint32_t *, cudaStream_t);
 template void launch_morton<uint32_t>(const float *, uint32_t, int, DevMeta *, uint32_t *, uint32_t *, int, bool,
-                                      cudaStream_t);
+                                      cudaStream_t, int);
 template void launch_morton<uint64_t>(const float *, uint32_t, int, DevMeta *, uint64_t *, uint32_t *, int, bool,
-                                      cudaStream_t);
+                                      cudaStream_t, int);
 template void launch_hierarchy<uint32_t>(const uint32_t *, uint32_t, int32_t *, cudaStream_t);
 template void launch_hierarchy<uint64_t>(const uint64_t *, uint32_t, int32_t *, cudaStream_t);
 

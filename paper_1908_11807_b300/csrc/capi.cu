@@ -50,6 +50,11 @@ namespace {
 constexpr size_t kAlign = 256;
 inline size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
+// Queries are ordered by the top 24 bits of their 30-bit Morton codes (8 bits
+// per axis, 16.7M cells): the order only decides speed, and three radix
+// passes instead of four give the same coherence.
+constexpr int kQueryKeyBits = 24;
+
 struct Carver {
   char *base;
   size_t off = 0;
@@ -287,7 +292,7 @@ struct QueryWs {
 };
 
 size_t query_ws_bytes(int64_t m, size_t *sort_words) {
-  *sort_words = sort_ws_words<uint32_t>(m, 30);
+  *sort_words = sort_ws_words<uint32_t>(m, kQueryKeyBits);
   return 4 * align_up((size_t)m * sizeof(uint32_t)) + align_up(*sort_words * sizeof(uint32_t)) +
          align_up((size_t)m * sizeof(int32_t)) + align_up(scan_tmp_words((uint32_t)m) * sizeof(int64_t)) +
          align_up(((size_t)m + 32) * sizeof(uint32_t));
@@ -322,8 +327,9 @@ int order_queries(arborx_bvh_s *h, const float *d_q, int64_t m, cudaStream_t s, 
   *perm = given;
   if (given || !h->opts.sort_queries || m < 2 || h->n == 0) return ARBORX_OK;
   cudaMemsetAsync(q.sortws, 0, q.sort_words * sizeof(uint32_t), s);
-  const SortWs ws = sort_ws_carve<uint32_t>(q.sortws, m, 30);
-  launch_morton<uint32_t>(d_q, (uint32_t)m, ARBORX_POINTS, h->meta, q.cA, ws.hist, ws.passes, false, s);
+  const SortWs ws = sort_ws_carve<uint32_t>(q.sortws, m, kQueryKeyBits);
+  launch_morton<uint32_t>(d_q, (uint32_t)m, ARBORX_POINTS, h->meta, q.cA, ws.hist, ws.passes, false, s,
+                          30 - kQueryKeyBits);
   uint32_t *sk, *pm;
   sort_pairs<uint32_t>(q.cA, q.cB, q.pA, q.pB, (uint32_t)m, ws, &h->meta->err, s, &sk, &pm);
   *perm = pm;
@@ -885,8 +891,9 @@ int arborx_query_order(arborx_handle h, const float *d_queries, int64_t m, void 
   const uint32_t *perm = nullptr;
   if (h->n > 0 && m > 1) {
     cudaMemsetAsync(q.sortws, 0, q.sort_words * sizeof(uint32_t), s);
-    const SortWs ws = sort_ws_carve<uint32_t>(q.sortws, m, 30);
-    launch_morton<uint32_t>(d_queries, (uint32_t)m, ARBORX_POINTS, h->meta, q.cA, ws.hist, ws.passes, false, s);
+    const SortWs ws = sort_ws_carve<uint32_t>(q.sortws, m, kQueryKeyBits);
+    launch_morton<uint32_t>(d_queries, (uint32_t)m, ARBORX_POINTS, h->meta, q.cA, ws.hist, ws.passes, false, s,
+                            30 - kQueryKeyBits);
     uint32_t *sk, *pm;
     sort_pairs<uint32_t>(q.cA, q.cB, q.pA, q.pB, (uint32_t)m, ws, &h->meta->err, s, &sk, &pm);
     perm = pm;

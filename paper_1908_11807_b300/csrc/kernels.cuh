@@ -10,7 +10,7 @@ void launch_init_meta(DevMeta *meta, cudaStream_t s);
 void launch_bounds(const float *prims, int64_t n, int kind, DevMeta *meta, cudaStream_t s);
 template <typename K>
 void launch_morton(const float *prims, uint32_t n, int kind, DevMeta *meta, K *codes, uint32_t *hist, int passes,
-                   bool write_scene, cudaStream_t s);
+                   bool write_scene, cudaStream_t s, int drop = 0);
 template <typename K>
 void launch_hierarchy(const K *codes, uint32_t n, int32_t *parent, cudaStream_t s);
 // bytes of the frontier list of launch_apetrei for n leaves
