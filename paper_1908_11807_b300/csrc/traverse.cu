@@ -190,6 +190,53 @@ __global__ void __launch_bounds__(256) k_compact(const int32_t *__restrict__ buf
   }
 }
 
+// Same move for row buffers whose width is a multiple of 4: one 16-byte load
+// brings four slots of a row, a thread takes kCompactPer such groups.
+template <typename IDX>
+__global__ void __launch_bounds__(256) k_compact4(const int4 *__restrict__ buf4, int bs,
+                                                 const int32_t *__restrict__ counts,
+                                                 const int64_t *__restrict__ offsets, uint32_t m,
+                                                 int32_t *__restrict__ indices, int64_t capacity,
+                                                 uint32_t *__restrict__ err) {
+  const int gpr = bs >> 2;  // 4-slot groups per row
+  const IDX total = (IDX)m * (IDX)gpr;
+  const IDX base = (IDX)blockIdx.x * (IDX)(blockDim.x * kCompactPer) + threadIdx.x;
+  int32_t c[kCompactPer], j[kCompactPer];
+  int64_t o[kCompactPer];
+  int4 v[kCompactPer];
+#pragma unroll
+  for (int k = 0; k < kCompactPer; ++k) {
+    const IDX t = base + (IDX)k * blockDim.x;
+    c[k] = -1;
+    j[k] = 0;
+    if (t < total) {
+      const IDX qi = t / (IDX)gpr;
+      j[k] = 4 * (int32_t)(t - qi * (IDX)gpr);
+      c[k] = __ldg(counts + qi);
+      o[k] = __ldg(offsets + qi);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kCompactPer; ++k) {
+    const IDX t = base + (IDX)k * blockDim.x;
+    if (c[k] <= bs && j[k] < c[k]) v[k] = __ldg(buf4 + t);
+  }
+#pragma unroll
+  for (int k = 0; k < kCompactPer; ++k) {
+    if (c[k] <= bs && j[k] < c[k]) {
+      const int32_t vv[4] = {v[k].x, v[k].y, v[k].z, v[k].w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        if (j[k] + e < c[k]) {
+          const int64_t pos = o[k] + j[k] + e;
+          if (pos < capacity) indices[pos] = vv[e];
+          else set_err(err, ERR_CSR);
+        }
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------------------- nearest
 
 // Ascending list of the KC best (d2, index) pairs in registers; the k-th entry
@@ -679,6 +726,16 @@ void launch_compact(const int32_t *buf, int bs, const int32_t *counts, const int
   const uint64_t slots = (uint64_t)m * bs;
   if (slots == 0) return;
   prof::Scope ps(s, "compact");
+  if (bs % 4 == 0 && (reinterpret_cast<uintptr_t>(buf) & 15u) == 0) {
+    const uint64_t groups = slots / 4;
+    const uint64_t gblocks = (groups + 256 * kCompactPer - 1) / (256 * kCompactPer);
+    const int4 *buf4 = reinterpret_cast<const int4 *>(buf);
+    if (groups + 256 * kCompactPer < (1ull << 32))
+      k_compact4<uint32_t><<<(unsigned)gblocks, 256, 0, s>>>(buf4, bs, counts, offsets, m, indices, capacity, err);
+    else
+      k_compact4<uint64_t><<<(unsigned)gblocks, 256, 0, s>>>(buf4, bs, counts, offsets, m, indices, capacity, err);
+    return;
+  }
   const uint64_t blocks = (slots + 256 * kCompactPer - 1) / (256 * kCompactPer);
   if (slots + 256 * kCompactPer < (1ull << 32))  // 32-bit slot arithmetic cannot wrap
     k_compact<uint32_t><<<(unsigned)blocks, 256, 0, s>>>(buf, bs, counts, offsets, m, indices, capacity, err);
