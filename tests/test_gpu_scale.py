@@ -4,6 +4,7 @@ launch configuration the benchmark uses.  Results are checked on sampled
 queries against the oracle's CPU BVH (exact rows) and FP64 checker, and at
 every query through size-independent properties (closed-form lattice counts,
 CSR structure, row order)."""
+import functools
 import math
 
 import numpy as np
@@ -178,3 +179,57 @@ def test_learned_full_size_sampled_exact():
     rows = np.sort(np.random.default_rng(7).choice(m, 10_000, replace=False))
     ko, do = oracle.CpuBVH(p).nearest(q[rows], 10)
     assert_nearest_equal(host(li)[rows], host(ld)[rows], ko, do)
+
+
+@functools.lru_cache(maxsize=1)
+def _large_cloud(n, m):
+    return datagen.cube(n, S2 + 7), datagen.cube(m, S2 + 7, datagen.STREAM_QUERIES)
+
+
+@pytest.mark.parametrize("key_bits", [30, 63])
+def test_large_n_sampled_exact(key_bits):
+    # 2^27 - 3 points (13x the benchmark's tree, a ragged last sort tile and Apetrei chunk):
+    # sampled rows of both queries exact against the oracle's brute force
+    ab = _ab()
+    n, m = (1 << 27) - 3, 100_000
+    p, q = _large_cloud(n, m)
+    r = datagen.radius_for_mean(n, "cube")
+    bvh = ab.BVH(dev(p), key_bits=key_bits, **BENCH_LAUNCH)
+    qd = dev(q)
+    order = bvh.query_order(qd)
+    og, ig = bvh.query_spatial(qd, r, order=order, buffer_size=BENCH_BUFFER)
+    kg, dg = bvh.query_nearest(qd, 10, order=order)
+    bvh.check()
+    og, ig, kg, dg = host(og), host(ig), host(kg), host(dg)
+    assert og[0] == 0 and np.all(np.diff(og) >= 0) and og[-1] == ig.size and 9.0 < ig.size / m < 11.0
+    rows = np.sort(np.random.default_rng(key_bits).choice(m, 64, replace=False))
+    oo, io = oracle.spatial_brute(p, q[rows], r)
+    so, si = _sub_csr(og, ig, rows)
+    assert_spatial_equal(so, si, oo, io)
+    ko, do = oracle.nearest_brute(p, q[rows], 10)
+    assert_nearest_equal(kg[rows], dg[rows], ko, do)
+
+
+def test_more_than_2_31_results():
+    # 2.4e9 CSR entries (9.6 GB of indices): 64-bit offsets end to end, rows exact on a sample
+    ab = _ab()
+    import torch
+    n, m = 10_000_000, 200_000
+    p = datagen.cube(n, S2 + 8)
+    q = datagen.cube(m, S2 + 8, datagen.STREAM_QUERIES)
+    r = datagen.radius_for_mean(n, "cube") * (12_000 / 10) ** (1 / 3)  # about 12 000 results per query
+    bvh = ab.BVH(dev(p))
+    qd = dev(q)
+    offsets = bvh.query_spatial_count(qd, r)
+    total = int(offsets[-1])
+    assert total > (1 << 31)
+    indices = torch.empty(total, dtype=torch.int32, device="cuda")
+    bvh.query_spatial_fill(qd, r, offsets, indices)
+    bvh.check()
+    off = host(offsets)
+    assert off.dtype == np.int64 and off[0] == 0 and np.all(np.diff(off) >= 0) and off[-1] == total
+    rows = np.array([0, 1, m // 2, m - 2, m - 1] + list(np.random.default_rng(8).choice(m, 11, replace=False)))
+    oo, io = oracle.spatial_brute(p, q[rows], r)
+    got = [host(indices[int(off[j]):int(off[j + 1])]) for j in rows]
+    so = np.concatenate([[0], np.cumsum([len(x) for x in got])])
+    assert_spatial_equal(so, np.concatenate(got), oo, io)
