@@ -77,7 +77,9 @@ typedef enum {
 
 /* Caller-supplied device allocator (e.g. a framework's caching allocator).
  * alloc returns device memory of at least `bytes` bytes usable on `stream`,
- * or NULL on failure; free releases it (stream-ordered). */
+ * aligned to 256 bytes (as cudaMalloc and the torch caching allocator return it),
+ * or NULL on failure; free releases it (stream-ordered).  A block that is not
+ * 256-byte aligned is released again and the call fails with ARBORX_ENOMEM. */
 typedef void *(*arborx_alloc_fn)(size_t bytes, void *stream, void *ctx);
 typedef void (*arborx_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
 

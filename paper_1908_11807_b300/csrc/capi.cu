@@ -99,7 +99,14 @@ cudaMemPool_t lib_pool() {
 
 void *dev_alloc(const arborx_opts &o, size_t bytes, cudaStream_t s) {
   if (bytes == 0) bytes = kAlign;
-  if (o.alloc) return o.alloc(bytes, (void *)s, o.alloc_ctx);
+  if (o.alloc) {
+    void *q = o.alloc(bytes, (void *)s, o.alloc_ctx);
+    if (q && (reinterpret_cast<uintptr_t>(q) & (kAlign - 1))) {  // the traversals read 32-byte slots
+      o.free(q, bytes, (void *)s, o.alloc_ctx);
+      return nullptr;
+    }
+    return q;
+  }
   void *p = nullptr;
   cudaMemPool_t pool = lib_pool();
   const cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, bytes, pool, s) : cudaMallocAsync(&p, bytes, s);
