@@ -368,9 +368,11 @@ struct SmemHeap {
 // which can only be larger than with every candidate inserted, so no node that
 // holds a result is skipped and every candidate still reaches the list once.
 // It pays for the shared-memory heap, whose data-dependent sift loop diverges.
-template <int DEFER, class List>
+// PACK: stack entries (node, box distance) as one 64-bit word, one shared-memory access per push or
+// pop (faster with the register lists, slower with the heap, whose sift shares the memory pipe).
+template <int DEFER, bool PACK, class List>
 __device__ __forceinline__ void knn_traverse(const float4 *__restrict__ rec, uint32_t n, float qx, float qy, float qz, List &L,
-                                             int k, int32_t *s_node, float *s_dist, int stride, int stack_smem,
+                                             int k, unsigned char *s_stack, int stride, int stack_smem,
                                              uint32_t *err, uint32_t &visited, uint32_t root_slot = 0) {
   const float4 r0 = __ldg(rec + 2 * (uint64_t)root_slot), r1 = __ldg(rec + 2 * (uint64_t)root_slot + 1);
   const int e0 = __float_as_int(r0.w);
@@ -380,8 +382,13 @@ __device__ __forceinline__ void knn_traverse(const float4 *__restrict__ rec, uin
     return;
   }
   if (d0 > L.bound()) return;
-  int32_t spn[kSpill];
+  // shared part of the stack, [level][thread]: packed words, or node ids then distances
+  unsigned long long *s_st = reinterpret_cast<unsigned long long *>(s_stack) + threadIdx.x;
+  int32_t *s_node = reinterpret_cast<int32_t *>(s_stack) + threadIdx.x;
+  float *s_dist = reinterpret_cast<float *>(s_stack) + (size_t)stack_smem * stride + threadIdx.x;
+  int32_t spn[kSpill];  // local spill beyond the shared part (one of the two forms is used)
   float spd[kSpill];
+  unsigned long long spl[kSpill];
   int sp = 0;
   int node = e0;
   constexpr int DB = DEFER > 0 ? DEFER : 1;
@@ -434,12 +441,20 @@ __device__ __forceinline__ void knn_traverse(const float4 *__restrict__ rec, uin
       const int far = lfirst ? er : el;
       const float fd = lfirst ? dr : dl;
       if (sp < stack_smem) {
-        s_node[sp * stride] = far;
-        s_dist[sp * stride] = fd;
+        if constexpr (PACK) {
+          s_st[sp * stride] = ((unsigned long long)__float_as_uint(fd) << 32) | (uint32_t)far;
+        } else {
+          s_node[sp * stride] = far;
+          s_dist[sp * stride] = fd;
+        }
         ++sp;
       } else if (sp - stack_smem < kSpill) {
-        spn[sp - stack_smem] = far;
-        spd[sp - stack_smem] = fd;
+        if constexpr (PACK) {
+          spl[sp - stack_smem] = ((unsigned long long)__float_as_uint(fd) << 32) | (uint32_t)far;
+        } else {
+          spn[sp - stack_smem] = far;
+          spd[sp - stack_smem] = fd;
+        }
         ++sp;
       } else {
         set_err(err, ERR_STACK);  // cannot happen: capacity exceeds the deepest LBVH
@@ -454,8 +469,16 @@ __device__ __forceinline__ void knn_traverse(const float4 *__restrict__ rec, uin
       while (sp > 0) {
         --sp;
         const bool sm = sp < stack_smem;
-        const int nd = sm ? s_node[sp * stride] : spn[sp - stack_smem];
-        const float dd = sm ? s_dist[sp * stride] : spd[sp - stack_smem];
+        int nd;
+        float dd;
+        if constexpr (PACK) {
+          const unsigned long long e = sm ? s_st[sp * stride] : spl[sp - stack_smem];
+          nd = (int)(uint32_t)e;
+          dd = __uint_as_float((uint32_t)(e >> 32));
+        } else {
+          nd = sm ? s_node[sp * stride] : spn[sp - stack_smem];
+          dd = sm ? s_dist[sp * stride] : spd[sp - stack_smem];
+        }
         if (dd <= L.bound()) {
           node = nd;
           break;
@@ -502,8 +525,6 @@ __global__ void __launch_bounds__(kMaxBlock) k_nearest(const __grid_constant__ N
   const uint32_t m = a.m_dev ? min(a.m, *a.m_dev) : a.m;  // count produced on the device (second passes)
   if (t >= m) return;
   const int B = blockDim.x;
-  int32_t *s_node = reinterpret_cast<int32_t *>(s_raw) + threadIdx.x;
-  float *s_dist = reinterpret_cast<float *>(s_raw) + (size_t)stack_smem * B + threadIdx.x;
   const uint32_t pos = pos_list ? __ldg(pos_list + t) : t;
   const uint32_t qi = qperm ? __ldg(qperm + pos) : pos;
   const float qx = __ldg(queries + 3 * (uint64_t)qi);
@@ -520,7 +541,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_nearest(const __grid_constant__ N
   if constexpr (KC > 0) {
     RegList<KC> L;
     L.init(b0, k);
-    if (ok && n > 0) knn_traverse<0>(rec, n, qx, qy, qz, L, k, s_node, s_dist, B, stack_smem, err, visited);
+    if (ok && n > 0) knn_traverse<0, true>(rec, n, qx, qy, qz, L, k, s_raw, B, stack_smem, err, visited);
     if (a.miss_list) append_flagged(ok && L.bound_idx() == INT_MAX, pos, a.miss_list, a.miss_count);
     L.write(row, kk, out_idx, out_d2);
   } else {
@@ -530,7 +551,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_nearest(const __grid_constant__ N
     H.s = B;
     H.k = k;
     H.init(b0, k);
-    if (ok && n > 0) knn_traverse<kHeapDefer>(rec, n, qx, qy, qz, H, k, s_node, s_dist, B, stack_smem, err, visited);
+    if (ok && n > 0) knn_traverse<kHeapDefer, false>(rec, n, qx, qy, qz, H, k, s_raw, B, stack_smem, err, visited);
     if (a.miss_list) append_flagged(ok && H.bound_idx() == INT_MAX, pos, a.miss_list, a.miss_count);
     H.write(row, kk, out_idx, out_d2);
   }
@@ -544,8 +565,6 @@ template <int KC>
 __global__ void __launch_bounds__(kMaxBlock) k_batch_nearest(const __grid_constant__ BatchQueryArgs a) {
   extern __shared__ unsigned char s_raw[];
   const int B = blockDim.x;
-  int32_t *s_node = reinterpret_cast<int32_t *>(s_raw) + threadIdx.x;
-  float *s_dist = reinterpret_cast<float *>(s_raw) + (size_t)a.stack_smem * B + threadIdx.x;
   const uint32_t lane = threadIdx.x & 31;
   while (true) {
     uint32_t base = 0;
@@ -568,7 +587,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_batch_nearest(const __grid_consta
         RegList<KC> L;
         L.init(__int_as_float(0x7f800000), k);
         if (go)
-          knn_traverse<0>(a.rec, a.n, qx, qy, qz, L, k, s_node, s_dist, B, a.stack_smem, a.err, visited,
+          knn_traverse<0, true>(a.rec, a.n, qx, qy, qz, L, k, s_raw, B, a.stack_smem, a.err, visited,
                           (uint32_t)slot);
         L.write(__ldg(a.row_off + qi), kk, a.out_idx, a.out_d2, (int32_t)__ldg(a.prim_base + c));
       } else {
@@ -579,7 +598,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_batch_nearest(const __grid_consta
         H.k = k;
         H.init(__int_as_float(0x7f800000), k);
         if (go)
-          knn_traverse<kHeapDefer>(a.rec, a.n, qx, qy, qz, H, k, s_node, s_dist, B, a.stack_smem, a.err, visited,
+          knn_traverse<kHeapDefer, false>(a.rec, a.n, qx, qy, qz, H, k, s_raw, B, a.stack_smem, a.err, visited,
                                    (uint32_t)slot);
         H.write(__ldg(a.row_off + qi), kk, a.out_idx, a.out_d2, (int32_t)__ldg(a.prim_base + c));
       }
