@@ -341,6 +341,13 @@ __global__ void __launch_bounds__(256) k_fit(const float *__restrict__ prims, ui
 // from every frontier node with the GPU-scope exchange on other[]; crossing
 // nodes are few (about ten per chunk).  Each node sees exactly two arrivals.
 
+// one 32-byte record (lo, hi) in a single 256-bit store; records are 32-byte aligned
+__device__ __forceinline__ void st_rec(float4 *p, const float4 lo, const float4 hi) {
+  asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(lo.x), "f"(lo.y), "f"(lo.z),
+               "f"(lo.w), "f"(hi.x), "f"(hi.y), "f"(hi.z), "f"(hi.w)
+               : "memory");
+}
+
 struct Frontier {
   float4 lo;  // w: enc
   float4 hi;
@@ -367,8 +374,7 @@ __device__ __forceinline__ void apetrei_climb_global(const K *__restrict__ codes
       return;
     }
     float4 *slot = rec + 4 + 4 * (uint64_t)p + (left_child ? 0 : 2);
-    slot[0] = lo;
-    slot[1] = hi;
+    st_rec(slot, lo, hi);
     const int got = atom_exch_acq_rel_gpu(other + p, left_child ? l : r);
     if (got < 0) return;  // sibling not done yet
     if (left_child) r = got;
@@ -502,15 +508,13 @@ __global__ void __launch_bounds__(kApBlock) k_apetrei_local(const float *__restr
   // write node [l, r] (box lo/hi, enc in lo.w) into its parent's slot, or as the root
   auto emit = [&](int l, int r, float4 blo, float4 bhi) {
     if (l == 0 && r == N - 1) {
-      rec[0] = blo;
-      rec[1] = bhi;
+      st_rec(rec, blo, bhi);
       return;
     }
     const bool left_child = D(r) > D(l - 1);
     const int p = left_child ? r : l - 1;
     float4 *slot = rec + 4 + 4 * (uint64_t)p + (left_child ? 0 : 2);
-    slot[0] = blo;
-    slot[1] = bhi;
+    st_rec(slot, blo, bhi);
     if (p < c0 || p >= cend) {  // boundary split: continued by the top kernel
       Frontier &f = s_front[p < c0 ? 0 : 1];
       f.lo = blo;
