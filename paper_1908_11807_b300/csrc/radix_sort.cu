@@ -76,8 +76,8 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(const K *__restric
   for (int i = 0; i < ITEMS; ++i) {
     const uint32_t pos = wbase + i * 32 + lane;
     if (pos < n) {
-      k[i] = kin[pos];
-      v[i] = FIRST ? pos : vin[pos];
+      k[i] = __ldcs(kin + pos);  // read once per pass: evict first (measured 7% faster)
+      v[i] = FIRST ? pos : __ldcs(vin + pos);
     } else {
       k[i] = 0;
       v[i] = 0;
