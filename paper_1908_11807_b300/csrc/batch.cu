@@ -71,7 +71,8 @@ int kc_of(int k) {
 
 int status_of(cudaError_t e) { return e == cudaSuccess ? ARBORX_OK : ARBORX_ECUDA; }
 
-void enqueue(arborx_batch_s *b, const float *pts, const float *qs, cudaStream_t s, int64_t *d_row_offsets,
+// Enqueue the whole batch on `s`; ARBORX_EINVAL if a query class cannot be launched.
+int enqueue(arborx_batch_s *b, const float *pts, const float *qs, cudaStream_t s, int64_t *d_row_offsets,
              int32_t *d_idx, float *d_d2) {
   const uint32_t N = (uint32_t)b->N, M = (uint32_t)b->M, C = (uint32_t)b->C;
   cudaMemsetAsync(b->zero_base, 0, b->zero_bytes, s);
@@ -91,7 +92,7 @@ void enqueue(arborx_batch_s *b, const float *pts, const float *qs, cudaStream_t 
   }
   if (d_row_offsets)
     cudaMemcpyAsync(d_row_offsets, b->row_off, (size_t)(M + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
-  if (M == 0) return;
+  if (M == 0) return ARBORX_OK;
   launch_seg_morton(qs, M, b->q_off, C, b->cmap, b->seg_scene, b->qkA, b->wsq.hist, b->wsq.passes, s);
   const bool qinA = launch_onesweep<uint64_t>(b->qkA, b->qkB, b->qvA, b->qvB, M, b->wsq, b->err, s);
   TravCfg cfg;
@@ -117,8 +118,9 @@ void enqueue(arborx_batch_s *b, const float *pts, const float *qs, cudaStream_t 
     a.out_d2 = d_d2;
     a.err = b->err;
     a.stack_smem = cfg.stack_smem;
-    launch_batch_nearest(a, b->classes[i].kc, cfg, s);
+    if (launch_batch_nearest(a, b->classes[i].kc, cfg, s)) return ARBORX_EINVAL;
   }
+  return ARBORX_OK;
 }
 
 }  // namespace
@@ -275,8 +277,8 @@ int arborx_batch_run(arborx_batch b, const float *d_points, const float *d_queri
   if (!b || (b->N > 0 && !d_points) || (b->M > 0 && !d_queries) || (b->entries > 0 && !d_indices)) return ARBORX_EINVAL;
   const cudaStream_t s = (cudaStream_t)stream;
   if (!use_graph) {
-    enqueue(b, d_points, d_queries, s, d_row_offsets, d_indices, d_dist2);
-    return status_of(cudaGetLastError());
+    const int st = enqueue(b, d_points, d_queries, s, d_row_offsets, d_indices, d_dist2);
+    return st ? st : status_of(cudaGetLastError());
   }
   if (!b->cap) {
     if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess ||
@@ -298,10 +300,11 @@ int arborx_batch_run(arborx_batch b, const float *d_points, const float *d_queri
     }
     cudaGraph_t g = nullptr;
     if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return ARBORX_ECUDA;
-    enqueue(b, d_points, d_queries, b->cap, d_row_offsets, d_indices, d_dist2);
-    if (cudaStreamEndCapture(b->cap, &g) != cudaSuccess || !g) {
+    const int st = enqueue(b, d_points, d_queries, b->cap, d_row_offsets, d_indices, d_dist2);
+    if (cudaStreamEndCapture(b->cap, &g) != cudaSuccess || !g || st) {
       cudaGetLastError();
-      return ARBORX_ECUDA;
+      if (g) cudaGraphDestroy(g);
+      return st ? st : ARBORX_ECUDA;
     }
     const cudaError_t e = cudaGraphInstantiate(&b->exec, g, 0);
     cudaGraphDestroy(g);
