@@ -347,6 +347,8 @@ def run_gpu(args):
         nnz_pin = torch.empty(1, dtype=torch.int64).pin_memory()
         ev_q = torch.cuda.Event()
         ev_sp = torch.cuda.Event()
+        ev_ka = torch.cuda.Event()
+        mh = m // 2
 
         def e2e_step():
             pd.copy_(p_pin, non_blocking=True)  # compute stream: the build needs every point
@@ -362,19 +364,29 @@ def run_gpu(args):
             else:
                 off, idx = bvh.query_spatial(qd, r, order=order)
             ev_sp.record(stream)
-            kidx, kd2 = bvh.query_nearest(qd, k, order=order)
+            # k-NN over the two halves of the query array (each in its own Morton order), so the
+            # first half's rows download while the second half is computed
+            oa, ob = bvh.query_order(qd[:mh]), bvh.query_order(qd[mh:])
+            ka, da = bvh.query_nearest(qd[:mh], k, order=oa)
+            ev_ka.record(stream)
             with torch.cuda.stream(cs):
                 cs.wait_event(ev_sp)
                 off.record_stream(cs)
                 idx.record_stream(cs)
-                outs["off"].copy_(off, non_blocking=True)  # downloads while the k-NN kernel runs
+                outs["off"].copy_(off, non_blocking=True)  # downloads while the k-NN kernels run
                 nnz_pin.copy_(off[-1:], non_blocking=True)
             cs.synchronize()  # the row total; the k-NN work is already queued on the compute stream
             got = int(nnz_pin[0])
+            kb, db = bvh.query_nearest(qd[mh:], k, order=ob)
             with torch.cuda.stream(cs):
                 idx_pin[:got].copy_(idx[:got], non_blocking=True)
-            outs["kidx"].copy_(kidx, non_blocking=True)
-            outs["kd2"].copy_(kd2, non_blocking=True)
+                cs.wait_event(ev_ka)
+                ka.record_stream(cs)
+                da.record_stream(cs)
+                outs["kidx"][:mh].copy_(ka, non_blocking=True)
+                outs["kd2"][:mh].copy_(da, non_blocking=True)
+            outs["kidx"][mh:].copy_(kb, non_blocking=True)
+            outs["kd2"][mh:].copy_(db, non_blocking=True)
             stream.wait_stream(cs)  # join the copies before the end event
             bvh.destroy()
             return got
@@ -400,7 +412,8 @@ def run_gpu(args):
 
         e2e = {"value": round(e2e_value, 3), "unit": UNIT, "ms_per_step": round(e2e_ms, 4),
                "h2d_bytes_per_step": int(p_h.nbytes + q_h.nbytes), "d2h_bytes_per_step": int(d2h),
-               "overlap": "queries upload during the build, spatial rows download during the k-NN query"}
+               "overlap": "queries upload during the build, spatial rows download during the k-NN query, "
+                          "k-NN in two halves with the first half's rows downloading during the second"}
 
     # ---- roofline of the dominant kernel
     peak, peak_kind = measured_peaks()
