@@ -15,6 +15,9 @@ Distributions:
 * ``lattice``         -- the 256^3 integer grid, site index x + 256 y + 65536 z.
 * ``boxes``           -- centres uniform in [0,1)^3, half-widths uniform in
                          [0, 1e-3] per axis.
+* ``query_cubes``     -- box queries: cubes of one half-width, centres uniform
+                         in [0,1)^3 (``box_half_for_mean`` sizes them for a
+                         target mean number of hits).
 * ``gaussian_mixture``-- 64 anisotropic Gaussians, means uniform in [0,1)^3,
                          covariance Q diag(lambda) Q^T, Q Haar-random (QR of a
                          normal matrix), lambda log-uniform in [1e-4, 1e-2].
@@ -91,6 +94,21 @@ def boxes(n: int, seed: int, half_max: float = 1e-3, stream: int = STREAM_POINTS
     c = g.random((n, 3), dtype=np.float64)
     h = g.random((n, 3), dtype=np.float64) * half_max
     return np.concatenate([c - h, c + h], axis=1).astype(np.float32)
+
+
+def query_cubes(m: int, seed: int, half: float, stream: int = STREAM_QUERIES) -> np.ndarray:
+    """m query boxes: cubes of half-width ``half`` with centres uniform in [0,1)^3, float32 [m][6]."""
+    c = rng(seed, stream).random((m, 3), dtype=np.float64)
+    return np.concatenate([c - half, c + half], axis=1).astype(np.float32)
+
+
+def box_half_for_mean(n: int, mean: float = 10.0, prim_half_max: float = 1e-3) -> float:
+    """Half-width of cube queries that meet ``mean`` of n unit-cube boxes on average.
+
+    Per axis a query of half-width h meets a box of half-width u when the centres are at most
+    h + u apart: probability 2 (h + u) for u ~ U[0, prim_half_max], 2 h + prim_half_max on
+    average; over three independent axes n (2 h + prim_half_max)^3 = mean.  Points: 0."""
+    return ((mean / n) ** (1.0 / 3.0) - prim_half_max) / 2.0
 
 
 def gaussian_mixture_params(seed: int, n_comp: int = 64, lam_lo: float = 1e-4, lam_hi: float = 1e-2):

@@ -7,7 +7,7 @@ and it never imports the product library: the two share no code.
 Contents (ArborX, arXiv 1908.11807):
 
 * ``arborx_oracle.c`` (loaded through ctypes): scene box, Morton codes, brute
-  force spatial / nearest queries (the definitions written out), a median-split
+  force spatial / box / nearest queries (the definitions written out), a median-split
   CPU BVH (independent accelerated evaluator) and the FP64 checkers.
 * ``tree_check``: invariants any LBVH over the given primitives must satisfy.
 * ``mlp``: float64 forward / backward / Adam of the k-th-distance regressor.
@@ -47,6 +47,10 @@ def lib():
         L.orc_spatial_count_brute.argtypes = [vp, i64, ctypes.c_int, vp, i64, ctypes.c_float, vp]
         L.orc_spatial_fill_brute.argtypes = [vp, i64, ctypes.c_int, vp, i64, ctypes.c_float, vp, vp]
         L.orc_nearest_brute.argtypes = [vp, i64, ctypes.c_int, vp, i64, ctypes.c_int, vp, vp]
+        L.orc_intersects_count_brute.argtypes = [vp, i64, ctypes.c_int, vp, i64, vp]
+        L.orc_intersects_fill_brute.argtypes = [vp, i64, ctypes.c_int, vp, i64, vp, vp]
+        L.orc_bvh_intersects_count.argtypes = [vp, vp, i64, vp]
+        L.orc_bvh_intersects_fill.argtypes = [vp, vp, i64, vp, vp]
         L.orc_bvh_build.restype = vp
         L.orc_bvh_build.argtypes = [vp, i64, ctypes.c_int]
         L.orc_bvh_free.argtypes = [vp]
@@ -127,6 +131,25 @@ def spatial_brute(prims: np.ndarray, queries: np.ndarray, r: float) -> Tuple[np.
     return offsets, indices
 
 
+def intersects_brute(prims: np.ndarray, qboxes: np.ndarray) -> Tuple[np.ndarray, np.ndarray]:
+    """All primitives whose box meets each query box (lo.xyz, hi.xyz), closed
+    intervals on every axis -- the spatial traversal of Sec. 2.2 with the box
+    intersection test of Sec. 2 as its predicate -- by brute force, as CSR
+    (offsets int64 [m+1], indices int32, rows ascending)."""
+    prims = _c(prims, np.float32)
+    qboxes = _c(qboxes, np.float32).reshape(-1, 6)
+    m = qboxes.shape[0]
+    counts = np.zeros(m, np.int64)
+    L = lib()
+    L.orc_intersects_count_brute(_p(prims), prims.shape[0], _kind_of(prims), _p(qboxes), m, _p(counts))
+    offsets = np.zeros(m + 1, np.int64)
+    np.cumsum(counts, out=offsets[1:])
+    indices = np.zeros(int(offsets[-1]), np.int32)
+    L.orc_intersects_fill_brute(_p(prims), prims.shape[0], _kind_of(prims), _p(qboxes), m, _p(offsets),
+                                _p(indices))
+    return offsets, indices
+
+
 def nearest_brute(prims: np.ndarray, queries: np.ndarray, k: int) -> Tuple[np.ndarray, np.ndarray]:
     """The min(k, n) nearest primitives of each query in (d^2, index) order
     (Sec. 2.2, nearest queries), by brute force: (indices int32 [m][kk],
@@ -174,6 +197,18 @@ class CpuBVH:
         indices = np.zeros(int(offsets[-1]), np.int32)
         lib().orc_bvh_spatial_fill(self._h, _p(queries), queries.shape[0], ctypes.c_float(r), _p(offsets),
                                    _p(indices))
+        return offsets, indices
+
+    def intersects(self, qboxes: np.ndarray) -> Tuple[np.ndarray, np.ndarray]:
+        """Box query (as ``intersects_brute``) through the median-split tree."""
+        qboxes = _c(qboxes, np.float32).reshape(-1, 6)
+        m = qboxes.shape[0]
+        counts = np.zeros(m, np.int64)
+        lib().orc_bvh_intersects_count(self._h, _p(qboxes), m, _p(counts))
+        offsets = np.zeros(m + 1, np.int64)
+        np.cumsum(counts, out=offsets[1:])
+        indices = np.zeros(int(offsets[-1]), np.int32)
+        lib().orc_bvh_intersects_fill(self._h, _p(qboxes), m, _p(offsets), _p(indices))
         return offsets, indices
 
     def nearest(self, queries: np.ndarray, k: int) -> Tuple[np.ndarray, np.ndarray]:

@@ -15,6 +15,10 @@
  *   - spatial query: every primitive whose AABB lies within distance r of the
  *     query point (Sec. 2.2, "Traversal for spatial queries"), read as the
  *     closed ball d^2 <= fl32(r*r);
+ *   - box query: every primitive whose AABB meets the query box, both taken
+ *     as closed intervals on each axis (lo_i <= qhi and hi_i >= qlo on x, y
+ *     and z); the spatial traversal of Sec. 2.2 with the box-intersection test
+ *     that Sec. 2 names as the AABB's cheap operation as its predicate;
  *   - nearest query: the min(k, n) primitives closest to the query point, ties
  *     broken by lower index, rows ordered by (d^2, index) (Sec. 2.2, "Traversal
  *     for nearest queries"; fewer than k when n < k, as the paper drops missing
@@ -239,6 +243,45 @@ void orc_spatial_fill_brute(const float *prims, int64_t n, int kind, const float
     if (finite3(q))
       for (int64_t i = 0; i < n; ++i)
         if (dist2_prim(prims, kind, i, q) <= r2) indices[o++] = (int32_t)i;
+  }
+}
+
+/* Box query predicate: the closed boxes [lo, hi] and [q[0..2], q[3..5]] meet
+ * on every axis.  Comparisons only; a NaN bound makes a comparison false. */
+static inline int boxes_meet(const float lo[3], const float hi[3], const float *q) {
+  for (int a = 0; a < 3; ++a)
+    if (!(lo[a] <= q[3 + a] && hi[a] >= q[a])) return 0;
+  return 1;
+}
+
+/* Box query, pass 1: counts[j] = number of primitives meeting query box j. */
+void orc_intersects_count_brute(const float *prims, int64_t n, int kind, const float *qboxes, int64_t m,
+                                int64_t *counts) {
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t j = 0; j < m; ++j) {
+    const float *q = qboxes + 6 * j;
+    int64_t c = 0;
+    for (int64_t i = 0; i < n; ++i) {
+      float lo[3], hi[3];
+      prim_box(prims, kind, i, lo, hi);
+      if (boxes_meet(lo, hi, q)) ++c;
+    }
+    counts[j] = c;
+  }
+}
+
+/* Box query, pass 2: row j of the CSR result in ascending index order. */
+void orc_intersects_fill_brute(const float *prims, int64_t n, int kind, const float *qboxes, int64_t m,
+                               const int64_t *offsets, int32_t *indices) {
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t j = 0; j < m; ++j) {
+    const float *q = qboxes + 6 * j;
+    int64_t o = offsets[j];
+    for (int64_t i = 0; i < n; ++i) {
+      float lo[3], hi[3];
+      prim_box(prims, kind, i, lo, hi);
+      if (boxes_meet(lo, hi, q)) indices[o++] = (int32_t)i;
+    }
   }
 }
 
@@ -483,6 +526,47 @@ void orc_bvh_spatial_fill(void *h, const float *queries, int64_t m, float r, con
   float r2 = r * r;
 #pragma omp parallel for schedule(dynamic, 256)
   for (int64_t j = 0; j < m; ++j) bvh_spatial_one(t, queries + 3 * j, r2, indices + offsets[j]);
+}
+
+/* Box query on the CPU BVH: a node is entered iff its box meets the query
+ * box (its box contains its members' boxes, so no match is skipped). */
+static int64_t bvh_intersects_one(const ctree *t, const float *q, int32_t *out) {
+  if (t->n == 0) return 0;
+  int64_t stack[128];
+  int sp = 0;
+  int64_t c = 0;
+  stack[sp++] = 0;
+  while (sp > 0) {
+    const cnode *nd = &t->nodes[stack[--sp]];
+    if (!boxes_meet(nd->lo, nd->hi, q)) continue;
+    if (nd->left < 0) {
+      for (int64_t s = nd->begin; s < nd->end; ++s) {
+        int64_t i = t->perm[s];
+        float lo[3], hi[3];
+        prim_box(t->prims, t->kind, i, lo, hi);
+        if (boxes_meet(lo, hi, q)) {
+          if (out) out[c] = (int32_t)i;
+          ++c;
+        }
+      }
+    } else {
+      stack[sp++] = nd->right;
+      stack[sp++] = nd->left;
+    }
+  }
+  return c;
+}
+
+void orc_bvh_intersects_count(void *h, const float *qboxes, int64_t m, int64_t *counts) {
+  const ctree *t = (const ctree *)h;
+#pragma omp parallel for schedule(dynamic, 256)
+  for (int64_t j = 0; j < m; ++j) counts[j] = bvh_intersects_one(t, qboxes + 6 * j, NULL);
+}
+
+void orc_bvh_intersects_fill(void *h, const float *qboxes, int64_t m, const int64_t *offsets, int32_t *indices) {
+  const ctree *t = (const ctree *)h;
+#pragma omp parallel for schedule(dynamic, 256)
+  for (int64_t j = 0; j < m; ++j) bvh_intersects_one(t, qboxes + 6 * j, indices + offsets[j]);
 }
 
 /* Nearest by stack traversal: the closer child is visited first; a node is

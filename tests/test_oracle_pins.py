@@ -352,3 +352,103 @@ def test_paper_shapes_count_statistics():
     o, _ = oracle.spatial_brute(datagen.paper_shape(p, "hollow_cube", 10), datagen.paper_shape(p, "hollow_sphere", 11), r)
     c = np.diff(o)
     assert 1.5 < c.mean() < 4.5 and c.min() == 0 and c.max() >= 8 * c.mean()
+
+
+# ------------------------------------------------------------------ box queries
+
+def _lattice_box_rows(side, qboxes):
+    """Rows of box queries over the side^3 lattice by integer enumeration: per axis the sites
+    from ceil(lo) to floor(hi), clipped to the grid (exact: the float32 bounds are exact in float64
+    and the sites are integers)."""
+    rows = []
+    for b in np.asarray(qboxes, np.float64):
+        axes = []
+        for a in range(3):
+            lo, hi = max(math.ceil(b[a]), 0), min(math.floor(b[3 + a]), side - 1)
+            axes.append(range(lo, hi + 1) if lo <= hi else range(0))
+        rows.append(sorted(x + side * y + side * side * z for z in axes[2] for y in axes[1] for x in axes[0]))
+    return rows
+
+
+def _lattice_query_boxes(side, m, seed):
+    g = np.random.default_rng(seed)
+    lo = g.uniform(-3, side + 2, (m, 3))
+    ext = g.uniform(0, 5, (m, 3)) * (g.random((m, 3)) < 0.9)  # some axes flat
+    qb = np.concatenate([lo, lo + ext], 1)
+    # integer bounds and zero-extent boxes at sites: every boundary case of the closed reading
+    ints = g.integers(-1, side + 1, (m // 4, 3)).astype(np.float64)
+    qb[: m // 4, :3] = ints
+    qb[: m // 4, 3:] = ints + g.integers(0, 3, (m // 4, 3)) * (g.random((m // 4, 1)) < 0.7)
+    return qb.astype(np.float32)
+
+
+@pytest.mark.parametrize("evaluator", ["brute", "bvh"])
+def test_box_query_lattice_rows_by_integer_enumeration(evaluator):
+    side = 16
+    pts = _lattice(side)
+    qb = _lattice_query_boxes(side, 600, 11)
+    want = _lattice_box_rows(side, qb)
+    off, idx = oracle.intersects_brute(pts, qb) if evaluator == "brute" else oracle.CpuBVH(pts).intersects(qb)
+    assert sum(len(r) for r in want) > 1000
+    for j, row in enumerate(want):
+        assert sorted(idx[off[j]:off[j + 1]].tolist()) == row, j
+
+
+def test_box_query_lattice_pin_catches_planted_mistakes():
+    # open intervals or a swapped axis pair give other rows on the same cases
+    side = 16
+    qb = _lattice_query_boxes(side, 600, 11)
+    want = _lattice_box_rows(side, qb)
+    strict = []
+    for b in np.asarray(qb, np.float64):
+        axes = [range(max(math.floor(b[a]) + 1, 0), min(math.ceil(b[3 + a]) - 1, side - 1) + 1) for a in range(3)]
+        strict.append(sorted(x + side * y + side * side * z for z in axes[2] for y in axes[1] for x in axes[0]))
+    assert strict != want
+    swapped = _lattice_box_rows(side, qb[:, [1, 0, 2, 4, 3, 5]])
+    assert swapped != want
+
+
+def test_box_query_unit_boxes_on_a_line_closed_form():
+    # boxes [i, i+1] x [0,1] x [0,1]: a query [a, b] on x meets box i iff i <= b and i + 1 >= a
+    n = 50
+    i = np.arange(n, dtype=np.float64)
+    prims = np.stack([i, 0 * i, 0 * i, i + 1, 0 * i + 1, 0 * i + 1], 1).astype(np.float32)
+    g = np.random.default_rng(5)
+    ab = np.sort(g.integers(-6, 2 * n + 6, (300, 2)) / 2.0, axis=1)
+    qb = np.stack([ab[:, 0], np.full(300, 0.25), np.full(300, 0.25), ab[:, 1], np.full(300, 0.75),
+                   np.full(300, 0.75)], 1).astype(np.float32)
+    for off, idx in (oracle.intersects_brute(prims, qb), oracle.CpuBVH(prims).intersects(qb)):
+        for j, (a, b) in enumerate(ab):
+            lo, hi = max(math.ceil(a) - 1, 0), min(math.floor(b), n - 1)
+            assert sorted(idx[off[j]:off[j + 1]].tolist()) == list(range(lo, hi + 1)), (a, b)
+
+
+def test_box_query_holds_the_ball_results():
+    # a point within distance r of q lies in the cube [q - r, q + r] (widened by 1e-3 r for the
+    # rounding of d^2): the box rows contain the radius rows
+    p = datagen.cube(4000, 3)
+    q = datagen.cube(500, 3, datagen.STREAM_QUERIES)
+    r = 0.06
+    off_s, idx_s = oracle.spatial_brute(p, q, r)
+    h = r * 1.001
+    qb = np.concatenate([q.astype(np.float64) - h, q.astype(np.float64) + h], 1).astype(np.float32)
+    off_b, idx_b = oracle.intersects_brute(p, qb)
+    assert np.all(np.diff(off_b) >= np.diff(off_s))
+    for j in range(500):
+        assert set(idx_s[off_s[j]:off_s[j + 1]].tolist()) <= set(idx_b[off_b[j]:off_b[j + 1]].tolist())
+    assert np.diff(off_b).sum() > np.diff(off_s).sum()  # the cube's corners hold more
+
+
+def test_box_query_nan_infinite_and_inverted_bounds():
+    inf = np.inf
+    pts = _lattice(4)
+    boxes = np.array([[0, 0, 0, 10, 10, 10], [20, 20, 20, 30, 30, 30]], np.float32)
+    qb = np.array([[np.nan, 0, 0, 3, 3, 3],        # NaN bound: nothing
+                   [-inf, -inf, -inf, inf, inf, inf],  # everything
+                   [6, -1, -1, 4, 11, 11],           # x inverted: the test alone decides
+                   [1, 1, 1, 1, 1, 1]], np.float32)  # a zero-extent box
+    off, idx = oracle.intersects_brute(pts, qb)
+    assert np.diff(off).tolist() == [0, 64, 0, 1] and idx[off[3]] == 1 + 4 + 16
+    off, idx = oracle.intersects_brute(boxes, qb)
+    # box [0,10]^3 meets the inverted x-interval [6, 4] (0 <= 4 and 10 >= 6); [20,30]^3 does not
+    assert [sorted(idx[off[j]:off[j + 1]].tolist()) for j in range(4)] == [[], [0, 1], [0], [0]]
