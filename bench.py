@@ -466,6 +466,7 @@ def run_gpu(args):
         line["query_ordering"] = ordering_extra(ab, p, q, r, k, topts)
         line["learned"] = learned_extra(ab, dev)
         line["batched"] = batched_extra(ab, dev)
+        line["intersects"] = intersects_extra(ab, dev, topts)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, p_h, q_h, r, k, n, m, budget_s=args.cpu_budget)
     if rank == 0:
@@ -495,9 +496,11 @@ def ordering_extra(ab, p, q, r, k, topts):
     included in the time) and in input order, with the internal nodes loaded per query."""
     out = {}
     for name, sq in (("sorted", 1), ("unsorted", 0)):
-        bvh = ab.BVH(p, sort_queries=sq, stats=1, **topts)
+        bvh = ab.BVH(p, sort_queries=sq, **topts)
         knn_ms = _time_ms(lambda: bvh.query_nearest(q, k))
         sp_ms = _time_ms(lambda: bvh.query_spatial(q, r))
+        bvh.destroy()
+        bvh = ab.BVH(p, sort_queries=sq, stats=1, **topts)  # node counts (instrumented, not timed)
         bvh.stats()
         bvh.query_nearest(q, k)
         nodes = bvh.stats()["nearest_nodes"] / q.shape[0]
@@ -507,6 +510,42 @@ def ordering_extra(ab, p, q, r, k, topts):
     out["knn_speedup_from_ordering"] = round(out["unsorted"]["knn_ms"] / out["sorted"]["knn_ms"], 2)
     out["spatial_speedup_from_ordering"] = round(out["unsorted"]["spatial_2p_ms"] / out["sorted"]["spatial_2p_ms"], 2)
     return out
+
+
+def intersects_extra(ab, dev, topts):
+    """Box-intersection queries over the 1e7-box tree (centres uniform in the unit cube, half-widths
+    uniform in [0, 1e-3]): 1e6 cube queries with the half-width that meets 10 boxes on average.
+    The query time includes the Morton order of the query boxes; rows go to a caller buffer."""
+    import torch
+    n, m = 10_000_000, 1_000_000
+    seed = datagen.SEED0 + 2
+    half = datagen.box_half_for_mean(n)
+    b = torch.from_numpy(datagen.boxes(n, seed)).to(dev)
+    qb = torch.from_numpy(datagen.query_cubes(m, seed, half)).to(dev)
+    idx = torch.empty(m * 32, dtype=torch.int32, device=dev)
+    build_ms = _time_ms(lambda: ab.BVH(b, **topts).destroy())
+    bvh = ab.BVH(b, **topts)
+
+    def query(t):
+        order = t.query_order_boxes(qb)
+        return t.query_intersects_async(qb, buffer_size=32, order=order, indices=idx)
+
+    query_ms = _time_ms(lambda: query(bvh))
+    off, _ = query(bvh)
+    bvh.check()
+    nnz = int(off[-1].item())
+    bvh.destroy()
+    sbvh = ab.BVH(b, stats=1, **topts)  # node counts from an instrumented tree (its atomics are not timed)
+    sbvh.stats()
+    query(sbvh)
+    nodes = sbvh.stats()["spatial_nodes"] / m
+    sbvh.destroy()
+    node_bytes = 24 * m + 4 * nnz + 64 * nodes * m
+    return {"workload": f"1e7 boxes (half-widths U[0,1e-3]), 1e6 cube queries of half-width {half:.4g}",
+            "build_ms": round(build_ms, 3), "build_mboxes_s": round(n / (build_ms * 1e-3) / 1e6, 1),
+            "query_ms": round(query_ms, 3), "query_mq_s": round(m / (query_ms * 1e-3) / 1e6, 1),
+            "hits_per_query": round(nnz / m, 2), "nodes_per_query": round(nodes, 2),
+            "node_fetch_gbs": round(node_bytes / (query_ms * 1e-3) / 1e9, 1)}
 
 
 def learned_extra(ab, dev):

@@ -217,6 +217,37 @@ ARBORX_API int arborx_query_spatial_buffered(arborx_handle h, const float *d_que
                                              int32_t buffer_size, const uint32_t *d_order, void *stream,
                                              int64_t *d_offsets, int32_t *d_indices, int64_t capacity);
 
+/* Traversal order of a set of query boxes: as arborx_query_order, with each box's centre
+ * 0.5 (lo + hi) in place of the point (a NaN centre sorts first).
+ *   d_boxes  device float[m][6] (lo.x, lo.y, lo.z, hi.x, hi.y, hi.z)
+ *   d_order  device uint32[m], written */
+ARBORX_API int arborx_query_order_boxes(arborx_handle h, const float *d_boxes, int64_t m, void *stream,
+                                        uint32_t *d_order);
+
+/* Spatial query with a box predicate (Sec. 2.2.1, where every node is tested against the query's
+ * predicate on its own; here the predicate is box intersection, the test AABBs make cheap, Sec. 2):
+ * row j lists every primitive whose box B (a point p is the box [p, p]) meets query box Q on every
+ * axis as closed intervals:  B.lo <= Q.hi  and  B.hi >= Q.lo.  Touching boxes match.  The test is
+ * comparisons only, so results are exact; a query box with a NaN bound matches nothing, infinite
+ * bounds are allowed, and a box with lo > hi on an axis matches what the same test accepts.
+ * One call with no host synchronisation (graph-capturable), in the one-pass form of
+ * arborx_query_spatial_buffered: a counting traversal that keeps the first `buffer_size` results
+ * of each row, the scan into d_offsets, the compaction, and a second traversal for the rows that
+ * overflowed the buffer.  d_offsets[m] receives the total on the device; entries at positions
+ * >= capacity are not written and set the CSR-overflow error (ARBORX_EOVERFLOW from
+ * arborx_check), with the offsets still complete so the caller can size a new buffer and repeat.
+ *   d_boxes      device float[m][6] (lo.xyz, hi.xyz), read only
+ *   buffer_size  1 <= buffer_size <= ARBORX_MAX_BUFFER_SIZE (speed only)
+ *   d_order      NULL (Morton order of the box centres when opts.sort_queries, else input order)
+ *                or a permutation of 0..m-1 from arborx_query_order_boxes
+ *   d_offsets    device int64[m + 1], written (original query order)
+ *   d_indices    device int32[capacity] (NULL when capacity == 0); rows are sets in traversal order
+ * Errors: ARBORX_EINVAL for a null handle, m out of range, a missing pointer or a bad
+ * buffer_size or capacity; ARBORX_ENOMEM when the row buffer cannot be allocated. */
+ARBORX_API int arborx_query_intersects(arborx_handle h, const float *d_boxes, int64_t m, int32_t buffer_size,
+                                       const uint32_t *d_order, void *stream, int64_t *d_offsets, int32_t *d_indices,
+                                       int64_t capacity);
+
 /* Release memory returned by arborx_query_spatial (stream-ordered on `stream`). */
 ARBORX_API int arborx_free(arborx_handle h, void *d_ptr, size_t bytes, void *stream);
 

@@ -8,7 +8,14 @@ from ._binding import (  # noqa: F401
     ARBORX_BOXES,
     ARBORX_BUILD_APETREI,
     ARBORX_BUILD_KARRAS,
+    ARBORX_ECUDA,
+    ARBORX_EINVAL,
+    ARBORX_ENOMEM,
+    ARBORX_EOVERFLOW,
+    ARBORX_ESTATE,
+    ARBORX_ETIMEOUT,
     ARBORX_MAX_K,
+    ARBORX_OK,
     ARBORX_POINTS,
     ArborXError,
     MLP_PARAMS,

@@ -89,6 +89,8 @@ def lib() -> ctypes.CDLL:
                                                           ctypes.POINTER(i64)]
         L.arborx_query_spatial_buffered_fill.argtypes = [vp, vp, i64, ctypes.c_float, vp, vp, vp, i64]
         L.arborx_query_spatial_buffered.argtypes = [vp, vp, i64, ctypes.c_float, i32, vp, vp, vp, vp, i64]
+        L.arborx_query_order_boxes.argtypes = [vp, vp, i64, vp, vp]
+        L.arborx_query_intersects.argtypes = [vp, vp, i64, i32, vp, vp, vp, vp, i64]
         L.arborx_batch_create.argtypes = [i64, vp, vp, vp, ctypes.POINTER(arborx_opts), vp, ctypes.POINTER(vp)]
         L.arborx_batch_entries.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]
         L.arborx_batch_run.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp]
@@ -194,6 +196,55 @@ class BVH:
         _check(lib().arborx_query_order(self.handle, _ptr(q), q.shape[0], _stream(), _ptr(order)),
                "arborx_query_order")
         return order
+
+    def query_order_boxes(self, boxes: torch.Tensor) -> torch.Tensor:
+        """Morton traversal order of a set of query boxes float32 [m, 6] (by box centre)."""
+        b = _as_f32_cuda(boxes, 6, "boxes")
+        order = torch.empty(b.shape[0], dtype=torch.int32, device=b.device)
+        _check(lib().arborx_query_order_boxes(self.handle, _ptr(b), b.shape[0], _stream(), _ptr(order)),
+               "arborx_query_order_boxes")
+        return order
+
+    def query_intersects_async(self, boxes: torch.Tensor, buffer_size: int = 16,
+                               order: Optional[torch.Tensor] = None, capacity: Optional[int] = None,
+                               indices: Optional[torch.Tensor] = None) -> Tuple[torch.Tensor, torch.Tensor]:
+        """Box-intersection query with no host synchronisation: (offsets int64 [m+1], indices int32
+        [capacity]); the first offsets[-1] entries of ``indices`` are the CSR rows.  ``capacity``
+        defaults to m * buffer_size; rows beyond it are dropped and ``check()`` raises."""
+        b = _as_f32_cuda(boxes, 6, "boxes")
+        m = b.shape[0]
+        offsets = torch.empty(m + 1, dtype=torch.int64, device=b.device)
+        if indices is None:
+            cap = int(m * buffer_size if capacity is None else capacity)
+            indices = torch.empty(max(cap, 1), dtype=torch.int32, device=b.device)
+        else:
+            cap = indices.numel() if capacity is None else int(capacity)
+            if indices.dtype != torch.int32 or not indices.is_cuda or indices.numel() < cap:
+                raise ValueError("indices must be an int32 CUDA tensor of at least `capacity` entries")
+        _check(lib().arborx_query_intersects(self.handle, _ptr(b), m, int(buffer_size), _ptr(order), _stream(),
+                                             _ptr(offsets), _ptr(indices), cap), "arborx_query_intersects")
+        self._async_keep = (b, order)  # inputs stay alive while the stream works
+        return offsets, indices
+
+    def query_intersects(self, boxes: torch.Tensor, buffer_size: int = 16,
+                         order: Optional[torch.Tensor] = None) -> Tuple[torch.Tensor, torch.Tensor]:
+        """Box-intersection query: (offsets int64 [m+1], indices int32 [nnz]).  Reads the total back
+        (synchronises) and, when the rows outgrew the first buffer, repeats with the exact size."""
+        b = _as_f32_cuda(boxes, 6, "boxes")
+        m = b.shape[0]
+        cap = max(m * int(buffer_size), 1)
+        while True:
+            offsets, idx = self.query_intersects_async(b, buffer_size, order=order, capacity=cap)
+            total = int(offsets[-1].item()) if m > 0 else 0
+            if total <= cap:
+                self.check()
+                return offsets, idx[:total]
+            try:
+                self.check()  # clears the overflow flag of the attempt that was too small
+            except ArborXError as e:
+                if e.code != ARBORX_EOVERFLOW:
+                    raise
+            cap = total
 
     def stats(self) -> dict:
         """Internal nodes loaded and queries traversed since the last call (needs stats=1)."""

@@ -330,12 +330,12 @@ int get_query_ws(arborx_bvh_s *h, int64_t m, cudaStream_t s, QueryWs *q) {
 // Morton-sort the queries against the tree's scene box; returns the
 // permutation (sorted position -> query index), or NULL for input order.
 int order_queries(arborx_bvh_s *h, const float *d_q, int64_t m, cudaStream_t s, QueryWs &q, const uint32_t **perm,
-                  const uint32_t *given = nullptr) {
+                  const uint32_t *given = nullptr, int kind = ARBORX_POINTS) {
   *perm = given;
   if (given || !h->opts.sort_queries || m < 2 || h->n == 0) return ARBORX_OK;
   cudaMemsetAsync(q.sortws, 0, q.sort_words * sizeof(uint32_t), s);
   const SortWs ws = sort_ws_carve<uint32_t>(q.sortws, m, kQueryKeyBits);
-  launch_morton<uint32_t>(d_q, (uint32_t)m, ARBORX_POINTS, h->meta, q.cA, ws.hist, ws.passes, false, s,
+  launch_morton<uint32_t>(d_q, (uint32_t)m, kind, h->meta, q.cA, ws.hist, ws.passes, false, s,
                           30 - kQueryKeyBits);
   uint32_t *sk, *pm;
   sort_pairs<uint32_t>(q.cA, q.cB, q.pA, q.pB, (uint32_t)m, ws, &h->meta->err, s, &sk, &pm);
@@ -887,7 +887,9 @@ int arborx_query_spatial_buffered(arborx_handle h, const float *d_queries, int64
   return launch_status();
 }
 
-int arborx_query_order(arborx_handle h, const float *d_queries, int64_t m, void *stream, uint32_t *d_order) {
+namespace {
+
+int query_order(arborx_handle h, const float *d_queries, int64_t m, int kind, void *stream, uint32_t *d_order) {
   if (!h || m < 0 || m >= ARBORX_MAX_QUERIES || (m > 0 && (!d_queries || !d_order))) return ARBORX_EINVAL;
   if (m == 0) return ARBORX_OK;
   const cudaStream_t s = (cudaStream_t)stream;
@@ -899,7 +901,7 @@ int arborx_query_order(arborx_handle h, const float *d_queries, int64_t m, void 
   if (h->n > 0 && m > 1) {
     cudaMemsetAsync(q.sortws, 0, q.sort_words * sizeof(uint32_t), s);
     const SortWs ws = sort_ws_carve<uint32_t>(q.sortws, m, kQueryKeyBits);
-    launch_morton<uint32_t>(d_queries, (uint32_t)m, ARBORX_POINTS, h->meta, q.cA, ws.hist, ws.passes, false, s,
+    launch_morton<uint32_t>(d_queries, (uint32_t)m, kind, h->meta, q.cA, ws.hist, ws.passes, false, s,
                             30 - kQueryKeyBits);
     uint32_t *sk, *pm;
     sort_pairs<uint32_t>(q.cA, q.cB, q.pA, q.pB, (uint32_t)m, ws, &h->meta->err, s, &sk, &pm);
@@ -910,6 +912,52 @@ int arborx_query_order(arborx_handle h, const float *d_queries, int64_t m, void 
   } else {
     launch_iota(d_order, (uint32_t)m, s);
   }
+  return launch_status();
+}
+
+}  // namespace
+
+int arborx_query_order(arborx_handle h, const float *d_queries, int64_t m, void *stream, uint32_t *d_order) {
+  return query_order(h, d_queries, m, ARBORX_POINTS, stream, d_order);
+}
+
+int arborx_query_order_boxes(arborx_handle h, const float *d_boxes, int64_t m, void *stream, uint32_t *d_order) {
+  return query_order(h, d_boxes, m, ARBORX_BOXES, stream, d_order);
+}
+
+int arborx_query_intersects(arborx_handle h, const float *d_boxes, int64_t m, int32_t buffer_size,
+                            const uint32_t *d_order, void *stream, int64_t *d_offsets, int32_t *d_indices,
+                            int64_t capacity) {
+  if (!h || m < 0 || m >= ARBORX_MAX_QUERIES || !d_offsets || (m > 0 && !d_boxes) || buffer_size < 1 ||
+      buffer_size > ARBORX_MAX_BUFFER_SIZE || capacity < 0 || (capacity > 0 && !d_indices))
+    return ARBORX_EINVAL;
+  const cudaStream_t s = (cudaStream_t)stream;
+  h->stream = s;
+  h->count_valid = false;
+  h->buffered_valid = false;
+  QueryWs q;
+  int st = get_query_ws(h, m, s, &q);
+  if (st) return st;
+  const size_t need = (size_t)m * buffer_size * sizeof(int32_t);
+  if (need > h->sbuf_bytes) {
+    dev_free(h->opts, h->sbuf, h->sbuf_bytes, s);
+    h->sbuf = (int32_t *)dev_alloc(h->opts, need, s);
+    h->sbuf_bytes = h->sbuf ? need : 0;
+    if (!h->sbuf) return ARBORX_ENOMEM;
+  }
+  const uint32_t *perm;
+  st = order_queries(h, d_boxes, m, s, q, &perm, d_order, ARBORX_BOXES);
+  if (st) return st;
+  uint32_t *ovf_count = q.miss + m;
+  cudaMemsetAsync(ovf_count, 0, sizeof(uint32_t), s);
+  const TravCfg cfg = trav_cfg(h, 0);
+  launch_spatial_buffered(h->rec, (uint32_t)h->n, d_boxes, perm, (uint32_t)m, 0.0f, q.counts, h->sbuf, buffer_size,
+                          q.miss, ovf_count, &h->meta->err, cfg, s, true);
+  launch_scan(q.counts, (uint32_t)m, d_offsets, q.scan_tmp, s);
+  launch_compact(h->sbuf, buffer_size, q.counts, d_offsets, (uint32_t)m, d_indices, capacity, &h->meta->err, s);
+  launch_spatial_fill(h->rec, (uint32_t)h->n, d_boxes, q.miss, (uint32_t)m, 0.0f, d_offsets, d_indices, capacity,
+                      &h->meta->err, cfg, s, ovf_count, true);
+  h->stat_queries[0] += (uint64_t)m;
   return launch_status();
 }
 

@@ -60,17 +60,20 @@ struct SpatialArgs {
   unsigned long long *stats;
 };
 
-// counts[j] (j in original query order) = number of primitives within r2
+// Spatial predicates: box = false, queries are points float[m][3] matched within r2; box = true,
+// queries are boxes float[m][6] (lo.xyz, hi.xyz) matched by closed-interval overlap (r2 unused).
+// counts[j] (j in original query order) = number of matching primitives
 void launch_spatial_count(const float4 *rec, uint32_t n, const float *queries, const uint32_t *qperm, uint32_t m,
-                          float r2, int32_t *counts, uint32_t *err, const TravCfg &cfg, cudaStream_t s);
+                          float r2, int32_t *counts, uint32_t *err, const TravCfg &cfg, cudaStream_t s,
+                          bool box = false);
 // fill rows at offsets[j]; m_dev (nullable) bounds the number of queries on the device
 void launch_spatial_fill(const float4 *rec, uint32_t n, const float *queries, const uint32_t *qperm, uint32_t m,
                          float r2, const int64_t *offsets, int32_t *indices, int64_t capacity, uint32_t *err,
-                         const TravCfg &cfg, cudaStream_t s, const uint32_t *m_dev = nullptr);
+                         const TravCfg &cfg, cudaStream_t s, const uint32_t *m_dev = nullptr, bool box = false);
 // one pass: counts + the first bs results of each query in buf; overflowing queries listed
 void launch_spatial_buffered(const float4 *rec, uint32_t n, const float *queries, const uint32_t *qperm, uint32_t m,
                              float r2, int32_t *counts, int32_t *buf, int bs, uint32_t *ovf_list, uint32_t *ovf_count,
-                             uint32_t *err, const TravCfg &cfg, cudaStream_t s);
+                             uint32_t *err, const TravCfg &cfg, cudaStream_t s, bool box = false);
 void launch_compact(const int32_t *buf, int bs, const int32_t *counts, const int64_t *offsets, uint32_t m,
                     int32_t *indices, int64_t capacity, uint32_t *err, cudaStream_t s);
 // exclusive scan counts[m] -> offsets[m+1]; tmp holds scan_tmp_words(m) int64

@@ -50,6 +50,14 @@ __device__ __forceinline__ bool pless(float d, int32_t i, float e, int32_t j) {
   return d < e || (d == e && i < j);
 }
 
+// Node-count statistics: one atomic per converged group of a warp (summed with a warp
+// reduction) instead of one per thread on the same counter.
+__device__ __forceinline__ void add_stat(unsigned long long *stats, uint32_t v) {
+  const unsigned act = __activemask();
+  const uint32_t sum = __reduce_add_sync(act, v);
+  if ((int)lane_id() == __ffs(act) - 1) atomicAdd(stats, (unsigned long long)sum);
+}
+
 // Queries flagged by a traversal (fewer than k hits inside a bound, or more
 // results than a row buffer holds): appended with one atomic per converged
 // group, in lane order (keeps the Morton order within a warp for the next pass).
@@ -70,7 +78,39 @@ __device__ __forceinline__ void append_flagged(bool flag, uint32_t qi, uint32_t 
 // fill pass.  m_dev (nullable) holds the number of queries on the device.
 enum : int { kCount = 0, kFill = 1, kBuffered = 2 };
 
-template <int MODE>
+// The spatial predicate of a query, applied alike to node boxes and primitive boxes (Sec. 2.2.1:
+// each node is tested on its own).  BOX = false: a point and r2, the box is a match when its FP32
+// squared distance to the point is at most r2.  BOX = true: a query box, closed intervals that
+// overlap on every axis.  Both are exact for pruning: a node box contains its children's boxes,
+// so its distance is no larger and its intervals reach at least as far.
+template <bool BOX>
+struct SpatialPred;
+
+template <>
+struct SpatialPred<false> {
+  float qx, qy, qz, r2;
+  __device__ __forceinline__ SpatialPred(const SpatialArgs &a, uint32_t qi)
+      : qx(__ldg(a.queries + 3 * (uint64_t)qi)), qy(__ldg(a.queries + 3 * (uint64_t)qi + 1)),
+        qz(__ldg(a.queries + 3 * (uint64_t)qi + 2)), r2(a.r2) {}
+  __device__ __forceinline__ bool valid() const { return finite3(qx, qy, qz); }
+  __device__ __forceinline__ bool operator()(float4 lo, float4 hi) const { return dist2_box(qx, qy, qz, lo, hi) <= r2; }
+};
+
+template <>
+struct SpatialPred<true> {
+  float lx, ly, lz, hx, hy, hz;
+  __device__ __forceinline__ SpatialPred(const SpatialArgs &a, uint32_t qi) {
+    const float *q = a.queries + 6 * (uint64_t)qi;
+    lx = __ldg(q); ly = __ldg(q + 1); lz = __ldg(q + 2);
+    hx = __ldg(q + 3); hy = __ldg(q + 4); hz = __ldg(q + 5);
+  }
+  __device__ __forceinline__ bool valid() const { return true; }  // a NaN bound fails every test below
+  __device__ __forceinline__ bool operator()(float4 lo, float4 hi) const {
+    return lo.x <= hx && hi.x >= lx && lo.y <= hy && hi.y >= ly && lo.z <= hz && hi.z >= lz;
+  }
+};
+
+template <int MODE, bool BOX>
 __global__ void __launch_bounds__(kMaxBlock) k_spatial(const __grid_constant__ SpatialArgs a) {
   extern __shared__ int32_t s_stack[];
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -78,11 +118,8 @@ __global__ void __launch_bounds__(kMaxBlock) k_spatial(const __grid_constant__ S
   if (t >= m) return;
   const float4 *__restrict__ rec = a.rec;
   const uint32_t n = a.n;
-  const float r2 = a.r2;
   const uint32_t qi = a.qperm ? __ldg(a.qperm + t) : t;
-  const float qx = __ldg(a.queries + 3 * (uint64_t)qi);
-  const float qy = __ldg(a.queries + 3 * (uint64_t)qi + 1);
-  const float qz = __ldg(a.queries + 3 * (uint64_t)qi + 2);
+  const SpatialPred<BOX> hit(a, qi);
   int64_t base = 0;
   if (MODE == kFill) base = __ldg(a.offsets + qi);
   if (MODE == kBuffered) base = (int64_t)qi * a.bs;
@@ -101,9 +138,9 @@ __global__ void __launch_bounds__(kMaxBlock) k_spatial(const __grid_constant__ S
     ++cnt;                                                \
   } while (0)
 
-  if (n > 0 && finite3(qx, qy, qz)) {
+  if (n > 0 && hit.valid()) {
     const float4 r0 = __ldg(rec), r1 = __ldg(rec + 1);
-    if (dist2_box(qx, qy, qz, r0, r1) <= r2) {
+    if (hit(r0, r1)) {
       const int e0 = __float_as_int(r0.w);
       if (e0 < 0) {
         ABX_EMIT(~e0);
@@ -124,8 +161,8 @@ __global__ void __launch_bounds__(kMaxBlock) k_spatial(const __grid_constant__ S
           ld_slot(rp, a0, a1);
           ld_slot(rp + 2, b0, b1);
           ++visited;
-          const bool hl = dist2_box(qx, qy, qz, a0, a1) <= r2;
-          const bool hr = dist2_box(qx, qy, qz, b0, b1) <= r2;
+          const bool hl = hit(a0, a1);
+          const bool hr = hit(b0, b1);
           const int el = __float_as_int(a0.w), er = __float_as_int(b0.w);
           if (hl && el < 0) ABX_EMIT(~el);
           if (hr && er < 0) ABX_EMIT(~er);
@@ -157,7 +194,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_spatial(const __grid_constant__ S
 #undef ABX_EMIT
   if (MODE != kFill) a.counts[qi] = (int32_t)cnt;
   if (MODE == kBuffered) append_flagged(cnt > (uint32_t)a.bs, qi, a.ovf_list, a.ovf_count);
-  if (a.stats) atomicAdd(a.stats, (unsigned long long)visited);
+  if (a.stats) add_stat(a.stats, visited);
 }
 
 // Move buffered rows (those that fit) to their CSR place.  A thread takes
@@ -556,7 +593,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_nearest(const __grid_constant__ N
     if (a.miss_list) append_flagged(ok && H.bound_idx() == INT_MAX, pos, a.miss_list, a.miss_count);
     H.write(row, kk, out_idx, out_d2);
   }
-  if (a.stats) atomicAdd(a.stats, (unsigned long long)visited);
+  if (a.stats) add_stat(a.stats, visited);
 }
 
 // Batched clouds: persistent warps take tiles of 32 sorted query positions from
@@ -696,12 +733,21 @@ void launch_iota(uint32_t *out, uint32_t m, cudaStream_t s) {
   k_iota<<<ceil_div<uint32_t>(m, 256u), 256, 0, s>>>(out, m);
 }
 
+template <int MODE, bool BOX>
+static void spatial_launch2(const SpatialArgs &args, int block, size_t smem, cudaStream_t s) {
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_spatial<MODE, BOX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_spatial<MODE, BOX><<<ceil_div<uint32_t>(args.m, block), block, smem, s>>>(args);
+}
+
 template <int MODE>
-static void spatial_launch(const SpatialArgs &args, int block, cudaStream_t s, const char *name) {
+static void spatial_launch(const SpatialArgs &args, bool box, int block, cudaStream_t s, const char *name) {
   const size_t smem = (size_t)args.stack_smem * block * sizeof(int32_t);
-  prof::Scope ps(s, name);
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k_spatial<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_spatial<MODE><<<ceil_div<uint32_t>(args.m, block), block, smem, s>>>(args);
+  prof::Scope ps(s, box ? (MODE == kBuffered ? "intersects_buffered" : MODE == kFill ? "intersects_fill"
+                                                                                     : "intersects_count")
+                        : name);
+  if (box) spatial_launch2<MODE, true>(args, block, smem, s);
+  else spatial_launch2<MODE, false>(args, block, smem, s);
 }
 
 static SpatialArgs spatial_args(const float4 *rec, uint32_t n, const float *queries, const uint32_t *qperm, uint32_t m,
@@ -720,28 +766,28 @@ static SpatialArgs spatial_args(const float4 *rec, uint32_t n, const float *quer
 }
 
 void launch_spatial_count(const float4 *rec, uint32_t n, const float *queries, const uint32_t *qperm, uint32_t m,
-                          float r2, int32_t *counts, uint32_t *err, const TravCfg &cfg, cudaStream_t s) {
+                          float r2, int32_t *counts, uint32_t *err, const TravCfg &cfg, cudaStream_t s, bool box) {
   if (m == 0) return;
   SpatialArgs a = spatial_args(rec, n, queries, qperm, m, r2, err, cfg);
   a.counts = counts;
-  spatial_launch<kCount>(a, cfg.block, s, "spatial_count");
+  spatial_launch<kCount>(a, box, cfg.block, s, "spatial_count");
 }
 
 void launch_spatial_fill(const float4 *rec, uint32_t n, const float *queries, const uint32_t *qperm, uint32_t m,
                          float r2, const int64_t *offsets, int32_t *indices, int64_t capacity, uint32_t *err,
-                         const TravCfg &cfg, cudaStream_t s, const uint32_t *m_dev) {
+                         const TravCfg &cfg, cudaStream_t s, const uint32_t *m_dev, bool box) {
   if (m == 0) return;
   SpatialArgs a = spatial_args(rec, n, queries, qperm, m, r2, err, cfg);
   a.offsets = offsets;
   a.indices = indices;
   a.capacity = capacity;
   a.m_dev = m_dev;
-  spatial_launch<kFill>(a, cfg.block, s, "spatial_fill");
+  spatial_launch<kFill>(a, box, cfg.block, s, "spatial_fill");
 }
 
 void launch_spatial_buffered(const float4 *rec, uint32_t n, const float *queries, const uint32_t *qperm, uint32_t m,
                              float r2, int32_t *counts, int32_t *buf, int bs, uint32_t *ovf_list, uint32_t *ovf_count,
-                             uint32_t *err, const TravCfg &cfg, cudaStream_t s) {
+                             uint32_t *err, const TravCfg &cfg, cudaStream_t s, bool box) {
   if (m == 0) return;
   SpatialArgs a = spatial_args(rec, n, queries, qperm, m, r2, err, cfg);
   a.counts = counts;
@@ -749,7 +795,7 @@ void launch_spatial_buffered(const float4 *rec, uint32_t n, const float *queries
   a.bs = bs;
   a.ovf_list = ovf_list;
   a.ovf_count = ovf_count;
-  spatial_launch<kBuffered>(a, cfg.block, s, "spatial_buffered");
+  spatial_launch<kBuffered>(a, box, cfg.block, s, "spatial_buffered");
 }
 
 void launch_compact(const int32_t *buf, int bs, const int32_t *counts, const int64_t *offsets, uint32_t m,
