@@ -463,10 +463,15 @@ def run_gpu(args):
         "clocks": clocks,
     }
     if rank == 0 and not args.no_extras:
-        line["query_ordering"] = ordering_extra(ab, p, q, r, k, topts)
-        line["learned"] = learned_extra(ab, dev)
-        line["batched"] = batched_extra(ab, dev)
-        line["intersects"] = intersects_extra(ab, dev, topts)
+        extras = set(args.extras.split(","))
+        if "query_ordering" in extras:
+            line["query_ordering"] = ordering_extra(ab, p, q, r, k, topts)
+        if "learned" in extras:
+            line["learned"] = learned_extra(ab, dev)
+        if "batched" in extras:
+            line["batched"] = batched_extra(ab, dev)
+        if "intersects" in extras:
+            line["intersects"] = intersects_extra(ab, dev, topts)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, p_h, q_h, r, k, n, m, budget_s=args.cpu_budget)
     if rank == 0:
@@ -699,6 +704,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the learned-bound and batched measurements")
+    ap.add_argument("--extras", default="query_ordering,learned,batched,intersects",
+                    help="comma-separated extra measurements to run (after the headline step)")
     ap.add_argument("--no-tune", action="store_true", help="default launch parameters instead of the autotuner's")
     ap.add_argument("--launch", default=None,
                     help="block,stack,buffer: fixed traversal launch parameters (skips the autotuner)")

@@ -111,7 +111,7 @@ struct SpatialPred<true> {
 };
 
 template <int MODE, bool BOX>
-__global__ void __launch_bounds__(kMaxBlock) k_spatial(const __grid_constant__ SpatialArgs a) {
+__device__ __forceinline__ void spatial_traverse(const SpatialArgs &a) {
   extern __shared__ int32_t s_stack[];
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t m = a.m_dev ? min(a.m, *a.m_dev) : a.m;
@@ -195,6 +195,17 @@ __global__ void __launch_bounds__(kMaxBlock) k_spatial(const __grid_constant__ S
   if (MODE != kFill) a.counts[qi] = (int32_t)cnt;
   if (MODE == kBuffered) append_flagged(cnt > (uint32_t)a.bs, qi, a.ovf_list, a.ovf_count);
   if (a.stats) add_stat(a.stats, visited);
+}
+
+// Radius queries (points within r) and box queries (boxes met), one kernel name each.
+template <int MODE>
+__global__ void __launch_bounds__(kMaxBlock) k_spatial(const __grid_constant__ SpatialArgs a) {
+  spatial_traverse<MODE, false>(a);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kMaxBlock) k_intersects(const __grid_constant__ SpatialArgs a) {
+  spatial_traverse<MODE, true>(a);
 }
 
 // Move buffered rows (those that fit) to their CSR place.  A thread takes
@@ -733,11 +744,10 @@ void launch_iota(uint32_t *out, uint32_t m, cudaStream_t s) {
   k_iota<<<ceil_div<uint32_t>(m, 256u), 256, 0, s>>>(out, m);
 }
 
-template <int MODE, bool BOX>
-static void spatial_launch2(const SpatialArgs &args, int block, size_t smem, cudaStream_t s) {
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(k_spatial<MODE, BOX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_spatial<MODE, BOX><<<ceil_div<uint32_t>(args.m, block), block, smem, s>>>(args);
+template <class F>
+static void spatial_launch2(F *kernel, const SpatialArgs &args, int block, size_t smem, cudaStream_t s) {
+  if (smem > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  kernel<<<ceil_div<uint32_t>(args.m, block), block, smem, s>>>(args);
 }
 
 template <int MODE>
@@ -746,8 +756,8 @@ static void spatial_launch(const SpatialArgs &args, bool box, int block, cudaStr
   prof::Scope ps(s, box ? (MODE == kBuffered ? "intersects_buffered" : MODE == kFill ? "intersects_fill"
                                                                                      : "intersects_count")
                         : name);
-  if (box) spatial_launch2<MODE, true>(args, block, smem, s);
-  else spatial_launch2<MODE, false>(args, block, smem, s);
+  if (box) spatial_launch2(k_intersects<MODE>, args, block, smem, s);
+  else spatial_launch2(k_spatial<MODE>, args, block, smem, s);
 }
 
 static SpatialArgs spatial_args(const float4 *rec, uint32_t n, const float *queries, const uint32_t *qperm, uint32_t m,
