@@ -29,6 +29,7 @@ constexpr int kHeapDefer = 8;  // deferred-insert buffer of the shared-memory he
 constexpr int kHeapFrom = 17;  // smallest k served by the shared-memory heap
 static_assert(kHeapFrom <= 17, "register lists exist for k <= 16 only");
 constexpr int kBatchHeapK = 32;             // largest k of the batched path (heap class)
+constexpr bool kSpatialDual = true;         // spatial traversals load two nodes per iteration
 
 
 // one 32-byte child slot (lo, hi) in a single 256-bit read-only load that does not allocate in L1
@@ -150,43 +151,74 @@ __device__ __forceinline__ void spatial_traverse(const SpatialArgs &a) {
         const int stack_smem = a.stack_smem;
         int32_t spill[kSpill];
         int sp = 0;
+        auto push = [&](int v) {
+          if (sp < stack_smem) {
+            my[sp * stride] = v;
+            ++sp;
+          } else if (sp - stack_smem < kSpill) {
+            spill[sp - stack_smem] = v;
+            ++sp;
+          } else {
+            set_err(a.err, ERR_STACK);  // cannot happen: capacity exceeds the deepest LBVH
+          }
+        };
+        auto pop = [&]() {
+          --sp;
+          return sp < stack_smem ? my[sp * stride] : spill[sp - stack_smem];
+        };
         int node = e0;
         while (true) {
-          if ((uint32_t)node >= n - 1) {  // corrupt tree: never read outside the records
+          // a second node, the stack top, is loaded alongside the current one: two independent
+          // node loads in flight per lane (the order of a spatial traversal is free).  Taken only
+          // while the stack is within its shared part, so the depth bound of the single-node
+          // traversal still holds beyond it.
+          int nb = -1;
+          if (kSpatialDual && sp > 0 && sp <= stack_smem) nb = pop();
+          if ((uint32_t)node >= n - 1 || (nb >= 0 && (uint32_t)nb >= n - 1)) {  // corrupt tree
             set_err(a.err, ERR_STACK);
             break;
           }
           const float4 *rp = rec + 4 + 4 * (uint64_t)node;
-          float4 a0, a1, b0, b1;
+          float4 a0, a1, b0, b1, c0, c1, d0, d1;
           ld_slot(rp, a0, a1);
           ld_slot(rp + 2, b0, b1);
-          ++visited;
+          if (nb >= 0) {
+            const float4 *rq = rec + 4 + 4 * (uint64_t)nb;
+            ld_slot(rq, c0, c1);
+            ld_slot(rq + 2, d0, d1);
+          }
+          visited += nb >= 0 ? 2 : 1;
           const bool hl = hit(a0, a1);
           const bool hr = hit(b0, b1);
           const int el = __float_as_int(a0.w), er = __float_as_int(b0.w);
           if (hl && el < 0) ABX_EMIT(~el);
           if (hr && er < 0) ABX_EMIT(~er);
-          const bool gl = hl && el >= 0, gr = hr && er >= 0;
-          if (gl) {
-            if (gr) {
-              if (sp < stack_smem) {
-                my[sp * stride] = er;
-                ++sp;
-              } else if (sp - stack_smem < kSpill) {
-                spill[sp - stack_smem] = er;
-                ++sp;
-              } else {
-                set_err(a.err, ERR_STACK);  // cannot happen: capacity exceeds the deepest LBVH
-              }
-            }
-            node = el;
-          } else if (gr) {
-            node = er;
-          } else {
-            if (sp == 0) break;
-            --sp;
-            node = sp < stack_smem ? my[sp * stride] : spill[sp - stack_smem];
+          int next = -1;
+          if (hl && el >= 0) next = el;
+          if (hr && er >= 0) {
+            if (next < 0) next = er;
+            else push(er);
           }
+          if (nb >= 0) {
+            const bool hl2 = hit(c0, c1);
+            const bool hr2 = hit(d0, d1);
+            const int el2 = __float_as_int(c0.w), er2 = __float_as_int(d0.w);
+            if (hl2 && el2 < 0) ABX_EMIT(~el2);
+            if (hr2 && er2 < 0) ABX_EMIT(~er2);
+            if (hl2 && el2 >= 0) {
+              if (next < 0) next = el2;
+              else push(el2);
+            }
+            if (hr2 && er2 >= 0) {
+              if (next < 0) next = er2;
+              else push(er2);
+            }
+          }
+          if (next < 0) {
+            if (sp == 0) break;
+            next = pop();
+          }
+          node = next;
         }
       }
     }
