@@ -45,8 +45,11 @@ __device__ __forceinline__ void block_excl_scan2(uint32_t a, uint32_t b, uint32_
   b_ex = wb + y - b;
 }
 
+// Four resident 256-thread blocks per SM (64 registers): the values are read only when the tile
+// is staged, so they hold no registers while the keys are ranked (measured 85.4 -> 82.4 us per
+// pass of 1e7 keys against three blocks of 80 registers; five blocks spill heavily).
 template <typename K, bool FIRST>
-__global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(const K *__restrict__ kin, const uint32_t *__restrict__ vin,
+__global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(const K *__restrict__ kin, const uint32_t *__restrict__ vin,
                                                           K *__restrict__ kout, uint32_t *__restrict__ vout,
                                                           uint32_t n, int shift, const uint32_t *__restrict__ hist,
                                                           uint32_t *__restrict__ status,
@@ -70,18 +73,11 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(const K *__restric
   const uint32_t wbase = tbase + warp * (uint32_t)(ITEMS * 32);
 
   K k[ITEMS];
-  uint32_t v[ITEMS];
   uint32_t rk[ITEMS];
 #pragma unroll
   for (int i = 0; i < ITEMS; ++i) {
     const uint32_t pos = wbase + i * 32 + lane;
-    if (pos < n) {
-      k[i] = __ldcs(kin + pos);  // read once per pass: evict first (measured 7% faster)
-      v[i] = FIRST ? pos : __ldcs(vin + pos);
-    } else {
-      k[i] = 0;
-      v[i] = 0;
-    }
+    k[i] = pos < n ? __ldcs(kin + pos) : (K)0;  // read once per pass: evict first (measured 7% faster)
   }
 
   // warp-level ranking in input order (item-major, lane-minor): the lanes
@@ -134,7 +130,8 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(const K *__restric
   __syncthreads();  // s_dstart and the warp offsets are complete
 
   // stage in digit order (needs only tile-local offsets, so it runs before the
-  // look-back and gives the predecessors time to publish)
+  // look-back and gives the predecessors time to publish); the values are read only
+  // here, so they hold no registers during the ranking
 #pragma unroll
   for (int i = 0; i < ITEMS; ++i) {
     const uint32_t pos = wbase + i * 32 + lane;
@@ -142,7 +139,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(const K *__restric
       const uint32_t dd = (uint32_t)(k[i] >> shift) & (kRadix - 1);
       const uint32_t p = s_dstart[dd] + s_whist[warp][dd] + rk[i];
       s_k[p] = k[i];
-      s_v[p] = v[i];
+      s_v[p] = FIRST ? pos : __ldcs(vin + pos);
     }
   }
 
