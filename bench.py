@@ -236,6 +236,182 @@ def kernel_bytes(name, n, m, k, nnz, nodes):
 
 # ---------------------------------------------------------------- GPU arm
 
+def measure_e2e(ab, args, dev, stream, flush, barrier, ws, p, q, p_h, q_h, r, k, n, m, nnz, topts, bsz, idx_buf):
+    """End to end through the public API: every batch copies its points and queries from pinned
+    host memory and its results (CSR rows, k-NN rows and distances) back.  Reported for a stream
+    of batches (the value) and for one batch at a time."""
+    import torch
+    p_pin = torch.from_numpy(p_h).pin_memory()
+    q_pin = torch.from_numpy(q_h).pin_memory()
+    kk = min(k, n)
+    outs = dict(off=torch.empty(m + 1, dtype=torch.int64).pin_memory(),
+                kidx=torch.empty((m, kk), dtype=torch.int32).pin_memory(),
+                kd2=torch.empty((m, kk), dtype=torch.float32).pin_memory())
+    idx_pin = torch.empty(max(nnz, 1) * 2, dtype=torch.int32).pin_memory()
+    pd = torch.empty_like(p)
+    qd = torch.empty_like(q)
+
+    cs = torch.cuda.Stream(device=dev)  # copy stream: overlaps transfers with the compute stream
+    nnz_pin = torch.empty(1, dtype=torch.int64).pin_memory()
+    ev_q = torch.cuda.Event()
+    ev_sp = torch.cuda.Event()
+    ev_ka = torch.cuda.Event()
+    mh = m // 2
+
+    def e2e_step():
+        pd.copy_(p_pin, non_blocking=True)  # compute stream: the build needs every point
+        cs.wait_stream(stream)
+        with torch.cuda.stream(cs):
+            qd.copy_(q_pin, non_blocking=True)  # uploads while the tree builds
+            ev_q.record(cs)
+        bvh = ab.BVH(pd, **topts)
+        stream.wait_event(ev_q)
+        order = bvh.query_order(qd)
+        if bsz > 0:
+            off, idx = bvh.query_spatial_async(qd, r, buffer_size=bsz, order=order, indices=idx_buf)
+        else:
+            off, idx = bvh.query_spatial(qd, r, order=order)
+        ev_sp.record(stream)
+        # k-NN over the two halves of the query array (each in its own Morton order), so the
+        # first half's rows download while the second half is computed
+        oa, ob = bvh.query_order(qd[:mh]), bvh.query_order(qd[mh:])
+        ka, da = bvh.query_nearest(qd[:mh], k, order=oa)
+        ev_ka.record(stream)
+        with torch.cuda.stream(cs):
+            cs.wait_event(ev_sp)
+            off.record_stream(cs)
+            idx.record_stream(cs)
+            outs["off"].copy_(off, non_blocking=True)  # downloads while the k-NN kernels run
+            nnz_pin.copy_(off[-1:], non_blocking=True)
+        cs.synchronize()  # the row total; the k-NN work is already queued on the compute stream
+        got = int(nnz_pin[0])
+        kb, db = bvh.query_nearest(qd[mh:], k, order=ob)
+        with torch.cuda.stream(cs):
+            idx_pin[:got].copy_(idx[:got], non_blocking=True)
+            cs.wait_event(ev_ka)
+            ka.record_stream(cs)
+            da.record_stream(cs)
+            outs["kidx"][:mh].copy_(ka, non_blocking=True)
+            outs["kd2"][:mh].copy_(da, non_blocking=True)
+        outs["kidx"][mh:].copy_(kb, non_blocking=True)
+        outs["kd2"][mh:].copy_(db, non_blocking=True)
+        stream.wait_stream(cs)  # join the copies before the end event
+        bvh.destroy()
+        return got
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_ms = 0.0
+    d2h = 0
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        got = e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
+        d2h = (m + 1) * 8 + got * 4 + m * kk * 8
+    lat_ms = max_over_ranks(e2e_ms / args.steps, ws, dev)
+    lat_value = ws * 2 * m / (lat_ms * 1e-3) / 1e6
+
+    # A stream of independent batches, as a service runs them: batch i+1 uploads on its own copy
+    # stream while batch i is computed and downloaded on a third.  Every batch still copies its
+    # inputs from pinned host memory and its results back; two sets of device buffers alternate.
+    NB = 2
+    up, down = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+    pdb = [torch.empty_like(p) for _ in range(NB)]
+    qdb = [torch.empty_like(q) for _ in range(NB)]
+    ibuf = [torch.empty(max(nnz, 1) * 2, dtype=torch.int32, device=dev) for _ in range(NB)]
+    outb = [dict(off=torch.empty(m + 1, dtype=torch.int64).pin_memory(),
+                 nnz=torch.empty(1, dtype=torch.int64).pin_memory(),
+                 kidx=torch.empty((m, kk), dtype=torch.int32).pin_memory(),
+                 kd2=torch.empty((m, kk), dtype=torch.float32).pin_memory(),
+                 idx=torch.empty(max(nnz, 1) * 2, dtype=torch.int32).pin_memory()) for _ in range(NB)]
+    ev_in = [torch.cuda.Event() for _ in range(NB)]    # inputs uploaded
+    ev_done = [torch.cuda.Event() for _ in range(NB)]  # computed: input buffers free again
+    ev_off = [torch.cuda.Event() for _ in range(NB)]   # offsets (row total) on the host
+    ev_idx = [torch.cuda.Event() for _ in range(NB)]   # rows on the host: row buffer free again
+    bsz_p = bsz if bsz > 0 else 32
+
+    def upload(i):
+        b = i % NB
+        with torch.cuda.stream(up):
+            up.wait_event(ev_done[b])  # the batch that last read these buffers is computed
+            pdb[b].copy_(p_pin, non_blocking=True)
+            qdb[b].copy_(q_pin, non_blocking=True)
+            ev_in[b].record(up)
+
+    def issue(i):
+        b = i % NB
+        stream.wait_event(ev_in[b])
+        bvh = ab.BVH(pdb[b], **topts)
+        order = bvh.query_order(qdb[b])
+        stream.wait_event(ev_idx[b])  # the row buffer's previous rows are on the host
+        off, _ = bvh.query_spatial_async(qdb[b], r, buffer_size=bsz_p, order=order, indices=ibuf[b])
+        kidx, kd2 = bvh.query_nearest(qdb[b], k, order=order)
+        ev_done[b].record(stream)
+        bvh.destroy()
+        with torch.cuda.stream(down):
+            down.wait_event(ev_done[b])
+            for t in (off, kidx, kd2):
+                t.record_stream(down)
+            outb[b]["off"].copy_(off, non_blocking=True)
+            outb[b]["nnz"].copy_(off[-1:], non_blocking=True)
+            ev_off[b].record(down)
+            outb[b]["kidx"].copy_(kidx, non_blocking=True)
+            outb[b]["kd2"].copy_(kd2, non_blocking=True)
+        return b
+
+    def finish(b):  # the rows of batch b once its total is on the host
+        ev_off[b].synchronize()
+        got = int(outb[b]["nnz"][0])
+        with torch.cuda.stream(down):
+            outb[b]["idx"][:got].copy_(ibuf[b][:got], non_blocking=True)
+            ev_idx[b].record(down)
+        return got
+
+    def stream_batches(count):
+        prev, got = None, 0
+        upload(0)
+        for i in range(count):
+            if i + 1 < count:
+                upload(i + 1)  # queued at once: the copy engine starts as soon as its buffers are free
+            b = issue(i)
+            if prev is not None:
+                got += finish(prev)
+            prev = b
+        return got + finish(prev)
+
+    stream_batches(max(1, args.warmup))
+    torch.cuda.synchronize()
+    barrier()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(up)
+    got_all = stream_batches(args.steps)
+    stream.wait_stream(up)
+    stream.wait_stream(down)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(t0.elapsed_time(t1) / args.steps, ws, dev)
+    e2e_value = ws * 2 * m / (e2e_ms * 1e-3) / 1e6
+    d2h = (m + 1) * 8 + got_all // args.steps * 4 + m * kk * 8
+
+    e2e = {"value": round(e2e_value, 3), "unit": UNIT, "ms_per_step": round(e2e_ms, 4),
+           "h2d_bytes_per_step": int(p_h.nbytes + q_h.nbytes), "d2h_bytes_per_step": int(d2h),
+           "pipelined": f"{args.steps} batches in one timed region: batch i+1 uploads while batch i is "
+                        "computed and downloaded (three streams, two buffer sets)",
+           "single_batch": {"value": round(lat_value, 3), "ms_per_step": round(lat_ms, 4),
+                            "overlap": "queries upload during the build, spatial rows download during the "
+                                       "k-NN query, k-NN in two halves with the first half's rows "
+                                       "downloading during the second"}}
+    return e2e
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -333,174 +509,8 @@ def run_gpu(args):
     # ---- end to end: pinned host buffers in, results back to host, every step
     e2e = None
     if not args.no_e2e:
-        p_pin = torch.from_numpy(p_h).pin_memory()
-        q_pin = torch.from_numpy(q_h).pin_memory()
-        kk = min(k, n)
-        outs = dict(off=torch.empty(m + 1, dtype=torch.int64).pin_memory(),
-                    kidx=torch.empty((m, kk), dtype=torch.int32).pin_memory(),
-                    kd2=torch.empty((m, kk), dtype=torch.float32).pin_memory())
-        idx_pin = torch.empty(max(nnz, 1) * 2, dtype=torch.int32).pin_memory()
-        pd = torch.empty_like(p)
-        qd = torch.empty_like(q)
-
-        cs = torch.cuda.Stream(device=dev)  # copy stream: overlaps transfers with the compute stream
-        nnz_pin = torch.empty(1, dtype=torch.int64).pin_memory()
-        ev_q = torch.cuda.Event()
-        ev_sp = torch.cuda.Event()
-        ev_ka = torch.cuda.Event()
-        mh = m // 2
-
-        def e2e_step():
-            pd.copy_(p_pin, non_blocking=True)  # compute stream: the build needs every point
-            cs.wait_stream(stream)
-            with torch.cuda.stream(cs):
-                qd.copy_(q_pin, non_blocking=True)  # uploads while the tree builds
-                ev_q.record(cs)
-            bvh = ab.BVH(pd, **topts)
-            stream.wait_event(ev_q)
-            order = bvh.query_order(qd)
-            if bsz > 0:
-                off, idx = bvh.query_spatial_async(qd, r, buffer_size=bsz, order=order, indices=idx_buf)
-            else:
-                off, idx = bvh.query_spatial(qd, r, order=order)
-            ev_sp.record(stream)
-            # k-NN over the two halves of the query array (each in its own Morton order), so the
-            # first half's rows download while the second half is computed
-            oa, ob = bvh.query_order(qd[:mh]), bvh.query_order(qd[mh:])
-            ka, da = bvh.query_nearest(qd[:mh], k, order=oa)
-            ev_ka.record(stream)
-            with torch.cuda.stream(cs):
-                cs.wait_event(ev_sp)
-                off.record_stream(cs)
-                idx.record_stream(cs)
-                outs["off"].copy_(off, non_blocking=True)  # downloads while the k-NN kernels run
-                nnz_pin.copy_(off[-1:], non_blocking=True)
-            cs.synchronize()  # the row total; the k-NN work is already queued on the compute stream
-            got = int(nnz_pin[0])
-            kb, db = bvh.query_nearest(qd[mh:], k, order=ob)
-            with torch.cuda.stream(cs):
-                idx_pin[:got].copy_(idx[:got], non_blocking=True)
-                cs.wait_event(ev_ka)
-                ka.record_stream(cs)
-                da.record_stream(cs)
-                outs["kidx"][:mh].copy_(ka, non_blocking=True)
-                outs["kd2"][:mh].copy_(da, non_blocking=True)
-            outs["kidx"][mh:].copy_(kb, non_blocking=True)
-            outs["kd2"][mh:].copy_(db, non_blocking=True)
-            stream.wait_stream(cs)  # join the copies before the end event
-            bvh.destroy()
-            return got
-
-        for _ in range(max(1, args.warmup)):
-            e2e_step()
-        torch.cuda.synchronize()
-        e2e_ms = 0.0
-        d2h = 0
-        for _ in range(args.steps):
-            flush.fill_(1.0)
-            barrier()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            got = e2e_step()
-            e1.record(stream)
-            torch.cuda.synchronize()
-            e2e_ms += e0.elapsed_time(e1)
-            d2h = (m + 1) * 8 + got * 4 + m * kk * 8
-        lat_ms = max_over_ranks(e2e_ms / args.steps, ws, dev)
-        lat_value = ws * 2 * m / (lat_ms * 1e-3) / 1e6
-
-        # A stream of independent batches, as a service runs them: batch i+1 uploads on its own copy
-        # stream while batch i is computed and downloaded on a third.  Every batch still copies its
-        # inputs from pinned host memory and its results back; two sets of device buffers alternate.
-        NB = 2
-        up, down = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
-        pdb = [torch.empty_like(p) for _ in range(NB)]
-        qdb = [torch.empty_like(q) for _ in range(NB)]
-        ibuf = [torch.empty(max(nnz, 1) * 2, dtype=torch.int32, device=dev) for _ in range(NB)]
-        outb = [dict(off=torch.empty(m + 1, dtype=torch.int64).pin_memory(),
-                     nnz=torch.empty(1, dtype=torch.int64).pin_memory(),
-                     kidx=torch.empty((m, kk), dtype=torch.int32).pin_memory(),
-                     kd2=torch.empty((m, kk), dtype=torch.float32).pin_memory(),
-                     idx=torch.empty(max(nnz, 1) * 2, dtype=torch.int32).pin_memory()) for _ in range(NB)]
-        ev_in = [torch.cuda.Event() for _ in range(NB)]    # inputs uploaded
-        ev_done = [torch.cuda.Event() for _ in range(NB)]  # computed: input buffers free again
-        ev_off = [torch.cuda.Event() for _ in range(NB)]   # offsets (row total) on the host
-        ev_idx = [torch.cuda.Event() for _ in range(NB)]   # rows on the host: row buffer free again
-        bsz_p = bsz if bsz > 0 else 32
-
-        def upload(i):
-            b = i % NB
-            with torch.cuda.stream(up):
-                up.wait_event(ev_done[b])  # the batch that last read these buffers is computed
-                pdb[b].copy_(p_pin, non_blocking=True)
-                qdb[b].copy_(q_pin, non_blocking=True)
-                ev_in[b].record(up)
-
-        def issue(i):
-            b = i % NB
-            stream.wait_event(ev_in[b])
-            bvh = ab.BVH(pdb[b], **topts)
-            order = bvh.query_order(qdb[b])
-            stream.wait_event(ev_idx[b])  # the row buffer's previous rows are on the host
-            off, _ = bvh.query_spatial_async(qdb[b], r, buffer_size=bsz_p, order=order, indices=ibuf[b])
-            kidx, kd2 = bvh.query_nearest(qdb[b], k, order=order)
-            ev_done[b].record(stream)
-            bvh.destroy()
-            with torch.cuda.stream(down):
-                down.wait_event(ev_done[b])
-                for t in (off, kidx, kd2):
-                    t.record_stream(down)
-                outb[b]["off"].copy_(off, non_blocking=True)
-                outb[b]["nnz"].copy_(off[-1:], non_blocking=True)
-                ev_off[b].record(down)
-                outb[b]["kidx"].copy_(kidx, non_blocking=True)
-                outb[b]["kd2"].copy_(kd2, non_blocking=True)
-            return b
-
-        def finish(b):  # the rows of batch b once its total is on the host
-            ev_off[b].synchronize()
-            got = int(outb[b]["nnz"][0])
-            with torch.cuda.stream(down):
-                outb[b]["idx"][:got].copy_(ibuf[b][:got], non_blocking=True)
-                ev_idx[b].record(down)
-            return got
-
-        def stream_batches(count):
-            prev, got = None, 0
-            upload(0)
-            for i in range(count):
-                if i + 1 < count:
-                    upload(i + 1)  # queued at once: the copy engine starts as soon as its buffers are free
-                b = issue(i)
-                if prev is not None:
-                    got += finish(prev)
-                prev = b
-            return got + finish(prev)
-
-        stream_batches(max(1, args.warmup))
-        torch.cuda.synchronize()
-        barrier()
-        t0 = torch.cuda.Event(enable_timing=True)
-        t1 = torch.cuda.Event(enable_timing=True)
-        t0.record(up)
-        got_all = stream_batches(args.steps)
-        stream.wait_stream(up)
-        stream.wait_stream(down)
-        t1.record(stream)
-        torch.cuda.synchronize()
-        e2e_ms = max_over_ranks(t0.elapsed_time(t1) / args.steps, ws, dev)
-        e2e_value = ws * 2 * m / (e2e_ms * 1e-3) / 1e6
-        d2h = (m + 1) * 8 + got_all // args.steps * 4 + m * kk * 8
-
-        e2e = {"value": round(e2e_value, 3), "unit": UNIT, "ms_per_step": round(e2e_ms, 4),
-               "h2d_bytes_per_step": int(p_h.nbytes + q_h.nbytes), "d2h_bytes_per_step": int(d2h),
-               "pipelined": f"{args.steps} batches in one timed region: batch i+1 uploads while batch i is "
-                            "computed and downloaded (three streams, two buffer sets)",
-               "single_batch": {"value": round(lat_value, 3), "ms_per_step": round(lat_ms, 4),
-                                "overlap": "queries upload during the build, spatial rows download during the "
-                                           "k-NN query, k-NN in two halves with the first half's rows "
-                                           "downloading during the second"}}
+        e2e = measure_e2e(ab, args, dev, stream, flush, barrier, ws, p, q, p_h, q_h, r, k, n, m, nnz, topts, bsz,
+                          idx_buf)
 
     # ---- roofline of the dominant kernel
     peak, peak_kind = measured_peaks()
