@@ -98,6 +98,10 @@ typedef struct arborx_opts {
   int32_t build_method; /* ARBORX_BUILD_APETREI (default) or ARBORX_BUILD_KARRAS; both build the same binary
                            radix tree (node numbering differs) */
   int32_t stats;        /* 1: count the internal nodes each traversal loads (read with arborx_stats) */
+  int32_t sorted_rows;  /* 1: every row of a spatial or box query lists its primitives in ascending index
+                           order (two stable radix sorts over the result entries; results up to
+                           ARBORX_MAX_PRIMS entries, else ARBORX_EINVAL); 0 (default): traversal order.
+                           The paper leaves row order open (rows are sets). */
   arborx_alloc_fn alloc; /* NULL: stream-ordered cudaMallocAsync / cudaFreeAsync */
   arborx_free_fn free;
   void *alloc_ctx;

@@ -43,6 +43,7 @@ class arborx_opts(ctypes.Structure):
         ("stack_smem", ctypes.c_int32),
         ("build_method", ctypes.c_int32),
         ("stats", ctypes.c_int32),
+        ("sorted_rows", ctypes.c_int32),
         ("alloc", _ALLOC_FN),
         ("free", _FREE_FN),
         ("alloc_ctx", ctypes.c_void_p),

@@ -166,6 +166,7 @@ bool opts_ok(const arborx_opts &o) {
   if (o.stack_smem < 0 || o.stack_smem > 64) return false;
   if ((o.alloc == nullptr) != (o.free == nullptr)) return false;
   if (o.build_method != ARBORX_BUILD_APETREI && o.build_method != ARBORX_BUILD_KARRAS) return false;
+  if (o.sorted_rows != 0 && o.sorted_rows != 1) return false;
   return true;
 }
 
@@ -347,6 +348,24 @@ bool finite_radius(float r) { return !std::isnan(r) && r >= 0.0f; }
 
 }  // namespace
 
+namespace {
+
+// opts.sorted_rows: put every row of the first `capacity` result entries in ascending index order
+int sort_rows(arborx_bvh_s *h, const int64_t *d_offsets, int32_t *d_indices, int64_t m, int64_t capacity,
+              cudaStream_t s) {
+  if (!h->opts.sorted_rows || m == 0 || capacity == 0) return ARBORX_OK;
+  if (capacity >= ARBORX_MAX_PRIMS) return ARBORX_EINVAL;
+  const uint32_t cap = (uint32_t)capacity;
+  const size_t bytes = sort_rows_bytes(cap, (uint32_t)m, (uint32_t)h->n);
+  void *ws = dev_alloc(h->opts, bytes, s);
+  if (!ws) return ARBORX_ENOMEM;
+  launch_sort_rows(d_offsets, d_indices, (uint32_t)m, cap, (uint32_t)h->n, ws, &h->meta->err, s);
+  dev_free(h->opts, ws, bytes, s);
+  return ARBORX_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char *arborx_version(void) { return "arborx-b300 0.1 (sm_103a)"; }
@@ -375,6 +394,7 @@ int arborx_default_opts(arborx_opts *o) {
   o->stack_smem = 0;
   o->build_method = ARBORX_BUILD_APETREI;
   o->stats = 0;
+  o->sorted_rows = 0;
   return ARBORX_OK;
 }
 
@@ -474,7 +494,8 @@ int arborx_query_spatial_fill(arborx_handle h, const float *d_queries, int64_t m
   const float r2 = radius * radius;  // one IEEE single rounding
   launch_spatial_fill(h->rec, (uint32_t)h->n, d_queries, h->qperm, (uint32_t)m, r2, d_offsets, d_indices, capacity,
                       &h->meta->err, trav_cfg(h, 0), s);
-  return launch_status();
+  const int st = sort_rows(h, d_offsets, d_indices, m, capacity, s);
+  return st ? st : launch_status();
 }
 
 int arborx_query_spatial(arborx_handle h, const float *d_queries, int64_t m, float radius, const uint32_t *d_order,
@@ -848,7 +869,8 @@ int arborx_query_spatial_buffered_fill(arborx_handle h, const float *d_queries, 
   const float r2 = radius * radius;
   launch_spatial_fill(h->rec, (uint32_t)h->n, d_queries, q.miss, (uint32_t)m, r2, d_offsets, d_indices, capacity,
                       &h->meta->err, trav_cfg(h, 0), s, q.miss + m);
-  return launch_status();
+  st = sort_rows(h, d_offsets, d_indices, m, capacity, s);
+  return st ? st : launch_status();
 }
 
 int arborx_query_spatial_buffered(arborx_handle h, const float *d_queries, int64_t m, float radius,
@@ -884,7 +906,8 @@ int arborx_query_spatial_buffered(arborx_handle h, const float *d_queries, int64
   launch_spatial_fill(h->rec, (uint32_t)h->n, d_queries, q.miss, (uint32_t)m, r2, d_offsets, d_indices, capacity,
                       &h->meta->err, trav_cfg(h, 0), s, ovf_count);
   h->stat_queries[0] += (uint64_t)m;
-  return launch_status();
+  st = sort_rows(h, d_offsets, d_indices, m, capacity, s);
+  return st ? st : launch_status();
 }
 
 namespace {
@@ -958,7 +981,8 @@ int arborx_query_intersects(arborx_handle h, const float *d_boxes, int64_t m, in
   launch_spatial_fill(h->rec, (uint32_t)h->n, d_boxes, q.miss, (uint32_t)m, 0.0f, d_offsets, d_indices, capacity,
                       &h->meta->err, cfg, s, ovf_count, true);
   h->stat_queries[0] += (uint64_t)m;
-  return launch_status();
+  st = sort_rows(h, d_offsets, d_indices, m, capacity, s);
+  return st ? st : launch_status();
 }
 
 int arborx_stats(arborx_handle h, void *stream, uint64_t out[4]) {

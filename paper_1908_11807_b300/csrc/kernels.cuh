@@ -80,6 +80,12 @@ void launch_compact(const int32_t *buf, int bs, const int32_t *counts, const int
 size_t scan_tmp_words(uint32_t m);
 void launch_scan(const int32_t *counts, uint32_t m, int64_t *offsets, int64_t *tmp, cudaStream_t s);
 
+// ---- row order (rows.cu): sort every CSR row of the first cap entries ascending (total read from
+// offsets[m] on the device); ws: sort_rows_bytes(cap, m, n_prims) bytes, 256-byte aligned
+size_t sort_rows_bytes(uint32_t cap, uint32_t m, uint32_t n_prims);
+void launch_sort_rows(const int64_t *offsets, int32_t *indices, uint32_t m, uint32_t cap, uint32_t n_prims,
+                      void *ws, uint32_t *err, cudaStream_t s);
+
 // nearest: rows of kk = min(k, n) (index, d2) in (d2, index) order.
 struct NearestArgs {
   const float4 *rec;
