@@ -384,6 +384,16 @@ ARBORX_API int arborx_batch_run(arborx_batch b, const float *d_points, const flo
 /* Synchronise `stream` and report device errors of the last run (non-finite input: EINVAL). */
 ARBORX_API int arborx_batch_check(arborx_batch b, void *stream);
 
+/* The whole batch in one synchronous call: arborx_batch_create, arborx_batch_run (eager, no graph),
+ * arborx_batch_check and arborx_batch_destroy.  Arguments as for those calls; capacity is the
+ * number of entries d_indices (and d_dist2, if not NULL) hold, at least the batch's entries
+ * (sum over queries of min(k_c, n_c)), else ARBORX_EINVAL.  Returns the first error.  The paper has
+ * no batched interface; results equal those of arborx_build + arborx_query_nearest per cloud. */
+ARBORX_API int arborx_batched(int64_t n_clouds, const int64_t *h_point_offsets, const int64_t *h_query_offsets,
+                              const int32_t *h_k, const float *d_points, const float *d_queries,
+                              const arborx_opts *opts, void *stream, int64_t *d_row_offsets, int32_t *d_indices,
+                              float *d_dist2, int64_t capacity);
+
 /* Release the batch (stream-ordered on the creation stream).  NULL is a no-op. */
 ARBORX_API int arborx_batch_destroy(arborx_batch b);
 

@@ -21,6 +21,7 @@ from ._binding import (  # noqa: F401
     MLP_PARAMS,
     BVH,
     Batch,
+    batched,
     arborx_build,
     arborx_query_nearest,
     arborx_query_spatial,

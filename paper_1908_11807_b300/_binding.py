@@ -95,6 +95,7 @@ def lib() -> ctypes.CDLL:
         L.arborx_batch_create.argtypes = [i64, vp, vp, vp, ctypes.POINTER(arborx_opts), vp, ctypes.POINTER(vp)]
         L.arborx_batch_entries.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]
         L.arborx_batch_run.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp]
+        L.arborx_batched.argtypes = [i64, vp, vp, vp, vp, vp, ctypes.POINTER(arborx_opts), vp, vp, vp, vp, i64]
         L.arborx_batch_check.argtypes = [vp, vp]
         L.arborx_batch_destroy.argtypes = [vp]
         L.arborx_query_nearest_bounded.argtypes = [vp, vp, i64, i32, vp, vp, vp, vp, vp, vp,
@@ -468,6 +469,29 @@ def profile_report() -> dict:
 def release_cached_memory() -> None:
     """Return the library's pooled device memory to the driver."""
     _check(lib().arborx_release_cached_memory(), "arborx_release_cached_memory")
+
+
+def batched(points: torch.Tensor, queries: torch.Tensor, point_offsets, query_offsets, ks, **opts):
+    """All clouds built and queried in one synchronous call (``arborx_batched``): (row_offsets int64
+    [M+1], indices int32 [entries] local to each cloud, dist2 float32 [entries])."""
+    import numpy as np
+    p = _as_f32_cuda(points, 3, "points")
+    q = _as_f32_cuda(queries, 3, "queries")
+    po = np.ascontiguousarray(point_offsets, dtype=np.int64)
+    qo = np.ascontiguousarray(query_offsets, dtype=np.int64)
+    kv = np.ascontiguousarray(ks, dtype=np.int32)
+    c = len(kv)
+    if po.shape != (c + 1,) or qo.shape != (c + 1,):
+        raise ValueError("offsets must have n_clouds + 1 entries")
+    entries = int(sum((qo[i + 1] - qo[i]) * min(int(kv[i]), int(po[i + 1] - po[i])) for i in range(c)))
+    row_off = torch.empty(int(qo[-1]) + 1, dtype=torch.int64, device=p.device)
+    idx = torch.empty(max(entries, 1), dtype=torch.int32, device=p.device)
+    d2 = torch.empty(max(entries, 1), dtype=torch.float32, device=p.device)
+    o = default_opts(**opts)
+    _check(lib().arborx_batched(c, po.ctypes.data_as(ctypes.c_void_p), qo.ctypes.data_as(ctypes.c_void_p),
+                                kv.ctypes.data_as(ctypes.c_void_p), _ptr(p), _ptr(q), ctypes.byref(o), _stream(),
+                                _ptr(row_off), _ptr(idx), _ptr(d2), entries), "arborx_batched")
+    return row_off, idx[:entries], d2[:entries]
 
 
 class Batch:

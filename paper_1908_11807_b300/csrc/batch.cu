@@ -338,6 +338,21 @@ int arborx_batch_check(arborx_batch b, void *stream) {
   return ARBORX_OK;
 }
 
+int arborx_batched(int64_t n_clouds, const int64_t *h_point_offsets, const int64_t *h_query_offsets,
+                    const int32_t *h_k, const float *d_points, const float *d_queries, const arborx_opts *opts,
+                    void *stream, int64_t *d_row_offsets, int32_t *d_indices, float *d_dist2, int64_t capacity) {
+  arborx_batch b = nullptr;
+  int st = arborx_batch_create(n_clouds, h_point_offsets, h_query_offsets, h_k, opts, stream, &b);
+  if (st) return st;
+  int64_t np = 0, nq = 0, entries = 0;
+  st = arborx_batch_entries(b, &np, &nq, &entries);
+  if (st == ARBORX_OK && (capacity < entries || (entries > 0 && !d_indices))) st = ARBORX_EINVAL;
+  if (st == ARBORX_OK) st = arborx_batch_run(b, d_points, d_queries, 0, stream, d_row_offsets, d_indices, d_dist2);
+  if (st == ARBORX_OK) st = arborx_batch_check(b, stream);
+  const int sd = arborx_batch_destroy(b);
+  return st ? st : sd;
+}
+
 int arborx_batch_destroy(arborx_batch b) {
   if (!b) return ARBORX_OK;
   if (b->cap) {

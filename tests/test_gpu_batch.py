@@ -98,3 +98,30 @@ def test_batch_rejects_bad_plans():
         ab.Batch([0, 10, 5], [0, 5, 6], [1, 1])
     with pytest.raises(ab.ArborXError):
         ab.Batch([1, 10], [0, 5], [1])
+
+
+def test_one_call_batched_matches_oracle_and_checks_capacity():
+    ab = _ab()
+    import ctypes
+    import torch
+    sizes = [0, 1, 3, 700, 2000, 64, 1500]
+    qsizes = [4, 9, 6, 300, 1000, 0, 800]
+    ks = [1, 10, 32, 10, 32, 16, 1]
+    pts, qs, po, qo, ks = _make(sizes, qsizes, ks, 9)
+    P = dev(np.concatenate(pts).astype(np.float32))
+    Q = dev(np.concatenate(qs).astype(np.float32))
+    off, idx, d2 = ab.batched(P, Q, po, qo, ks)
+    _check_against_oracle(pts, qs, ks, host(off), host(idx), host(d2), range(len(ks)))
+    # the same rows as the planned batch
+    o2, i2, d22 = ab.Batch(po, qo, ks).run(P, Q, use_graph=False)
+    assert np.array_equal(host(off), host(o2)) and np.array_equal(host(idx), host(i2))
+    # a capacity below the batch's entries is refused before any work
+    entries = int(idx.numel())
+    rows = torch.empty(int(qo[-1]) + 1, dtype=torch.int64, device="cuda")
+    small = torch.empty(entries, dtype=torch.int32, device="cuda")
+    o = ab.default_opts()
+    st = ab.lib().arborx_batched(len(ks), po.ctypes.data_as(ctypes.c_void_p), qo.ctypes.data_as(ctypes.c_void_p),
+                                 ks.ctypes.data_as(ctypes.c_void_p), P.data_ptr(), Q.data_ptr(), ctypes.byref(o),
+                                 ctypes.c_void_p(torch.cuda.current_stream().cuda_stream), rows.data_ptr(),
+                                 small.data_ptr(), None, entries - 1)
+    assert st == ab.ARBORX_EINVAL
