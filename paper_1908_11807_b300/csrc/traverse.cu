@@ -29,6 +29,11 @@ constexpr int kHeapDefer = 8;  // deferred-insert buffer of the shared-memory he
 constexpr int kHeapFrom = 17;  // smallest k served by the shared-memory heap
 static_assert(kHeapFrom <= 17, "register lists exist for k <= 16 only");
 constexpr int kBatchHeapK = 32;             // largest k of the batched path (heap class)
+// shared-memory stack entries of the heap paths (deeper entries spill to local memory): the heap
+// takes 8k bytes of shared memory per thread, so a short shared stack buys resident warps
+// (measured at 1e7 points: k = 32 4.13 -> 3.96 ms, k = 50 8.43 -> 7.60 ms per 1e6 queries, and the
+// 512-cloud batch 24.8 -> 22.9 ms, against 16 entries)
+constexpr int kHeapStackSmem = 4;
 constexpr bool kSpatialDual = true;         // spatial traversals load two nodes per iteration
 
 
@@ -892,8 +897,10 @@ static void nearest_kc(dim3 grid, int block, size_t smem, cudaStream_t s, const 
   else nearest_kc2<KC, false>(grid, block, smem, s, a);
 }
 
-int launch_batch_nearest(const BatchQueryArgs &a, int kc, const TravCfg &cfg, cudaStream_t s) {
-  if (a.pos_end <= a.pos_begin) return 0;
+int launch_batch_nearest(const BatchQueryArgs &args, int kc, const TravCfg &cfg, cudaStream_t s) {
+  if (args.pos_end <= args.pos_begin) return 0;
+  BatchQueryArgs a = args;
+  if (kc == 0) a.stack_smem = std::min(a.stack_smem, kHeapStackSmem);
   // the heap class runs 64-thread blocks at most (its shared heap limits the resident blocks)
   const int block = kc == 0 ? std::min(cfg.block, 64) : cfg.block;
   size_t smem = (size_t)2 * a.stack_smem * block * sizeof(int32_t);
@@ -932,19 +939,19 @@ int launch_batch_nearest(const BatchQueryArgs &a, int kc, const TravCfg &cfg, cu
 
 int launch_nearest(NearestArgs a, const TravCfg &cfg, cudaStream_t s) {
   a.kk = (int)std::min<int64_t>(a.k, a.n);
-  a.stack_smem = cfg.stack_smem;
   a.stats = cfg.stats_nodes;
   const int k = a.k;
   const uint32_t threads = a.m + 1;
   int block = cfg.block;
-  size_t smem = (size_t)2 * cfg.stack_smem * block * sizeof(int32_t);
   // large k: candidates in a shared-memory heap (a 64-entry register list measured 2x slower at k = 50)
   const bool use_heap = k >= kHeapFrom;
+  a.stack_smem = use_heap ? std::min(cfg.stack_smem, kHeapStackSmem) : cfg.stack_smem;
+  size_t smem = (size_t)2 * a.stack_smem * block * sizeof(int32_t);
   if (use_heap) {
     // heap of k pairs per thread in shared memory: shrink the block to fit
     while (block > 32 && smem + (size_t)2 * k * block * sizeof(int32_t) > 200 * 1024) {
       block >>= 1;
-      smem = (size_t)2 * cfg.stack_smem * block * sizeof(int32_t);
+      smem = (size_t)2 * a.stack_smem * block * sizeof(int32_t);
     }
     smem += (size_t)2 * k * block * sizeof(int32_t);
     if (smem > 227 * 1024) return -1;
