@@ -569,6 +569,8 @@ def run_gpu(args):
             line["batched"] = batched_extra(ab, dev)
         if "intersects" in extras:
             line["intersects"] = intersects_extra(ab, dev, topts)
+        if "configs" in extras:
+            line["configs"] = configs_extra(ab, dev, topts)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, p_h, q_h, r, k, n, m, budget_s=args.cpu_budget)
     if rank == 0:
@@ -648,6 +650,54 @@ def intersects_extra(ab, dev, topts):
             "query_ms": round(query_ms, 3), "query_mq_s": round(m / (query_ms * 1e-3) / 1e6, 1),
             "hits_per_query": round(nnz / m, 2), "nodes_per_query": round(nodes, 2),
             "node_fetch_gbs": round(node_bytes / (query_ms * 1e-3) / 1e9, 1)}
+
+
+def configs_extra(ab, dev, topts):
+    """Each test configuration's shape timed like the headline step (build, Morton order of the
+    queries, one-pass radius query, k-NN), device-resident inputs, best of three: the small cube,
+    the paper-scale cube and hollow sphere at 1e6 and 1e7 points, the 1e7-box build, and the
+    256^3 lattice with 1e6 query sites at r = 1, 2.5, 4 and k = 27."""
+    import torch
+    seed = datagen.SEED0 + 2
+    out = {}
+
+    def run(name, p_h, q_h, radii, k):
+        p = torch.from_numpy(p_h).to(dev)
+        q = torch.from_numpy(q_h).to(dev)
+        build_ms = _time_ms(lambda: ab.BVH(p, **topts).destroy())
+        bvh = ab.BVH(p, **topts)
+        order = bvh.query_order(q)
+        order_ms = _time_ms(lambda: bvh.query_order(q))
+        row = {"n": int(p_h.shape[0]), "m": int(q_h.shape[0]), "build_ms": round(build_ms, 3),
+               "build_mpts_s": round(p_h.shape[0] / build_ms / 1e3, 1), "order_ms": round(order_ms, 3)}
+        for r in radii:
+            off, _ = bvh.query_spatial(q, r, order=order, buffer_size=32)  # sizes the result buffer
+            nnz = int(off[-1].item())
+            rows = torch.empty(max(nnz, 1), dtype=torch.int32, device=dev)
+            sp_ms = _time_ms(lambda: bvh.query_spatial_async(q, r, buffer_size=32, order=order, indices=rows))
+            bvh.check()
+            row[f"radius_{r:.4g}"] = {"ms": round(sp_ms, 3), "mq_s": round(q_h.shape[0] / sp_ms / 1e3, 1),
+                                      "hits_per_query": round(nnz / q_h.shape[0], 2)}
+            del rows
+        if k:
+            kn_ms = _time_ms(lambda: bvh.query_nearest(q, k, order=order))
+            row[f"knn_{k}"] = {"ms": round(kn_ms, 3), "mq_s": round(q_h.shape[0] / kn_ms / 1e3, 1)}
+        bvh.destroy()
+        out[name] = row
+
+    for dist in ("cube", "hollow_sphere"):
+        for n in (1_000_000, 10_000_000):
+            p_h, q_h = datagen.workload(dist, n, 1_000_000, seed)
+            run(f"{dist}_{n:.0e}".replace("+0", ""), p_h, q_h, [datagen.radius_for_mean(n, dist)], 10)
+    p_h, q_h = datagen.workload("cube", 10_000, 10_000, seed)
+    run("cube_1e4", p_h, q_h, [datagen.radius_for_mean(10_000, "cube")], 10)
+    b = torch.from_numpy(datagen.boxes(10_000_000, seed)).to(dev)
+    bms = _time_ms(lambda: ab.BVH(b, **topts).destroy())
+    out["boxes_1e7"] = {"n": 10_000_000, "build_ms": round(bms, 3), "build_mboxes_s": round(1e7 / bms / 1e3, 1)}
+    del b
+    _, sites = datagen.lattice_sites(1_000_000, datagen.SEED0 + 3)
+    run("lattice_256", datagen.lattice(), sites, [1.0, 2.5, 4.0], 27)
+    return out
 
 
 def learned_extra(ab, dev):
@@ -806,7 +856,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the learned-bound and batched measurements")
-    ap.add_argument("--extras", default="query_ordering,learned,batched,intersects",
+    ap.add_argument("--extras", default="query_ordering,learned,batched,intersects,configs",
                     help="comma-separated extra measurements to run (after the headline step)")
     ap.add_argument("--no-tune", action="store_true", help="default launch parameters instead of the autotuner's")
     ap.add_argument("--launch", default=None,
