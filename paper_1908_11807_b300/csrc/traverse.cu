@@ -34,7 +34,6 @@ constexpr int kBatchHeapK = 32;             // largest k of the batched path (he
 // (measured at 1e7 points: k = 32 4.13 -> 3.96 ms, k = 50 8.43 -> 7.60 ms per 1e6 queries, and the
 // 512-cloud batch 24.8 -> 22.9 ms, against 16 entries)
 constexpr int kHeapStackSmem = 4;
-constexpr bool kSpatialDual = true;         // spatial traversals load two nodes per iteration
 
 
 // one 32-byte child slot (lo, hi) in a single 256-bit read-only load that does not allocate in L1
@@ -173,18 +172,19 @@ __device__ __forceinline__ void spatial_traverse(const SpatialArgs &a) {
         };
         int node = e0;
         while (true) {
-          // a second node, the stack top, is loaded alongside the current one: two independent
-          // node loads in flight per lane (the order of a spatial traversal is free).  Taken only
-          // while the stack is within its shared part, so the depth bound of the single-node
-          // traversal still holds beyond it.
-          int nb = -1;
-          if (kSpatialDual && sp > 0 && sp <= stack_smem) nb = pop();
-          if ((uint32_t)node >= n - 1 || (nb >= 0 && (uint32_t)nb >= n - 1)) {  // corrupt tree
-            set_err(a.err, ERR_STACK);
+          // up to two more nodes, the top entries of the stack, are loaded alongside the current
+          // one: three independent node loads in flight per lane (the order of a spatial traversal
+          // is free).  Taken only while the stack is within its shared part, so the depth bound
+          // of the single-node traversal still holds beyond it.
+          int nb = -1, nc = -1;
+          if (sp > 0 && sp <= stack_smem) nb = pop();
+          if (sp > 0 && sp <= stack_smem) nc = pop();
+          if ((uint32_t)node >= n - 1 || (nb >= 0 && (uint32_t)nb >= n - 1) || (nc >= 0 && (uint32_t)nc >= n - 1)) {
+            set_err(a.err, ERR_STACK);  // corrupt tree: never read outside the records
             break;
           }
           const float4 *rp = rec + 4 + 4 * (uint64_t)node;
-          float4 a0, a1, b0, b1, c0, c1, d0, d1;
+          float4 a0, a1, b0, b1, c0, c1, d0, d1, e0v, e1v, f0, f1;
           ld_slot(rp, a0, a1);
           ld_slot(rp + 2, b0, b1);
           if (nb >= 0) {
@@ -192,32 +192,36 @@ __device__ __forceinline__ void spatial_traverse(const SpatialArgs &a) {
             ld_slot(rq, c0, c1);
             ld_slot(rq + 2, d0, d1);
           }
-          visited += nb >= 0 ? 2 : 1;
-          const bool hl = hit(a0, a1);
-          const bool hr = hit(b0, b1);
-          const int el = __float_as_int(a0.w), er = __float_as_int(b0.w);
-          if (hl && el < 0) ABX_EMIT(~el);
-          if (hr && er < 0) ABX_EMIT(~er);
-          int next = -1;
-          if (hl && el >= 0) next = el;
-          if (hr && er >= 0) {
-            if (next < 0) next = er;
-            else push(er);
+          if (nc >= 0) {
+            const float4 *rr = rec + 4 + 4 * (uint64_t)nc;
+            ld_slot(rr, e0v, e1v);
+            ld_slot(rr + 2, f0, f1);
           }
+          visited += 1 + (nb >= 0) + (nc >= 0);
+          // a child slot that meets the predicate: a leaf is a result, an internal node is walked
+          // next (the first one) or pushed
+          int next = -1;
+          auto take = [&](float4 lo, float4 hi) {
+            const int e = __float_as_int(lo.w);
+            if (hit(lo, hi)) {
+              if (e < 0) {
+                ABX_EMIT(~e);
+              } else if (next < 0) {
+                next = e;
+              } else {
+                push(e);
+              }
+            }
+          };
+          take(a0, a1);
+          take(b0, b1);
           if (nb >= 0) {
-            const bool hl2 = hit(c0, c1);
-            const bool hr2 = hit(d0, d1);
-            const int el2 = __float_as_int(c0.w), er2 = __float_as_int(d0.w);
-            if (hl2 && el2 < 0) ABX_EMIT(~el2);
-            if (hr2 && er2 < 0) ABX_EMIT(~er2);
-            if (hl2 && el2 >= 0) {
-              if (next < 0) next = el2;
-              else push(el2);
-            }
-            if (hr2 && er2 >= 0) {
-              if (next < 0) next = er2;
-              else push(er2);
-            }
+            take(c0, c1);
+            take(d0, d1);
+          }
+          if (nc >= 0) {
+            take(e0v, e1v);
+            take(f0, f1);
           }
           if (next < 0) {
             if (sp == 0) break;
