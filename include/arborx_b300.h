@@ -252,6 +252,13 @@ ARBORX_API int arborx_query_intersects(arborx_handle h, const float *d_boxes, in
                                        const uint32_t *d_order, void *stream, int64_t *d_offsets, int32_t *d_indices,
                                        int64_t capacity);
 
+/* Self-test of the bounded waits (not in the paper): one GPU thread waits on a flag that nothing
+ * sets, with the iteration cap and backoff of the sort's decoupled look-back, gives up, and the
+ * call reports it the way arborx_check reports a timed-out look-back.  Returns ARBORX_ETIMEOUT
+ * (the expected result; the device stays usable), ARBORX_ENOMEM or ARBORX_ECUDA.  Synchronises
+ * `stream`; takes about a second. */
+ARBORX_API int arborx_selftest_bounded_wait(void *stream);
+
 /* Release memory returned by arborx_query_spatial (stream-ordered on `stream`). */
 ARBORX_API int arborx_free(arborx_handle h, void *d_ptr, size_t bytes, void *stream);
 

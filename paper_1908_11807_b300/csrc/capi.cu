@@ -620,6 +620,23 @@ int arborx_sort_pairs(void *d_keys, uint32_t *d_perm, int64_t n, int32_t key_bit
   return err_bits_to_status(bits);
 }
 
+int arborx_selftest_bounded_wait(void *stream) {
+  const cudaStream_t s = (cudaStream_t)stream;
+  arborx_opts o;
+  arborx_default_opts(&o);
+  uint32_t *w = (uint32_t *)dev_alloc(o, 256, s);  // flag (never set) and error word
+  if (!w) return ARBORX_ENOMEM;
+  uint32_t bits = 0;
+  cudaMemsetAsync(w, 0, 8, s);
+  launch_spin_probe(w, w + 1, s);
+  cudaMemcpyAsync(&bits, w + 1, sizeof bits, cudaMemcpyDeviceToHost, s);
+  dev_free(o, w, 256, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return ARBORX_ECUDA;
+  const int st = launch_status();
+  if (st) return st;
+  return err_bits_to_status(bits);
+}
+
 // ------------------------------------------------------------ learned bound
 
 int arborx_mlp_forward(arborx_handle h, const float *d_params, const float *d_queries, int64_t m, int32_t tensor_cores,

@@ -213,7 +213,22 @@ __global__ void __launch_bounds__(256) k_histogram(const K *__restrict__ keys, u
   }
 }
 
+// The look-back's wait on its own: spins on a flag with the look-back's cap and backoff, and
+// reports a wait that gives up the way the sort does (ERR_TIMEOUT in the error word).
+__global__ void k_spin_probe(const uint32_t *flag, uint32_t *err) {
+  uint32_t spins = 0;
+  while (ld_relaxed_gpu(flag) == 0u) {
+    if (++spins >= kSpinCap) {
+      set_err(err, ERR_TIMEOUT);
+      return;
+    }
+    if (spins > 256) __nanosleep(64);
+  }
+}
+
 }  // namespace
+
+void launch_spin_probe(const uint32_t *flag, uint32_t *err, cudaStream_t s) { k_spin_probe<<<1, 1, 0, s>>>(flag, err); }
 
 template <typename K>
 void launch_histogram(const K *keys, uint32_t n, int passes, uint32_t *hist, cudaStream_t s) {

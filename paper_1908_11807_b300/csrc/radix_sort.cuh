@@ -60,6 +60,10 @@ SortWs sort_ws_carve(uint32_t *base, int64_t n, int key_bits) {
 template <typename K>
 void launch_histogram(const K *keys, uint32_t n, int passes, uint32_t *hist, cudaStream_t s);
 
+// One thread waiting on *flag with the look-back's iteration cap and backoff; sets ERR_TIMEOUT in
+// *err when it gives up (self-test of the bounded wait).
+void launch_spin_probe(const uint32_t *flag, uint32_t *err, cudaStream_t s);
+
 // Run all passes.  keys/vals: A buffers hold the input keys (vals unused: the
 // first pass generates the identity); B buffers are scratch of the same size.
 // Result lands in (keysA, valsA) when passes is even, else in (keysB, valsB);
