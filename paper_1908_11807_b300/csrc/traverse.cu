@@ -174,8 +174,10 @@ __device__ __forceinline__ void spatial_traverse(const SpatialArgs &a) {
         while (true) {
           // up to two more nodes, the top entries of the stack, are loaded alongside the current
           // one: three independent node loads in flight per lane (the order of a spatial traversal
-          // is free).  Taken only while the stack is within its shared part, so the depth bound
-          // of the single-node traversal still holds beyond it.
+          // is free).  Taken only while the stack is within its shared part: one iteration there
+          // ends at most three entries past it, and beyond it the stack grows as in the
+          // single-node traversal (one entry per level), so the capacity still exceeds the deepest
+          // tree (93 levels for 63-bit codes) by a wide margin.
           int nb = -1, nc = -1;
           if (sp > 0 && sp <= stack_smem) nb = pop();
           if (sp > 0 && sp <= stack_smem) nc = pop();
