@@ -134,6 +134,18 @@ ARBORX_API int arborx_default_opts(arborx_opts *opts);
 ARBORX_API int arborx_build(const float *d_prims, int64_t n, int32_t kind, const arborx_opts *opts, void *stream,
                  arborx_handle *out);
 
+/* Rebuild the tree in place over new coordinates of the same n primitives of the same kind (a
+ * simulation's next time step): the same kernels as arborx_build, writing the handle's records.
+ * The first call allocates a build scratch block that the handle keeps (freed by
+ * arborx_destroy); later calls allocate nothing and, with opts.validate = 0, do not synchronise,
+ * so a rebuild and the queries after it can be captured in one CUDA graph and replayed.  Counts
+ * kept for arborx_query_spatial_fill / _buffered_fill are invalidated.  Work on other streams that
+ * still reads the old tree must be ordered before the rebuild.
+ *   d_prims  device float[n][3] or float[n][6], as for arborx_build (NULL only when n = 0)
+ * Errors: ARBORX_EINVAL (null handle or pointer, or a non-finite coordinate when validate = 1),
+ * ARBORX_ENOMEM (first call only). */
+ARBORX_API int arborx_rebuild(arborx_handle h, const float *d_prims, void *stream);
+
 /* Release every allocation of the handle, stream-ordered on the stream of the handle's last call
  * (a handle is used from one stream at a time).  NULL is a no-op. */
 ARBORX_API int arborx_destroy(arborx_handle h);

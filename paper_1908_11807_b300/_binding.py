@@ -92,6 +92,7 @@ def lib() -> ctypes.CDLL:
         L.arborx_query_spatial_buffered.argtypes = [vp, vp, i64, ctypes.c_float, i32, vp, vp, vp, vp, i64]
         L.arborx_query_order_boxes.argtypes = [vp, vp, i64, vp, vp]
         L.arborx_selftest_bounded_wait.argtypes = [vp]
+        L.arborx_rebuild.argtypes = [vp, vp, vp]
         L.arborx_query_intersects.argtypes = [vp, vp, i64, i32, vp, vp, vp, vp, i64]
         L.arborx_batch_create.argtypes = [i64, vp, vp, vp, ctypes.POINTER(arborx_opts), vp, ctypes.POINTER(vp)]
         L.arborx_batch_entries.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]
@@ -175,6 +176,16 @@ class BVH:
         if self._h is None:
             raise RuntimeError("BVH destroyed")
         return self._h
+
+    def rebuild(self, prims: torch.Tensor) -> None:
+        """Rebuild the tree in place over new coordinates of the same primitives (same n and kind);
+        with validate=0 the call only enqueues work and can be captured in a CUDA graph."""
+        width = 3 if self.kind == ARBORX_POINTS else 6
+        p = _as_f32_cuda(prims, width, "prims")
+        if p.shape[0] != self.n:
+            raise ValueError(f"rebuild needs the same number of primitives ({self.n})")
+        _check(lib().arborx_rebuild(self.handle, _ptr(p), _stream()), "arborx_rebuild")
+        self.prims = p
 
     def destroy(self) -> None:
         if getattr(self, "_h", None) is not None:

@@ -30,6 +30,9 @@ struct arborx_bvh_s {
   // query workspace, grown on demand
   void *qws;
   size_t qws_bytes;
+  // build scratch kept between arborx_rebuild calls (allocated by the first one)
+  void *bscratch;
+  size_t bscratch_bytes;
   // state handed from spatial count to spatial fill
   const uint32_t *qperm;
   const float *count_queries;
@@ -180,24 +183,31 @@ void sort_pairs(K *kA, K *kB, uint32_t *vA, uint32_t *vB, uint32_t n, const Sort
   *perm = inA ? vA : vB;
 }
 
+// Build scratch: keys A/B, vals A/B, parent links (Karras, preset to -1) or range ends (Apetrei),
+// the Apetrei frontier list, then the zero-initialised region (arrival counters, sort workspace).
 template <typename K>
-int build_impl(arborx_bvh_s *h, const float *d_prims, cudaStream_t s) {
+size_t build_scratch_bytes(const arborx_bvh_s *h) {
+  const int64_t n = h->n;
+  const int64_t n_int = n > 0 ? n - 1 : 0;
+  const bool karras = h->opts.build_method == ARBORX_BUILD_KARRAS;
+  const size_t ws_words = sort_ws_words<K>(n, h->opts.key_bits);
+  const size_t arrival_words = karras ? (size_t)n_int : 0;
+  const size_t link_words = karras ? (size_t)(2 * n - 1) : (size_t)n_int;
+  const size_t front_bytes = karras ? 0 : align_up(apetrei_front_bytes((uint32_t)n));
+  return 2 * align_up((size_t)n * sizeof(K)) + 2 * align_up((size_t)n * sizeof(uint32_t)) +
+         align_up(link_words * sizeof(int32_t)) + front_bytes + align_up(arrival_words * sizeof(uint32_t)) +
+         align_up(ws_words * sizeof(uint32_t));
+}
+
+// The build's work into the handle's records (allocated): scratch NULL takes a temporary block
+// from the allocator and returns it at the end.
+template <typename K>
+int build_work(arborx_bvh_s *h, const float *d_prims, cudaStream_t s, void *scratch) {
   const int64_t n = h->n;
   const uint32_t un = (uint32_t)n;
   const int key_bits = h->opts.key_bits;
   const int passes = sort_passes(key_bits);
   const int64_t n_int = n > 0 ? n - 1 : 0;
-
-  // persistent block: meta + records (root, reserved, 2 per internal node)
-  const size_t rec_floats = (size_t)(2 + 2 * n_int) * 8;
-  h->persist_bytes = align_up(sizeof(DevMeta)) + align_up(rec_floats * sizeof(float));
-  h->persist = dev_alloc(h->opts, h->persist_bytes, s);
-  if (!h->persist) return ARBORX_ENOMEM;
-  {
-    Carver c(h->persist);
-    h->meta = c.take<DevMeta>(1);
-    h->rec = c.take<float4>(rec_floats / 4);
-  }
   launch_init_meta(h->meta, s);
   if (n == 0) {
     // empty tree: the root record must still be readable; mark it empty by n == 0
@@ -216,17 +226,15 @@ int build_impl(arborx_bvh_s *h, const float *d_prims, cudaStream_t s) {
     if (nonfinite) return ARBORX_EINVAL;
   }
 
-  // scratch: keys A/B, vals A/B, parent links (Karras, preset to -1) or range
-  // ends (Apetrei), the Apetrei frontier list, then the zero-initialised region
   const bool karras = h->opts.build_method == ARBORX_BUILD_KARRAS;
   const size_t ws_words = sort_ws_words<K>(n, key_bits);
   const size_t arrival_words = karras ? (size_t)n_int : 0;  // Karras fit's arrival counters
   const size_t zero_bytes = align_up(arrival_words * sizeof(uint32_t)) + align_up(ws_words * sizeof(uint32_t));
   const size_t link_words = karras ? (size_t)(2 * n - 1) : (size_t)n_int;
   const size_t front_bytes = karras ? 0 : align_up(apetrei_front_bytes(un));
-  const size_t scratch_bytes = 2 * align_up((size_t)n * sizeof(K)) + 2 * align_up((size_t)n * sizeof(uint32_t)) +
-                               align_up(link_words * sizeof(int32_t)) + front_bytes + zero_bytes;
-  void *scratch = dev_alloc(h->opts, scratch_bytes, s);
+  const size_t scratch_bytes = build_scratch_bytes<K>(h);
+  const bool own = scratch == nullptr;
+  if (own) scratch = dev_alloc(h->opts, scratch_bytes, s);
   if (!scratch) return ARBORX_ENOMEM;
   Carver c(scratch);
   K *kA = c.take<K>(n);
@@ -255,7 +263,7 @@ int build_impl(arborx_bvh_s *h, const float *d_prims, cudaStream_t s) {
   st = launch_status();
   if (st == ARBORX_OK && h->opts.keep_order) {
     h->order_bytes = align_up((size_t)n * sizeof(uint64_t)) + align_up((size_t)n * sizeof(uint32_t));
-    h->order = dev_alloc(h->opts, h->order_bytes, s);
+    if (!h->order) h->order = dev_alloc(h->opts, h->order_bytes, s);
     if (!h->order) {
       st = ARBORX_ENOMEM;
     } else {
@@ -275,13 +283,31 @@ int build_impl(arborx_bvh_s *h, const float *d_prims, cudaStream_t s) {
       st = launch_status();
     }
   }
-  dev_free(h->opts, scratch, scratch_bytes, s);
+  if (own) dev_free(h->opts, scratch, scratch_bytes, s);
   return st;
+}
+
+template <typename K>
+int build_impl(arborx_bvh_s *h, const float *d_prims, cudaStream_t s) {
+  // persistent block: meta + records (root, reserved, 2 per internal node)
+  const int64_t n_int = h->n > 0 ? h->n - 1 : 0;
+  const size_t rec_floats = (size_t)(2 + 2 * n_int) * 8;
+  h->persist_bytes = align_up(sizeof(DevMeta)) + align_up(rec_floats * sizeof(float));
+  h->persist = dev_alloc(h->opts, h->persist_bytes, s);
+  if (!h->persist) return ARBORX_ENOMEM;
+  {
+    Carver c(h->persist);
+    h->meta = c.take<DevMeta>(1);
+    h->rec = c.take<float4>(rec_floats / 4);
+  }
+  return build_work<K>(h, d_prims, s, nullptr);
 }
 
 void release(arborx_bvh_s *h) {
   if (!h) return;
   dev_free(h->opts, h->qws, h->qws_bytes, h->stream);
+  dev_free(h->opts, h->bscratch, h->bscratch_bytes, h->stream);
+  h->bscratch = nullptr;
   dev_free(h->opts, h->sbuf, h->sbuf_bytes, h->stream);
   h->sbuf = nullptr;
   dev_free(h->opts, h->order, h->order_bytes, h->stream);
@@ -424,6 +450,23 @@ int arborx_build(const float *d_prims, int64_t n, int32_t kind, const arborx_opt
   }
   *out = h;
   return ARBORX_OK;
+}
+
+int arborx_rebuild(arborx_handle h, const float *d_prims, void *stream) {
+  if (!h || (h->n > 0 && !d_prims)) return ARBORX_EINVAL;
+  const cudaStream_t s = (cudaStream_t)stream;
+  h->stream = s;
+  h->count_valid = false;  // rows counted on the old tree cannot be filled from the new one
+  h->buffered_valid = false;
+  const bool wide = h->opts.key_bits != 30;
+  const size_t need = wide ? build_scratch_bytes<uint64_t>(h) : build_scratch_bytes<uint32_t>(h);
+  if (need > h->bscratch_bytes) {
+    dev_free(h->opts, h->bscratch, h->bscratch_bytes, s);
+    h->bscratch = dev_alloc(h->opts, need, s);
+    h->bscratch_bytes = h->bscratch ? need : 0;
+    if (!h->bscratch) return ARBORX_ENOMEM;
+  }
+  return wide ? build_work<uint64_t>(h, d_prims, s, h->bscratch) : build_work<uint32_t>(h, d_prims, s, h->bscratch);
 }
 
 int arborx_destroy(arborx_handle h) {
