@@ -211,6 +211,15 @@ def measured_peaks():
         return 6400.0, "fallback"
 
 
+def measured_bf16_peak():
+    """Dense BF16 tensor TFLOP/s for a kernel timed alone (the burst figure)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured"
+    except Exception:
+        return 1800.0, "fallback"
+
+
 # algorithmic bytes per unit of each kernel: compulsory reads and writes of one launch, plus
 # 64 bytes per internal node a traversal loads (counted by an instrumented untimed run)
 def kernel_bytes(name, n, m, k, nnz, nodes):
@@ -565,6 +574,8 @@ def run_gpu(args):
             line["query_ordering"] = ordering_extra(ab, p, q, r, k, topts)
         if "learned" in extras:
             line["learned"] = learned_extra(ab, dev)
+        if "mlp" in extras:
+            line["mlp"] = mlp_extra(ab, dev)
         if "batched" in extras:
             line["batched"] = batched_extra(ab, dev)
         if "intersects" in extras:
@@ -746,6 +757,39 @@ def learned_extra(ab, dev):
     return out
 
 
+def mlp_extra(ab, dev):
+    """Bound-regressor inference (3 -> 64 -> 64 -> 1) over 1e7 queries: the BF16 tcgen05 kernel
+    (the 64 x 64 layer on the tensor cores, accumulators in tensor memory) against the FP32
+    CUDA-core form, with the flop and byte rates of the tensor-core launch."""
+    import torch
+    n, m = 1_000_000, 10_000_000
+    seed = datagen.SEED0 + 5
+    p = torch.from_numpy(datagen.gaussian_mixture(n, seed)).to(dev)
+    q = torch.from_numpy(datagen.gaussian_mixture(m, seed, datagen.STREAM_QUERIES)).to(dev)
+    g = np.random.default_rng(seed)
+    init = np.concatenate([g.standard_normal(192) * np.sqrt(2 / 3), np.zeros(64),
+                           g.standard_normal(4096) * np.sqrt(2 / 64), np.zeros(64),
+                           g.standard_normal(64) * np.sqrt(1 / 64), np.zeros(1)]).astype(np.float32)
+    params = torch.from_numpy(init).to(dev)
+    bvh = ab.BVH(p)
+    tc_ms = _time_ms(lambda: bvh.mlp_forward(params, q, tensor_cores=True), reps=5)
+    fp32_ms = _time_ms(lambda: bvh.mlp_forward(params, q, tensor_cores=False), reps=5)
+    bvh.destroy()
+    hbm, hbm_kind = measured_peaks()
+    bf16, bf16_kind = measured_bf16_peak()
+    flop = 2 * (3 * 64 + 64 * 64 + 64) * m    # every layer
+    tensor_flop = 2 * 64 * 64 * m             # the layer on the tensor cores
+    nbytes = (12 + 4) * m                     # query in, output out
+    return {"workload": f"gaussian mixture queries, m={m}, random-init regressor (4481 parameters)",
+            "tensor_core_ms": round(tc_ms, 4), "fp32_ms": round(fp32_ms, 4),
+            "speedup_over_fp32": round(fp32_ms / tc_ms, 2),
+            "tflops_all_layers": round(flop / tc_ms / 1e9, 1),
+            "tensor_layer_frac_of_bf16_peak": round(tensor_flop / tc_ms / 1e9 / bf16, 4),
+            "hbm_gbs": round(nbytes / tc_ms / 1e6, 1),
+            "hbm_frac": round(nbytes / tc_ms / 1e6 / hbm, 4),
+            "peak_source": f"bf16 {bf16_kind}, hbm {hbm_kind}"}
+
+
 def batched_extra(ab, dev):
     """512 independent clouds (sizes log-uniform in [1e3, 1e5], cube or hollow sphere, k in
     {1, 10, 32}): one graph-replayed batch vs a per-cloud build + query loop."""
@@ -856,7 +900,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the learned-bound and batched measurements")
-    ap.add_argument("--extras", default="query_ordering,learned,batched,intersects,configs",
+    ap.add_argument("--extras", default="query_ordering,learned,mlp,batched,intersects,configs",
                     help="comma-separated extra measurements to run (after the headline step)")
     ap.add_argument("--no-tune", action="store_true", help="default launch parameters instead of the autotuner's")
     ap.add_argument("--launch", default=None,

@@ -431,11 +431,8 @@ __global__ void __launch_bounds__(kApBlock) k_apetrei_local(const float *__restr
     }
     return;
   }
-  for (int i = tid; i < C + 2; i += kApBlock) {
-    const int x = c0 - 1 + i;
-    if (x >= 0 && x < N) s_code[i] = codes[x];
-  }
-  if (tid < 2) s_front[tid].l = -1;
+  // the leaf gather is issued first; the d values, which need only the codes, are computed
+  // while it is in flight
   const int t = c0 + tid;  // this thread's leaf, and split t (between t and t + 1)
   const bool has_leaf = t <= cend;
   uint32_t prim = 0;
@@ -452,6 +449,20 @@ __global__ void __launch_bounds__(kApBlock) k_apetrei_local(const float *__restr
       hi = make_float4(q[3], q[4], q[5], 0.0f);
     }
   }
+  for (int i = tid; i < C + 2; i += kApBlock) {
+    const int x = c0 - 1 + i;
+    if (x >= 0 && x < N) s_code[i] = codes[x];
+  }
+  if (tid < 2) s_front[tid].l = -1;
+  __syncthreads();
+  // d at positions c0 - 1 + x (-1 outside [0, N - 2])
+  auto dl = [&](int pos) -> int {
+    if (pos < 0 || pos >= N - 1) return -1;
+    const K ci = s_code[pos - c0 + 1], cj = s_code[pos - c0 + 2];
+    if (ci != cj) return clz_key<K>(ci ^ cj);
+    return (int)(8 * sizeof(K)) + __clz((uint32_t)(pos ^ (pos + 1)));
+  };
+  for (int x = tid; x <= last; x += kApBlock) s_dmin[0][x] = dl(c0 - 1 + x);
   // unions within 16-leaf segments (lanes of one half-warp), before and after each leaf
   {
     float4 plo = lo, phi = hi, slo = lo, shi = hi;
@@ -482,15 +493,6 @@ __global__ void __launch_bounds__(kApBlock) k_apetrei_local(const float *__restr
       s_seg[0][1][tid / kApSeg] = shi;
     }
   }
-  __syncthreads();
-  // d at positions c0 - 1 + x (-1 outside [0, N - 2])
-  auto dl = [&](int pos) -> int {
-    if (pos < 0 || pos >= N - 1) return -1;
-    const K ci = s_code[pos - c0 + 1], cj = s_code[pos - c0 + 2];
-    if (ci != cj) return clz_key<K>(ci ^ cj);
-    return (int)(8 * sizeof(K)) + __clz((uint32_t)(pos ^ (pos + 1)));
-  };
-  for (int x = tid; x <= last; x += kApBlock) s_dmin[0][x] = dl(c0 - 1 + x);
   __syncthreads();
 #pragma unroll 1
   for (int j = 1; j < kApLevels; ++j) {

@@ -232,6 +232,9 @@ constexpr uint32_t kTmemCols = 64;          // FP32 accumulator columns (N = 64)
 constexpr uint32_t kLBO = 128;              // bytes between K-adjacent 8x16B core matrices
 constexpr uint32_t kSBO = 1024;             // bytes between M/N-adjacent 8-row groups (8 K chunks)
 constexpr uint32_t kMbarSpinCap = 1u << 24;
+// Resident blocks per SM: 8 x 64 accumulator columns fill the SM's 512 TMEM columns, and the
+// kernel's 27 KB of static shared memory admits no ninth block, so every allocation is granted.
+constexpr int kTcBlocksPerSm = 8;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -265,15 +268,17 @@ __device__ __forceinline__ uint32_t core_off(int row, int k) {
   return (uint32_t)((row >> 3) * kSBO + (k >> 3) * kLBO + (row & 7) * 16 + (k & 7) * 2);
 }
 
-__global__ void __launch_bounds__(kTile) k_mlp_bound_tc(const float *__restrict__ params,
+__global__ void __launch_bounds__(kTile, kTcBlocksPerSm) k_mlp_bound_tc(const float *__restrict__ params,
                                                        const float *__restrict__ queries, uint32_t m,
                                                        const DevMeta *__restrict__ meta, float margin,
                                                        float *__restrict__ bound2, float *__restrict__ y_out,
                                                        uint32_t *__restrict__ err) {
   __shared__ __align__(1024) unsigned char sA[kTile * kH * 2];  // h1 tile, BF16
   __shared__ __align__(1024) unsigned char sB[kH * kH * 2];     // W2, BF16 ([n = out][k = in])
-  __shared__ float sW1[192], sb1[kH], sb2[kH], sw3[kH];
+  __shared__ float4 sL1[kH];  // layer 1, hidden unit j: (W1[j][0], W1[j][1], W1[j][2], b1[j])
+  __shared__ float sb2[kH], sw3[kH];
   __shared__ float sb3;
+  __shared__ float s_lo[3], s_inv[3];  // scene-box corner and reciprocal extents (0 on a flat axis)
   __shared__ __align__(8) unsigned long long mbar;
   __shared__ uint32_t tmem_base;
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -283,13 +288,18 @@ __global__ void __launch_bounds__(kTile) k_mlp_bound_tc(const float *__restrict_
                  "r"(kTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  for (int i = tid; i < 192; i += kTile) sW1[i] = params[OFF_W1 + i];
   if (tid < kH) {
-    sb1[tid] = params[OFF_B1 + tid];
+    sL1[tid] = make_float4(params[OFF_W1 + 3 * tid], params[OFF_W1 + 3 * tid + 1], params[OFF_W1 + 3 * tid + 2],
+                           params[OFF_B1 + tid]);
     sb2[tid] = params[OFF_B2 + tid];
     sw3[tid] = params[OFF_W3 + tid];
   }
   if (tid == 0) sb3 = params[OFF_B3];
+  if (tid < 3) {
+    const float e = meta->scene[3 + tid] - meta->scene[tid];
+    s_lo[tid] = meta->scene[tid];
+    s_inv[tid] = e > 0.f ? 1.0f / e : 0.f;
+  }
   for (int e = tid; e < kH * kH / 2; e += kTile) {  // two consecutive k per store
     const int n = (2 * e) >> 6, k = (2 * e) & 63;
     *reinterpret_cast<uint32_t *>(sB + core_off(n, k)) =
@@ -308,13 +318,27 @@ __global__ void __launch_bounds__(kTile) k_mlp_bound_tc(const float *__restrict_
   uint32_t phase = 0;
   bool failed = false;
 
+  // the next tile's query is loaded while this tile computes
+  float r0 = 0.f, r1 = 0.f, r2 = 0.f;
+  auto fetch = [&](uint32_t tile) {
+    const uint64_t qn = (uint64_t)tile * kTile + tid;
+    if (qn < m) {
+      r0 = __ldg(queries + 3 * qn);
+      r1 = __ldg(queries + 3 * qn + 1);
+      r2 = __ldg(queries + 3 * qn + 2);
+    }
+  };
+  fetch(blockIdx.x);
   for (uint32_t tile = blockIdx.x; tile * kTile < m && !failed; tile += gridDim.x) {
     const uint32_t q = tile * kTile + tid;
     const bool valid = q < m;
     float x0 = 0.f, x1 = 0.f, x2 = 0.f;
-    if (valid)
-      normalise(meta, queries[3 * (uint64_t)q], queries[3 * (uint64_t)q + 1], queries[3 * (uint64_t)q + 2], x0, x1,
-                x2);
+    if (valid) {  // the scene-box scaling as one multiply per axis (a flat axis gives 0)
+      x0 = s_inv[0] > 0.f ? (r0 - s_lo[0]) * s_inv[0] : 0.f;
+      x1 = s_inv[1] > 0.f ? (r1 - s_lo[1]) * s_inv[1] : 0.f;
+      x2 = s_inv[2] > 0.f ? (r2 - s_lo[2]) * s_inv[2] : 0.f;
+    }
+    fetch(tile + gridDim.x);
     // layer 1 in FP32, stored as BF16 row `tid` of the A tile (8 K-chunks of 16 bytes)
 #pragma unroll
     for (int kc = 0; kc < 8; ++kc) {
@@ -322,8 +346,9 @@ __global__ void __launch_bounds__(kTile) k_mlp_bound_tc(const float *__restrict_
 #pragma unroll
       for (int h = 0; h < 4; ++h) {
         const int j = kc * 8 + 2 * h;
-        const float a = fmaxf(sb1[j] + sW1[3 * j] * x0 + sW1[3 * j + 1] * x1 + sW1[3 * j + 2] * x2, 0.f);
-        const float b = fmaxf(sb1[j + 1] + sW1[3 * j + 3] * x0 + sW1[3 * j + 4] * x1 + sW1[3 * j + 5] * x2, 0.f);
+        const float4 ua = sL1[j], ub = sL1[j + 1];
+        const float a = fmaxf(fmaf(ua.z, x2, fmaf(ua.y, x1, fmaf(ua.x, x0, ua.w))), 0.f);
+        const float b = fmaxf(fmaf(ub.z, x2, fmaf(ub.y, x1, fmaf(ub.x, x0, ub.w))), 0.f);
         w[h] = pack_bf16(a, b);
       }
       *reinterpret_cast<uint4 *>(sA + core_off(tid, kc * 8)) = make_uint4(w[0], w[1], w[2], w[3]);
@@ -426,7 +451,7 @@ void launch_mlp_bound(const float *params, const float *queries, uint32_t m, con
                       float *bound2, float *y_out, uint32_t *err, cudaStream_t s) {
   if (m == 0) return;
   const uint32_t tiles = ceil_div<uint32_t>(m, (uint32_t)kTile);
-  const uint32_t grid = std::min<uint32_t>(tiles, (uint32_t)sms() * 4u);
+  const uint32_t grid = std::min<uint32_t>(tiles, (uint32_t)sms() * (uint32_t)kTcBlocksPerSm);
   prof::Scope ps(s, "mlp_bound_tc");
   k_mlp_bound_tc<<<grid, kTile, 0, s>>>(params, queries, m, meta, margin, bound2, y_out, err);
 }
