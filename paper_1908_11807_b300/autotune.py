@@ -24,7 +24,7 @@ from . import _binding as _b
 DEFAULT_BLOCKS = (64, 128, 256)
 DEFAULT_STACKS = (4, 8, 16)
 DEFAULT_BUFFERS = (0, 16, 24, 32)
-DEFAULT_MARGINS = (0.35, 0.5, 0.7, 0.9)
+DEFAULT_MARGINS = (0.0, 0.1, 0.2, 0.35, 0.5, 0.7, 0.9)
 
 
 def cache_path() -> str:
