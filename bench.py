@@ -533,7 +533,7 @@ def run_gpu(args):
     tot_k = sum(ms for _, ms in prof.values())
     for name in kernels:
         kernels[name]["share"] = round(prof[name][1] / tot_k, 4) if tot_k else None
-    launches = int(sum(c for c, _ in prof.values()) / args.steps)
+    launches = int(sum(c for c, _ in prof.values()))  # every launch of the K timed steps
     roofline = None
     if dom is not None:
         b = kernel_bytes(dom, n, m, k, nnz, nodes)
@@ -566,6 +566,7 @@ def run_gpu(args):
         "roofline": roofline,
         "e2e": e2e,
         "gpu_launches": launches,
+        "gpu_launches_per_step": round(launches / args.steps, 2),
         "clocks": clocks,
     }
     if rank == 0 and not args.no_extras:
