@@ -143,7 +143,8 @@ ARBORX_API int arborx_build(const float *d_prims, int64_t n, int32_t kind, const
  * still reads the old tree must be ordered before the rebuild.
  *   d_prims  device float[n][3] or float[n][6], as for arborx_build (NULL only when n = 0)
  * Errors: ARBORX_EINVAL (null handle or pointer, or a non-finite coordinate when validate = 1),
- * ARBORX_ENOMEM (first call only). */
+ * ARBORX_ENOMEM (first call only).  After an error the handle's tree is unspecified until a
+ * rebuild succeeds; arborx_destroy still releases it. */
 ARBORX_API int arborx_rebuild(arborx_handle h, const float *d_prims, void *stream);
 
 /* Release every allocation of the handle, stream-ordered on the stream of the handle's last call
