@@ -168,6 +168,18 @@ ARBORX_API int arborx_check(arborx_handle h, void *stream);
 ARBORX_API int arborx_query_order(arborx_handle h, const float *d_queries, int64_t m, void *stream,
                                   uint32_t *d_order);
 
+/* Traversal order of a point or box set without a tree (Sec. 2.2, "Query ordering"): the same
+ * 24-bit Morton keys as arborx_query_order, scaled by the set's own bounding box (its finite
+ * coordinates; box centres for boxes) instead of a tree's.  Any permutation gives the same query
+ * results, so the order may be computed on another stream while the tree is built, or before it.
+ * Only enqueues work (graph-capturable); if the sort gives up a bounded wait, d_order is the
+ * identity, which is still a valid order.
+ *   d_prims  device float[m][3] (ARBORX_POINTS) or float[m][6] (ARBORX_BOXES)
+ *   opts     NULL for defaults; only the allocator is used (temporary memory, stream-ordered)
+ *   d_order  device uint32[m], written: a permutation of 0..m-1 */
+ARBORX_API int arborx_order(const float *d_prims, int64_t m, int32_t kind, const arborx_opts *opts, void *stream,
+                            uint32_t *d_order);
+
 /* Spatial query, pass 1 of the count-and-fill scheme (Sec. 2.2, "2P"): traverse the tree for
  * each of the m query points, count the primitives within distance `radius`, and write the
  * exclusive prefix sum of the counts to d_offsets[0..m] (d_offsets[m] = total, int64).

@@ -22,6 +22,7 @@ from ._binding import (  # noqa: F401
     BVH,
     Batch,
     batched,
+    order,
     arborx_build,
     arborx_query_nearest,
     arborx_query_spatial,

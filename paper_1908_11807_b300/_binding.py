@@ -93,6 +93,7 @@ def lib() -> ctypes.CDLL:
         L.arborx_query_order_boxes.argtypes = [vp, vp, i64, vp, vp]
         L.arborx_selftest_bounded_wait.argtypes = [vp]
         L.arborx_rebuild.argtypes = [vp, vp, vp]
+        L.arborx_order.argtypes = [vp, i64, i32, ctypes.POINTER(arborx_opts), vp, vp]
         L.arborx_query_intersects.argtypes = [vp, vp, i64, i32, vp, vp, vp, vp, i64]
         L.arborx_batch_create.argtypes = [i64, vp, vp, vp, ctypes.POINTER(arborx_opts), vp, ctypes.POINTER(vp)]
         L.arborx_batch_entries.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]
@@ -460,6 +461,18 @@ def arborx_sort_pairs(keys: torch.Tensor, key_bits: int) -> Tuple[torch.Tensor, 
     perm = torch.empty(k.numel(), dtype=torch.int32, device=k.device)
     _check(lib().arborx_sort_pairs(_ptr(k), _ptr(perm), k.numel(), int(key_bits), _stream()), "arborx_sort_pairs")
     return k, perm
+
+
+def order(prims: torch.Tensor, kind: Optional[int] = None) -> torch.Tensor:
+    """Morton traversal order (int32 [m]) of points float32 [m, 3] or boxes [m, 6], scaled by the
+    set's own bounding box: needs no tree, so it can run on another stream during a build.  Only
+    enqueues work on the current stream."""
+    if kind is None:
+        kind = ARBORX_BOXES if (prims.dim() == 2 and prims.shape[1] == 6) else ARBORX_POINTS
+    x = _as_f32_cuda(prims, 6 if kind == ARBORX_BOXES else 3, "prims")
+    out = torch.empty(x.shape[0], dtype=torch.int32, device=x.device)
+    _check(lib().arborx_order(_ptr(x), x.shape[0], int(kind), None, _stream(), _ptr(out)), "arborx_order")
+    return out
 
 
 def profile_enable(on: bool = True) -> None:

@@ -589,6 +589,14 @@ __global__ void __launch_bounds__(256) k_apetrei_top(const K *__restrict__ codes
   apetrei_climb_global<K>(codes, (int)n, other, rec, err, e.l, e.r, e.lo, e.hi);
 }
 
+// Identity order when a sort of the order's keys gave up its bounded wait (ERR_TIMEOUT in *err):
+// every permutation is a correct traversal order, the identity included.
+__global__ void k_iota_on_timeout(uint32_t *__restrict__ out, uint32_t m, const uint32_t *__restrict__ err) {
+  if (!(*err & ERR_TIMEOUT)) return;
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) out[i] = i;
+}
+
 // ------------------------------------------------------ batched clouds
 // Cloud c of a batch owns points [off[c], off[c+1]) of the concatenation.
 
@@ -714,6 +722,11 @@ int sm_count() {
 }
 
 }  // namespace
+
+void launch_iota_on_timeout(uint32_t *order, uint32_t m, const uint32_t *err, cudaStream_t s) {
+  if (m == 0) return;
+  k_iota_on_timeout<<<ceil_div<uint32_t>(m, 256u), 256, 0, s>>>(order, m, err);
+}
 
 void launch_init_meta(DevMeta *meta, cudaStream_t s) { k_init_meta<<<1, 32, 0, s>>>(meta); }
 

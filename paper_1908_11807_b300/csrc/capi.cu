@@ -1008,6 +1008,45 @@ int arborx_query_order_boxes(arborx_handle h, const float *d_boxes, int64_t m, v
   return query_order(h, d_boxes, m, ARBORX_BOXES, stream, d_order);
 }
 
+int arborx_order(const float *d_prims, int64_t m, int32_t kind, const arborx_opts *opts, void *stream,
+                 uint32_t *d_order) {
+  if (m < 0 || m >= ARBORX_MAX_QUERIES || (kind != ARBORX_POINTS && kind != ARBORX_BOXES) ||
+      (m > 0 && (!d_prims || !d_order)))
+    return ARBORX_EINVAL;
+  arborx_opts o;
+  if (opts) o = *opts;
+  else arborx_default_opts(&o);
+  if (!opts_ok(o)) return ARBORX_EINVAL;
+  if (m == 0) return ARBORX_OK;
+  const cudaStream_t s = (cudaStream_t)stream;
+  if (m == 1) {
+    launch_iota(d_order, 1u, s);
+    return launch_status();
+  }
+  const uint32_t um = (uint32_t)m;
+  const size_t ws_words = sort_ws_words<uint32_t>(m, kQueryKeyBits);
+  const size_t bytes = align_up(sizeof(DevMeta)) + 3 * align_up((size_t)m * sizeof(uint32_t)) +
+                       align_up(ws_words * sizeof(uint32_t));
+  void *tmp = dev_alloc(o, bytes, s);
+  if (!tmp) return ARBORX_ENOMEM;
+  Carver c(tmp);
+  DevMeta *meta = c.take<DevMeta>(1);
+  uint32_t *cA = c.take<uint32_t>(m), *cB = c.take<uint32_t>(m), *pB = c.take<uint32_t>(m);
+  uint32_t *wsb = c.take<uint32_t>(ws_words);
+  // the box of the set itself (finite coordinates only), its Morton codes, then the stable sort
+  launch_init_meta(meta, s);
+  launch_bounds(d_prims, m, kind, meta, s);
+  cudaMemsetAsync(wsb, 0, ws_words * sizeof(uint32_t), s);
+  const SortWs ws = sort_ws_carve<uint32_t>(wsb, m, kQueryKeyBits);
+  launch_morton<uint32_t>(d_prims, um, kind, meta, cA, ws.hist, ws.passes, false, s, 30 - kQueryKeyBits);
+  uint32_t *sk, *pm;
+  sort_pairs<uint32_t>(cA, cB, d_order, pB, um, ws, &meta->err, s, &sk, &pm);
+  if (pm != d_order) cudaMemcpyAsync(d_order, pm, (size_t)m * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
+  launch_iota_on_timeout(d_order, um, &meta->err, s);
+  dev_free(o, tmp, bytes, s);
+  return launch_status();
+}
+
 int arborx_query_intersects(arborx_handle h, const float *d_boxes, int64_t m, int32_t buffer_size,
                             const uint32_t *d_order, void *stream, int64_t *d_offsets, int32_t *d_indices,
                             int64_t capacity) {

@@ -38,6 +38,8 @@ struct TravCfg {
 };
 
 void launch_iota(uint32_t *out, uint32_t m, cudaStream_t s);
+// out[i] = i for i < m, only when *err holds ERR_TIMEOUT (a sort of the order gave up)
+void launch_iota_on_timeout(uint32_t *order, uint32_t m, const uint32_t *err, cudaStream_t s);
 
 struct SpatialArgs {
   const float4 *rec;

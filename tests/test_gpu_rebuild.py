@@ -92,3 +92,23 @@ def test_rebuild_and_queries_in_one_graph_follow_moving_points():
         assert_spatial_equal(off, host(rows)[:int(off[-1])], oo, io)
         eo, ed = oracle.nearest_brute(p, q, k)
         assert_nearest_equal(host(gidx), host(gd2), eo, ed)
+
+
+def test_rebuild_rejects_a_non_finite_coordinate_and_recovers():
+    ab = _ab()
+    p0 = datagen.cube(4000, 30)
+    bad = p0.copy()
+    bad[1234, 1] = np.nan
+    bvh = ab.BVH(dev(p0))
+    with pytest.raises(ab.ArborXError) as e:
+        bvh.rebuild(dev(bad))
+    assert e.value.code == ab.ARBORX_EINVAL
+    p1 = datagen.cube(4000, 31)
+    bvh.rebuild(dev(p1))  # a successful rebuild makes the tree valid again
+    q = datagen.cube(700, 32)
+    og, ig = bvh.query_spatial(dev(q), 0.05)
+    oo, io = oracle.spatial_brute(p1, q, 0.05)
+    assert_spatial_equal(host(og), host(ig), oo, io)
+    ki, kd = bvh.query_nearest(dev(q), 5)
+    eo, ed = oracle.nearest_brute(p1, q, 5)
+    assert_nearest_equal(host(ki), host(kd), eo, ed)
