@@ -736,8 +736,8 @@ def learned_extra(ab, dev):
         loss = bvh.mlp_train(params, qt, k, epochs=1200, batch=2048, lr=5e-3, lr_final=1e-5)
         torch.cuda.synchronize()
         train_s = time.perf_counter() - t0
-        sub = q[:1_000_000]
-        margin = autotune.tune_margin(bvh, sub, k, params)
+        margin = autotune.tune_margin(bvh, q, k, params)  # on the query set itself (a sparser subsample
+        # gives its Morton neighbours looser bounds and favours another margin)
         plain_ms = _time_ms(lambda: bvh.query_nearest(q, k, order=order))
         learned_ms = _time_ms(lambda: bvh.query_nearest_learned(q, k, params, margin, order=order))
         pi, pd = bvh.query_nearest(q, k, order=order)
