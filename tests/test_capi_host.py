@@ -80,6 +80,14 @@ def test_invalid_arguments_rejected_without_device(L):
     assert L.arborx_sort_pairs(None, None, 10, 0, None) == b.ARBORX_EINVAL
     assert L.arborx_sort_pairs(None, None, 10, 65, None) == b.ARBORX_EINVAL
     assert L.arborx_sort_pairs(None, None, 0, 30, None) == b.ARBORX_OK
+    # tree-free order: bad size, null pointers, bad kind; an empty set needs no device
+    assert L.arborx_order(None, -1, 0, None, None, None) == b.ARBORX_EINVAL
+    assert L.arborx_order(None, 10, 0, None, None, None) == b.ARBORX_EINVAL
+    assert L.arborx_order(ctypes.c_void_p(16), 10, 2, None, None, ctypes.c_void_p(16)) == b.ARBORX_EINVAL
+    assert L.arborx_order(None, 1 << 30, 0, None, None, None) == b.ARBORX_EINVAL
+    assert L.arborx_order(None, 0, 0, None, None, None) == b.ARBORX_OK
+    # rebuild needs a handle
+    assert L.arborx_rebuild(None, None, None) == b.ARBORX_EINVAL
 
 
 def test_binding_refuses_cpu_tensors():
