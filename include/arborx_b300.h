@@ -324,8 +324,12 @@ ARBORX_API int arborx_sort_pairs(void *d_keys, uint32_t *d_perm, int64_t n, int3
  * counterpart; this is a property of this library's interface only.
  *   n  at most ARBORX_SORT_NOALLOC_MAX_KEYS; larger n returns ARBORX_EINVAL without touching the GPU
  * The first call on a device looks up the array's device address (make it before any stream
- * capture).  All calls on a device share the one array: calls whose GPU work overlaps (different
- * streams or host threads) race and must be serialised by the caller.  Synchronises `stream`. */
+ * capture) and keeps it for the life of the process; after a cudaDeviceReset of that device the
+ * kept address is stale, as is the library's per-device memory pool, so the library must not be
+ * called on that device again.  All calls on a device share the one array, which keeps the last
+ * call's contents (each call clears what must start at zero): calls whose GPU work overlaps
+ * (different streams or host threads) race and must be serialised by the caller.  Synchronises
+ * `stream`.  Status is reported as by arborx_sort_pairs. */
 #define ARBORX_SORT_NOALLOC_MAX_KEYS (1 << 20)
 ARBORX_API int arborx_sort_pairs_noalloc(void *d_keys, uint32_t *d_perm, int64_t n, int32_t key_bits, void *stream);
 

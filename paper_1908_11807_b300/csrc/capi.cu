@@ -10,6 +10,7 @@
 #include "../../include/arborx_b300.h"
 #include "kernels.cuh"
 #include "radix_sort.cuh"
+#include "status.cuh"
 
 using namespace abx;
 
@@ -128,18 +129,6 @@ void dev_free(const arborx_opts &o, void *p, size_t bytes, cudaStream_t s) {
     return;
   }
   cudaFreeAsync(p, s);
-}
-
-int launch_status() {
-  const cudaError_t e = cudaGetLastError();
-  return e == cudaSuccess ? ARBORX_OK : ARBORX_ECUDA;
-}
-
-int err_bits_to_status(uint32_t bits) {
-  if (bits & ERR_NONFINITE) return ARBORX_EINVAL;
-  if (bits & ERR_TIMEOUT) return ARBORX_ETIMEOUT;
-  if (bits & (ERR_STACK | ERR_CSR)) return ARBORX_EOVERFLOW;
-  return ARBORX_OK;
 }
 
 TravCfg trav_cfg(const arborx_bvh_s *h, int which) {

@@ -11,6 +11,7 @@
 
 #include "../../include/arborx_b300.h"
 #include "radix_sort.cuh"
+#include "status.cuh"
 
 namespace abx {
 namespace {
@@ -29,7 +30,9 @@ constexpr size_t kAlign = 256;
 size_t up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
 // Device address of the scratch array on the current device.  Host code only
-// holds a stand-in symbol for it; the real address is looked up once per device.
+// holds a stand-in symbol for it; the real address is looked up once per device
+// and kept for the life of the process (like the library's per-device memory
+// pool, it does not survive a cudaDeviceReset of that device).
 int scratch_address(void **out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
@@ -58,19 +61,22 @@ int sort_in_scratch(K *keys, uint32_t *perm, uint32_t n, int key_bits, char *scr
   uint32_t *err = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(wsb) + up(ws_words * 4));
   if (reinterpret_cast<char *>(err) + kAlign > scratch + kScratchBytes) return ARBORX_EINVAL;
   // the array keeps the previous call's contents: clear what must start at zero
-  if (cudaMemsetAsync(wsb, 0, up(ws_words * 4) + kAlign, s) != cudaSuccess) return ARBORX_ECUDA;
+  if (cudaMemsetAsync(wsb, 0, up(ws_words * 4) + kAlign, s) != cudaSuccess) return launch_status();
   const SortWs ws = sort_ws_carve<K>(wsb, n, key_bits);
   launch_histogram<K>(keys, n, ws.passes, ws.hist, s);
   const bool inA = launch_onesweep<K>(keys, kB, perm, vB, n, ws, err, s);
-  if (!inA) {
-    cudaMemcpyAsync(keys, kB, (size_t)n * sizeof(K), cudaMemcpyDeviceToDevice, s);
-    cudaMemcpyAsync(perm, vB, (size_t)n * 4, cudaMemcpyDeviceToDevice, s);
+  if (!inA) {  // an odd number of passes leaves the result in the scratch buffers
+    if (cudaMemcpyAsync(keys, kB, (size_t)n * sizeof(K), cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(perm, vB, (size_t)n * 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return launch_status();
   }
   uint32_t bits = 0;
-  cudaMemcpyAsync(&bits, err, sizeof bits, cudaMemcpyDeviceToHost, s);
-  if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) return ARBORX_ECUDA;
-  if (bits & ERR_TIMEOUT) return ARBORX_ETIMEOUT;
-  return ARBORX_OK;
+  if (cudaMemcpyAsync(&bits, err, sizeof bits, cudaMemcpyDeviceToHost, s) != cudaSuccess) return launch_status();
+  // the same status mapping as arborx_sort_pairs
+  if (cudaStreamSynchronize(s) != cudaSuccess) return ARBORX_ECUDA;
+  const int st = launch_status();
+  if (st) return st;
+  return err_bits_to_status(bits);
 }
 
 }  // namespace

@@ -55,6 +55,23 @@ def test_noalloc_sort_matches_allocating_sort_twice_in_a_row():
     assert np.array_equal(c_perm, np.argsort(k3, kind="stable"))
 
 
+@pytest.mark.parametrize("key_bits,wide", [(8, False), (20, False), (40, True)])
+def test_noalloc_sort_odd_pass_counts_copy_back_from_the_array(key_bits, wide):
+    # 1, 3 and 5 eight-bit passes leave the sorted pairs in the array's second buffers, from
+    # which the call copies them back into the caller's; two calls in a row near the size limit
+    g = np.random.default_rng([2025, key_bits])
+    for n in (MAX_KEYS - 5, 777_777):
+        k = g.integers(0, 1 << key_bits, size=n, dtype=np.uint64)
+        k[::5] = k[1]
+        k = k if wide else k.astype(np.uint32)
+        view = k.view(np.int64) if wide else k.view(np.int32)
+        a_keys, a_perm = _sort_noalloc(view, key_bits)
+        r_keys, r_perm = _sort_reference(view, key_bits)
+        assert np.array_equal(a_perm, r_perm) and np.array_equal(a_keys, r_keys)
+        assert np.array_equal(a_perm, np.argsort(k, kind="stable"))
+        assert np.array_equal(a_keys.view(k.dtype), np.sort(k, kind="stable"))
+
+
 def test_noalloc_sort_rejects_sizes_beyond_its_array():
     import paper_1908_11807_b300 as ab
     L = ab.lib()
