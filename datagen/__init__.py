@@ -46,6 +46,7 @@ STREAM_TRAIN = 5
 STREAM_MIXTURE = 6
 STREAM_KIND = 7
 STREAM_K = 8
+STREAM_HELDOUT = 9  # a held-out query draw for tuning (never the timed or tested queries)
 
 
 def rng(seed: int, stream: int = 0, sub: int = 0) -> np.random.Generator:

@@ -110,8 +110,24 @@ def tune(points: torch.Tensor, queries: torch.Tensor, radius: float, k: int, tag
 
 
 def tune_margin(bvh, queries: torch.Tensor, k: int, params: torch.Tensor,
-                margins: Iterable[float] = DEFAULT_MARGINS) -> float:
-    """Margin of the learned bound with the fastest nearest query on ``queries``."""
+                margins: Iterable[float] = DEFAULT_MARGINS, objective: str = "time") -> float:
+    """Margin of the learned bound that minimises the nearest query's cost on ``queries``, which
+    should be a held-out draw of the workload's query distribution (not the queries that are
+    then timed or checked).  ``objective`` is "time" (CUDA-event time) or "nodes" (internal nodes
+    loaded by all passes, bounded pass and fallbacks together; needs a tree built with stats=1;
+    deterministic for a given regressor)."""
     order = bvh.query_order(queries)
-    return min((_time(lambda: bvh.query_nearest_learned(queries, k, params, mg, order=order)), mg)
-               for mg in margins)[1]
+    if objective == "time":
+        return min((_time(lambda: bvh.query_nearest_learned(queries, k, params, mg, order=order)), mg)
+                   for mg in margins)[1]
+    if objective != "nodes":
+        raise ValueError("objective must be 'time' or 'nodes'")
+    best = None
+    for mg in margins:
+        bvh.stats()
+        bvh.query_nearest_learned(queries, k, params, mg, order=order)
+        cand = (bvh.stats()["nearest_nodes"], mg)
+        if cand[0] == 0:
+            raise RuntimeError("objective 'nodes' needs a tree built with stats=1")
+        best = cand if best is None or cand < best else best
+    return best[1]

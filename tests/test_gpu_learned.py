@@ -1,7 +1,7 @@
 """GPU parity of the learned initial bound: FP32 forward / backward against the
 float64 oracle, the BF16 tensor-core forward within its rounding bound, Adam
 training against the oracle's Adam, exactness of the bounded nearest query
-with its fallback, and the traversal work the trained bound saves."""
+with its fallback, and how often the trained bound holds."""
 import numpy as np
 import pytest
 
@@ -136,25 +136,40 @@ def test_tight_initial_bound_prunes_traversal():
     assert bounded < 0.95 * plain
 
 
-def test_trained_bound_falls_back_rarely():
-    # after training, the learned bound (margin 0.5 in log space) must hold for most queries:
-    # few fallbacks, total work within 10% of the plain traversal, results identical
+def test_trained_bound_holds_for_most_queries():
+    # After training, the learned bound (margin tuned on a held-out draw, never on the queries
+    # measured here) holds for most queries: few fall back, results identical.  What the bound
+    # gains is time, not internal nodes: even the exact k-th distance as the bound loads only
+    # about 15% fewer nodes than plain traversal (the saving is in candidates never inserted
+    # into the list), and a learned bound with its margin loads about as many as plain.  The gain
+    # needs the workload's density (1e7 points, 1e7 queries: at 1e6 points it is within a few
+    # percent), so it is asserted by test_gpu_scale.py::test_learned_full_size_exact_and_faster.
     ab, p, q, bvh, m = _prune_setup()
+    from paper_1908_11807_b300 import autotune
     k = 10
     qt = datagen.gaussian_mixture(100_000, 92, datagen.STREAM_TRAIN)
+    q_tune = datagen.gaussian_mixture(m, 92, datagen.STREAM_HELDOUT)
     params = dev(mlp.he_init(np.random.default_rng(7)).astype(np.float32))
     loss = host(bvh.mlp_train(params, dev(qt), k, epochs=60, batch=1024, lr=3e-3, lr_final=3e-5))
     assert loss[-1] < 0.5 * loss[0]
+    margin = autotune.tune_margin(bvh, dev(q_tune), k, params, objective="nodes")
     qd = dev(q)
     bvh.stats()
     pi, pd = bvh.query_nearest(qd, k)
     plain = bvh.stats()["nearest_nodes"]
-    li, ld, fb = bvh.query_nearest_learned(qd, k, params, 0.5, count_fallbacks=True)
+    b2 = pd.view(m, k)[:, -1].contiguous() * (1.0 + 2.0 ** -10)
+    bvh.query_nearest_bounded(qd, k, b2, count_fallbacks=True)
+    exact = bvh.stats()["nearest_nodes"]
+    li, ld, fb = bvh.query_nearest_learned(qd, k, params, margin, count_fallbacks=True)
     learned = bvh.stats()["nearest_nodes"]
     assert np.array_equal(host(pi), host(li)) and np.array_equal(host(pd), host(ld))
-    print(f"nodes per query: plain {plain / m:.1f}, learned {learned / m:.1f}, fallbacks {fb / m:.3f}")
+    print(f"nodes per query: plain {plain / m:.1f}, learned {learned / m:.1f} (margin {margin}, "
+          f"fallbacks {fb / m:.3f}), exact bound {exact / m:.1f}")
+    assert exact < plain
+    # no bound at or above the k-th distance can load fewer nodes than the exact one (up to the
+    # 2^-10 slack of the exact bound)
+    assert learned >= 0.99 * exact
     assert fb < 0.15 * m
-    assert learned < 1.1 * plain
 
 
 def test_bounded_nearest_is_exact_for_any_bounds():

@@ -155,30 +155,74 @@ def test_lattice_256_all_sites():
     assert_nearest_equal(kg[bnd], dg[bnd], ko, do)
 
 
-def test_learned_full_size_sampled_exact():
-    # the learned-bound workload at its full point count (1e7 Gaussian-mixture points; 1e6 of the
-    # 1e7 queries), the regressor trained by the library on 1e5 labels: sampled rows exact
+@functools.lru_cache(maxsize=1)
+def _mixture_full():
+    # the learned-bound workload at its stated size: 1e7 mixture points, 1e7 queries, 1e6 training
+    # queries, and a held-out draw of 1e7 queries for the margin
+    seed = datagen.SEED0 + 5
+    n = m = 10_000_000
+    p = datagen.gaussian_mixture(n, seed)
+    q = datagen.gaussian_mixture(m, seed, datagen.STREAM_QUERIES)
+    qt = datagen.gaussian_mixture(1_000_000, seed, datagen.STREAM_TRAIN)
+    qh = datagen.gaussian_mixture(m, seed, datagen.STREAM_HELDOUT)
+    return p, q, qt, qh
+
+
+@functools.lru_cache(maxsize=1)
+def _mixture_cpu_bvh():
+    return oracle.CpuBVH(_mixture_full()[0])
+
+
+@pytest.mark.parametrize("k", [10, 50])
+def test_learned_full_size_exact_and_faster(k):
+    # 1e7 points, all 1e7 queries, the regressor trained by the library on 1e6 exact labels, the
+    # margin tuned on a held-out draw: every row equals the plain traversal's, sampled rows equal
+    # the oracle's CPU BVH, and the learned query is faster than the plain one
     ab = _ab()
     import torch
     from oracle import mlp
-    n, m = 10_000_000, 1_000_000
-    seed = datagen.SEED0 + 5
-    p = datagen.gaussian_mixture(n, seed)
-    q = datagen.gaussian_mixture(m, seed, datagen.STREAM_QUERIES)
-    qt = datagen.gaussian_mixture(100_000, seed, datagen.STREAM_TRAIN)
+    from paper_1908_11807_b300 import autotune
+    p, q, qt, qh = _mixture_full()
+    m = q.shape[0]
     bvh = ab.BVH(dev(p), **BENCH_LAUNCH)
     params = dev(mlp.he_init(np.random.default_rng(5)).astype(np.float32))
-    bvh.mlp_train(params, dev(qt), 10, epochs=20, batch=1024, lr=3e-3, lr_final=3e-5)
+    loss = host(bvh.mlp_train(params, dev(qt), k, epochs=200, batch=2048, lr=5e-3, lr_final=1e-5))
+    assert loss[-1] < 0.5 * loss[0]
+    margin = autotune.tune_margin(bvh, dev(qh), k, params)
     qd = dev(q)
     order = bvh.query_order(qd)
-    li, ld, fb = bvh.query_nearest_learned(qd, 10, params, 0.35, order=order, count_fallbacks=True)
-    pi, pd = bvh.query_nearest(qd, 10, order=order)
+    li, ld, fb = bvh.query_nearest_learned(qd, k, params, margin, order=order, count_fallbacks=True)
+    pi, pd = bvh.query_nearest(qd, k, order=order)
     bvh.check()
     assert torch.equal(li, pi) and torch.equal(ld, pd)
-    assert 0 < fb < m
-    rows = np.sort(np.random.default_rng(7).choice(m, 10_000, replace=False))
-    ko, do = oracle.CpuBVH(p).nearest(q[rows], 10)
+    assert 0 <= fb < m // 4
+    rows = np.sort(np.random.default_rng(7 + k).choice(m, 10_000, replace=False))
+    ko, do = _mixture_cpu_bvh().nearest(q[rows], k)
     assert_nearest_equal(host(li)[rows], host(ld)[rows], ko, do)
+    del li, ld, pi, pd
+
+    def best_ms(fn):
+        fn()
+        torch.cuda.synchronize()
+        t = []
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            t.append(e0.elapsed_time(e1))
+        return min(t)
+
+    plain_ms = best_ms(lambda: bvh.query_nearest(qd, k, order=order))
+    learned_ms = best_ms(lambda: bvh.query_nearest_learned(qd, k, params, margin, order=order))
+    print(f"k={k}: plain {plain_ms:.2f} ms, learned {learned_ms:.2f} ms ({plain_ms / learned_ms:.3f}x), "
+          f"margin {margin}, fallbacks {fb / m:.4f}")
+    # what the trained network gains over the method without it, at identical results: measured
+    # 1.32x (k = 10) and 1.14x (k = 50) with this training; the thresholds keep about half of it
+    # so that clock noise between the best-of-three timings cannot flip the result
+    assert plain_ms / learned_ms >= {10: 1.15, 50: 1.05}[k]
+    bvh.destroy()
 
 
 @functools.lru_cache(maxsize=1)
