@@ -72,7 +72,8 @@ typedef enum {
  * box); record 1 is reserved; the two children of internal node p are records
  * 2 + 2p (left) and 3 + 2p (right), adjacent, so one 64-byte load tests both.
  * Leaves are not stored separately: a child record of a leaf is its primitive's
- * box.  aux is unspecified. */
+ * box.  aux is the bit pattern of an int32: the number of leaves under the
+ * record (1 for a leaf; record 0 holds n). */
 #define ARBORX_RECORD_FLOATS 8
 
 /* Caller-supplied device allocator (e.g. a framework's caching allocator).
@@ -102,6 +103,12 @@ typedef struct arborx_opts {
                            order (two stable radix sorts over the result entries; results up to
                            ARBORX_MAX_PRIMS entries, else ARBORX_EINVAL); 0 (default): traversal order.
                            The paper leaves row order open (rows are sets). */
+  int32_t knn_anchor;   /* 1 (default): a nearest query with no caller-supplied bound first walks from the
+                           root toward the query through subtrees of at least k leaves and starts its
+                           traversal with the farthest-corner distance of the smallest such box as the
+                           k-th-distance bound (exact: that box holds k primitives), so candidates and
+                           stack entries beyond it are never inserted or pushed; 0: the traversal starts
+                           unbounded, as in Sec. 2.2.2.  Results are identical either way. */
   arborx_alloc_fn alloc; /* NULL: stream-ordered cudaMallocAsync / cudaFreeAsync */
   arborx_free_fn free;
   void *alloc_ctx;

@@ -8,6 +8,8 @@ fixes (Sec. 2, Sec. 2.1), independently of how the tree was built:
 * the root box is the scene box (Sec. 2: the root bounds every object);
 * every node box is the union of its children's boxes, leaves hold their
   primitive's box (Sec. 2.1, the bottom-up box step);
+* the aux word of every record counts the leaves under it (1 for a leaf, n
+  for the root record), the library's documented format;
 * leaves are ordered by Morton code, the codes of the leaves are
   non-decreasing, the permutation is a permutation, and each internal node
   covers a contiguous range of sorted leaves split at the highest differing
@@ -16,7 +18,8 @@ fixes (Sec. 2, Sec. 2.1), independently of how the tree was built:
 Exported layout being checked (the library's documented format): ``records``
 float32 [2 + 2 (n - 1)][8]; a record is (lo.x, lo.y, lo.z, enc, hi.x, hi.y,
 hi.z, aux) with ``enc`` an int32 bit pattern: enc >= 0 is an internal node id,
-enc < 0 a leaf holding primitive ~enc.  Record 0 describes the root; the
+enc < 0 a leaf holding primitive ~enc, and ``aux`` the int32 bit pattern of
+the number of leaves under the record.  Record 0 describes the root; the
 children of internal node p are records 2 + 2p (left) and 3 + 2p (right).
 """
 from __future__ import annotations
@@ -63,7 +66,7 @@ def _delta(codes_aug_hi, codes_aug_lo, i, j):
 
 def check_lbvh(records: np.ndarray, prims: np.ndarray, perm: np.ndarray | None = None,
                codes: np.ndarray | None = None, scene: np.ndarray | None = None,
-               check_split: bool = True) -> dict:
+               check_split: bool = True, check_counts: bool = True) -> dict:
     """Raise TreeError on the first violated invariant; return summary stats."""
     prims = np.asarray(prims, np.float32)
     n = prims.shape[0]
@@ -89,9 +92,12 @@ def check_lbvh(records: np.ndarray, prims: np.ndarray, perm: np.ndarray | None =
     if not (np.array_equal(lo[0], true_lo) and np.array_equal(hi[0], true_hi)):
         _fail(f"root box {lo[0]},{hi[0]} != union of primitive boxes {true_lo},{true_hi}")
 
+    aux = rec[:, 7].view(np.int32)
     if n == 1:
         if enc[0] != ~0:
             _fail(f"single-leaf root must hold primitive 0, enc={enc[0]}")
+        if check_counts and aux[0] != 1:
+            _fail(f"single-leaf root record counts {aux[0]} leaves, expected 1")
         return dict(n=1, depth=0)
     root = int(enc[0])
     if root < 0 or root >= n_int:
@@ -147,6 +153,27 @@ def check_lbvh(records: np.ndarray, prims: np.ndarray, perm: np.ndarray | None =
     lp = ~enc[leaf_slots]
     if not (np.array_equal(lo[leaf_slots], boxes[lp, :3]) and np.array_equal(hi[leaf_slots], boxes[lp, 3:])):
         _fail("a leaf record does not hold its primitive's box")
+
+    if check_counts:
+        # leaves under each internal node, bottom-up over the BFS levels
+        levels = []
+        fr = np.array([root], np.int64)
+        while fr.size:
+            levels.append(fr)
+            kids = enc[np.stack([2 + 2 * fr, 3 + 2 * fr], axis=1).ravel()]
+            fr = kids[kids >= 0].astype(np.int64)
+        under = np.zeros(n_int, np.int64)
+        for lev in reversed(levels):
+            for side in (2, 3):
+                e = enc[side + 2 * lev].astype(np.int64)
+                under[lev] += np.where(e < 0, 1, under[np.where(e < 0, 0, e)])
+        want = np.where(enc[2:] < 0, 1, under[np.where(enc[2:] < 0, 0, enc[2:])])
+        bad = np.nonzero(aux[2:] != want)[0]
+        if bad.size:
+            r = int(bad[0]) + 2
+            _fail(f"record {r} counts {aux[r]} leaves, expected {want[bad[0]]}")
+        if aux[0] != n:
+            _fail(f"root record counts {aux[0]} leaves, expected {n}")
 
     stats = dict(n=n, depth=depth)
     if perm is None:

@@ -118,6 +118,7 @@ int enqueue(arborx_batch_s *b, const float *pts, const float *qs, cudaStream_t s
     a.out_d2 = d_d2;
     a.err = b->err;
     a.stack_smem = cfg.stack_smem;
+    a.anchor = b->opts.knn_anchor;
     if (launch_batch_nearest(a, b->classes[i].kc, cfg, s)) return ARBORX_EINVAL;
   }
   return ARBORX_OK;
@@ -145,6 +146,7 @@ int arborx_batch_create(int64_t n_clouds, const int64_t *h_point_offsets, const 
   else arborx_default_opts(&o);
   if (o.block_size != 0 && (o.block_size < 32 || o.block_size > 256 || o.block_size % 32)) return ARBORX_EINVAL;
   if (o.stack_smem < 0 || o.stack_smem > 64) return ARBORX_EINVAL;
+  if (o.knn_anchor != 0 && o.knn_anchor != 1) return ARBORX_EINVAL;
   arborx_batch_s *b = new (std::nothrow) arborx_batch_s();
   if (!b) return ARBORX_ENOMEM;
   b->C = C;

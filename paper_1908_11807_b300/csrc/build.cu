@@ -283,9 +283,10 @@ __global__ void __launch_bounds__(256) k_fit(const float *__restrict__ prims, ui
     lx = p[0]; ly = p[1]; lz = p[2]; hx = p[3]; hy = p[4]; hz = p[5];
   }
   int enc = ~(int)prim;
+  int cnt = 1;  // leaves under the current node (the record's aux word)
   if (n == 1) {
     rec[0] = make_float4(lx, ly, lz, __int_as_float(enc));
-    rec[1] = make_float4(hx, hy, hz, 0.0f);
+    rec[1] = make_float4(hx, hy, hz, __int_as_float(1));
     return;
   }
   int c = (int)n - 1 + (int)t;
@@ -298,17 +299,18 @@ __global__ void __launch_bounds__(256) k_fit(const float *__restrict__ prims, ui
     }
     float4 *slot = rec + 4 + 4 * (uint64_t)p + 2 * side;
     slot[0] = make_float4(lx, ly, lz, __int_as_float(enc));
-    slot[1] = make_float4(hx, hy, hz, 0.0f);
+    slot[1] = make_float4(hx, hy, hz, __int_as_float(cnt));
     if (atom_add_acq_rel_gpu(arrival + p, 1u) == 0u) return;  // sibling not done yet
     const float4 *sib = rec + 4 + 4 * (uint64_t)p + 2 * (1 - side);
     const float4 slo = ld_cg_f4(sib), shi = ld_cg_f4(sib + 1);
     lx = fminf(lx, slo.x); ly = fminf(ly, slo.y); lz = fminf(lz, slo.z);
     hx = fmaxf(hx, shi.x); hy = fmaxf(hy, shi.y); hz = fmaxf(hz, shi.z);
+    cnt += __float_as_int(shi.w);
     enc = p;
     c = p;
     if (p == 0) {
       rec[0] = make_float4(lx, ly, lz, __int_as_float(0));
-      rec[1] = make_float4(hx, hy, hz, 0.0f);
+      rec[1] = make_float4(hx, hy, hz, __int_as_float(cnt));
       return;
     }
   }
@@ -382,7 +384,7 @@ __device__ __forceinline__ void apetrei_climb_global(const K *__restrict__ codes
     const float4 *sib = rec + 4 + 4 * (uint64_t)p + (left_child ? 2 : 0);
     const float4 slo = ld_cg_f4(sib), shi = ld_cg_f4(sib + 1);
     lo = make_float4(fminf(lo.x, slo.x), fminf(lo.y, slo.y), fminf(lo.z, slo.z), __int_as_float(p));
-    hi = make_float4(fmaxf(hi.x, shi.x), fmaxf(hi.y, shi.y), fmaxf(hi.z, shi.z), 0.0f);
+    hi = make_float4(fmaxf(hi.x, shi.x), fmaxf(hi.y, shi.y), fmaxf(hi.z, shi.z), __int_as_float(r - l + 1));
     if (l == 0 && r == N - 1) {
       rec[0] = lo;
       rec[1] = hi;
@@ -426,7 +428,8 @@ __global__ void __launch_bounds__(kApBlock) k_apetrei_local(const float *__restr
       const uint32_t prim = perm[0];
       const float *q = prims + (KIND == 0 ? 3 : 6) * (uint64_t)prim;
       rec[0] = make_float4(q[0], q[1], q[2], __int_as_float(~(int)prim));
-      rec[1] = KIND == 0 ? make_float4(q[0], q[1], q[2], 0.0f) : make_float4(q[3], q[4], q[5], 0.0f);
+      rec[1] = KIND == 0 ? make_float4(q[0], q[1], q[2], __int_as_float(1))
+                         : make_float4(q[3], q[4], q[5], __int_as_float(1));
       front[0].l = front[1].l = -1;
     }
     return;
@@ -527,6 +530,7 @@ __global__ void __launch_bounds__(kApBlock) k_apetrei_local(const float *__restr
   };
   if (has_leaf) {
     lo.w = __int_as_float(~(int)prim);
+    hi.w = __int_as_float(1);
     emit(t, t, lo, hi);
   }
   if (t < cend) {
@@ -564,7 +568,7 @@ __global__ void __launch_bounds__(kApBlock) k_apetrei_local(const float *__restr
         }
       }
       blo.w = __int_as_float(t);
-      bhi.w = 0.0f;
+      bhi.w = __int_as_float(r - l + 1);  // leaves under the node
       emit(l, r, blo, bhi);
     } else {
       other[t] = found_l ? l : (found_r ? r : -1);  // local child's outer end: a completed first arrival

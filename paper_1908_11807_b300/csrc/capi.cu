@@ -149,6 +149,7 @@ NearestArgs nearest_args(const arborx_bvh_s *h, const float *queries, const uint
   a.k = k;
   a.bound_scale = 1.0f;
   a.err = &h->meta->err;
+  a.anchor = h->opts.knn_anchor;
   return a;
 }
 
@@ -159,6 +160,7 @@ bool opts_ok(const arborx_opts &o) {
   if ((o.alloc == nullptr) != (o.free == nullptr)) return false;
   if (o.build_method != ARBORX_BUILD_APETREI && o.build_method != ARBORX_BUILD_KARRAS) return false;
   if (o.sorted_rows != 0 && o.sorted_rows != 1) return false;
+  if (o.knn_anchor != 0 && o.knn_anchor != 1) return false;
   return true;
 }
 
@@ -410,6 +412,7 @@ int arborx_default_opts(arborx_opts *o) {
   o->build_method = ARBORX_BUILD_APETREI;
   o->stats = 0;
   o->sorted_rows = 0;
+  o->knn_anchor = 1;
   return ARBORX_OK;
 }
 
@@ -777,6 +780,7 @@ int nearest_bounded(arborx_handle h, const float *d_queries, int64_t m, int32_t 
   a.out_idx = d_indices;
   a.out_d2 = d2;
   a.init_bound2 = bound2;
+  a.anchor = 0;  // the caller's bound takes its place; the unbounded last pass below uses it
   a.miss_list = miss;
   a.miss_count = miss_count;
   int st = launch_nearest(a, cfg, s) ? ARBORX_EINVAL : ARBORX_OK;
@@ -787,6 +791,7 @@ int nearest_bounded(arborx_handle h, const float *d_queries, int64_t m, int32_t 
     b.pos_list = miss;
     b.m_dev = miss_count;
     b.nbr_bound = 1;
+    b.anchor = 0;
     b.miss_list = miss2;
     b.miss_count = miss2_count;
     launch_nearest(b, cfg, s);

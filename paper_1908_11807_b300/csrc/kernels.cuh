@@ -110,6 +110,7 @@ struct NearestArgs {
   uint32_t *err;
   int stack_smem;            // set by launch_nearest
   unsigned long long *stats; // set by launch_nearest
+  int anchor;                // start from the tree's own k-th-distance bound (needs the leaf counts)
 };
 int launch_nearest(NearestArgs a, const TravCfg &cfg, cudaStream_t s);
 
@@ -131,6 +132,7 @@ struct BatchQueryArgs {
   float *out_d2;            // nullable
   uint32_t *err;
   int stack_smem;
+  int anchor;                // start from the tree's own k-th-distance bound
 };
 int launch_batch_nearest(const BatchQueryArgs &a, int kc, const TravCfg &cfg, cudaStream_t s);
 

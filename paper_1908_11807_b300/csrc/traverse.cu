@@ -582,6 +582,48 @@ __device__ __forceinline__ void knn_traverse(const float4 *__restrict__ rec, uin
   if constexpr (DEFER > 0) flush();
 }
 
+// Per-axis distance to the farther face of [lo, hi]: for every p in the box, |fl(q - p)| is at
+// most this (round-to-nearest subtraction is monotone), so the sum below bounds the FP32 squared
+// distance of every point in the box, computed in the same order.
+__device__ __forceinline__ float far_gap(float q, float lo, float hi) {
+  return fmaxf(fabsf(__fsub_rn(q, lo)), fabsf(__fsub_rn(q, hi)));
+}
+__device__ __forceinline__ float far2_box(float qx, float qy, float qz, float4 lo, float4 hi) {
+  const float gx = far_gap(qx, lo.x, hi.x), gy = far_gap(qy, lo.y, hi.y), gz = far_gap(qz, lo.z, hi.z);
+  return __fadd_rn(__fadd_rn(__fmul_rn(gx, gx), __fmul_rn(gy, gy)), __fmul_rn(gz, gz));
+}
+
+// Exact upper bound on the squared distance to the k-th nearest primitive, taken from the tree
+// before the traversal: a subtree with at least k leaves (the count is the aux word of its child
+// record) holds k primitives no farther than its box's farthest corner, so that distance bounds
+// the k-th.  A greedy walk from the subtree root at root_slot toward the query through children
+// of at least k leaves keeps the smallest such bound (about 20 node loads at 1e7 points, all on
+// the path the traversal then takes first).  With it as the initial bound the traversal inserts
+// and pushes nothing beyond it; results are unchanged.  +inf when the subtree has fewer than k.
+__device__ __forceinline__ float anchor_bound2(const float4 *__restrict__ rec, uint32_t n, float qx, float qy,
+                                               float qz, int k, uint32_t root_slot = 0) {
+  float B = __int_as_float(0x7f800000);
+  if (n < 2) return B;
+  const float4 r0 = __ldg(rec + 2 * (uint64_t)root_slot), r1 = __ldg(rec + 2 * (uint64_t)root_slot + 1);
+  if (__float_as_int(r1.w) < k) return B;
+  B = far2_box(qx, qy, qz, r0, r1);
+  int node = __float_as_int(r0.w);
+  for (int level = 0; level < 128; ++level) {
+    if (node < 0 || (uint32_t)node >= n - 1) break;  // a leaf, or a corrupt id: never read outside
+    const float4 *rp = rec + 4 + 4 * (uint64_t)node;
+    float4 a0, a1, b0, b1;
+    ld_slot(rp, a0, a1);
+    ld_slot(rp + 2, b0, b1);
+    const bool oka = __float_as_int(a1.w) >= k, okb = __float_as_int(b1.w) >= k;
+    const float fa = oka ? far2_box(qx, qy, qz, a0, a1) : __int_as_float(0x7f800000);
+    const float fb = okb ? far2_box(qx, qy, qz, b0, b1) : __int_as_float(0x7f800000);
+    B = fminf(B, fminf(fa, fb));
+    if (!oka && !okb) break;
+    node = (oka && (fa <= fb || !okb)) ? __float_as_int(a0.w) : __float_as_int(b0.w);
+  }
+  return B;
+}
+
 // Upper bound on the k-th squared distance of query q taken from a finished row
 // of its Morton neighbour q': the neighbour's k primitives lie within
 // d_k(q') + |q - q'| of q (triangle inequality).  Inflated by 2^-10 relative
@@ -630,6 +672,8 @@ __global__ void __launch_bounds__(kMaxBlock) k_nearest(const __grid_constant__ N
   const bool ok = finite3(qx, qy, qz);
   const int64_t row = (int64_t)qi * kk;
   uint32_t visited = 0;
+  // the tree's own bound (k = 1 gains nothing: its first leaf already sets the bound)
+  if (a.anchor && k > 1 && ok) b0 = fminf(b0, anchor_bound2(rec, n, qx, qy, qz, k));
   if constexpr (KC > 0) {
     RegList<KC> L;
     L.init(b0, k);
@@ -675,9 +719,11 @@ __global__ void __launch_bounds__(kMaxBlock) k_batch_nearest(const __grid_consta
       const float qz = __ldg(a.queries + 3 * (uint64_t)qi + 2);
       uint32_t visited = 0;
       const bool go = finite3(qx, qy, qz) && slot >= 0;
+      float b0 = __int_as_float(0x7f800000);
+      if (a.anchor && go && k > 1) b0 = anchor_bound2(a.rec, a.n, qx, qy, qz, k, (uint32_t)slot);
       if constexpr (KC > 0) {
         RegList<KC> L;
-        L.init(__int_as_float(0x7f800000), k);
+        L.init(b0, k);
         if (go)
           knn_traverse<0, true>(a.rec, a.n, qx, qy, qz, L, k, s_raw, B, a.stack_smem, a.err, visited,
                           (uint32_t)slot);
@@ -688,7 +734,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_batch_nearest(const __grid_consta
         H.hi = reinterpret_cast<int32_t *>(s_raw) + (size_t)(2 * a.stack_smem + kBatchHeapK) * B + threadIdx.x;
         H.s = B;
         H.k = k;
-        H.init(__int_as_float(0x7f800000), k);
+        H.init(b0, k);
         if (go)
           knn_traverse<kHeapDefer, false>(a.rec, a.n, qx, qy, qz, H, k, s_raw, B, a.stack_smem, a.err, visited,
                                    (uint32_t)slot);

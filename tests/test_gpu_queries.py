@@ -73,7 +73,7 @@ def test_nearest_every_list_width(k):
 
 @pytest.mark.parametrize("opts", [dict(sort_queries=0), dict(key_bits=63), dict(build_method=1), dict(stack_smem=1),
                                   dict(stack_smem=64, block_size=64), dict(block_size=256, stack_smem=4),
-                                  dict(block_size=32)])
+                                  dict(block_size=32), dict(knn_anchor=0), dict(knn_anchor=0, build_method=1)])
 def test_options_do_not_change_results(opts):
     ab = _ab()
     p, q = datagen.workload("hollow_sphere", 30_000, 4000, 22)
@@ -86,6 +86,29 @@ def test_options_do_not_change_results(opts):
     assert_spatial_equal(host(og), host(ig), oo, io)
     ko, do = oracle.nearest_brute(p, q, 10)
     assert_nearest_equal(host(kg), host(dg), ko, do)
+
+
+@pytest.mark.parametrize("build_method", [0, 1])
+@pytest.mark.parametrize("k", [2, 5, 10, 27, 33])
+def test_anchor_bound_with_ties_at_the_bound(k, build_method):
+    # The tree's own initial bound (a subtree box's farthest corner) is exact only if a primitive
+    # at exactly that distance still wins by index.  Clouds where it lands on ties: 40 copies of
+    # each point (queries on and off the points), and an integer lattice whose box corners are
+    # lattice points; both builders write the leaf counts the bound needs.
+    ab = _ab()
+    base = datagen.cube(300, 50)
+    dup = np.repeat(base, 40, 0)
+    q = np.concatenate([base[:200], datagen.cube(500, 51)]).astype(np.float32)
+    g = np.arange(12, dtype=np.float32)
+    lat = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    ql = np.concatenate([lat[::7], lat[::11] + 0.5]).astype(np.float32)
+    for p, qq in ((dup, q), (lat, ql)):
+        ref_i, ref_d = oracle.nearest_brute(p, qq, k)
+        for anchor in (1, 0):
+            bvh = ab.BVH(dev(p), build_method=build_method, knn_anchor=anchor)
+            ig, dg = bvh.query_nearest(dev(qq), k)
+            bvh.check()
+            assert_nearest_equal(host(ig), host(dg), ref_i, ref_d)
 
 
 @pytest.mark.parametrize("n", [0, 1, 2, 3, 9, 10, 11])

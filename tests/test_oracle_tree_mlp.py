@@ -29,6 +29,7 @@ def _radix_tree_records(prims, key_bits=30):
 
     recs = np.zeros((2 + 2 * max(n - 1, 0), 8), np.float32)
     encv = recs[:, 3].view(np.int32)
+    auxv = recs[:, 7].view(np.int32)
     next_id = [1]
 
     def build(i, j, slot):
@@ -38,6 +39,7 @@ def _radix_tree_records(prims, key_bits=30):
             recs[slot, 0:3] = lo
             recs[slot, 4:7] = hi
             encv[slot] = ~int(perm[i])
+            auxv[slot] = 1
             return lo, hi
         node = 0 if slot == 0 else next_id[0]
         if slot != 0:
@@ -53,6 +55,7 @@ def _radix_tree_records(prims, key_bits=30):
         recs[slot, 0:3] = lo
         recs[slot, 4:7] = hi
         encv[slot] = node
+        auxv[slot] = j - i + 1
         return lo, hi
 
     if n:
@@ -81,10 +84,14 @@ def _mutants(recs):
     r = recs.copy()
     ints = np.nonzero(enc(r)[2:] > 0)[0] + 2
     enc(r)[ints[0]] = 0; out.append(("cycle to root", r))
+    aux = lambda r: r[:, 7].view(np.int32)
+    r = recs.copy(); aux(r)[ints[1]] += 1; out.append(("leaf count of an internal child", r))
+    r = recs.copy(); aux(r)[leaves[2]] = 0; out.append(("leaf count of a leaf", r))
+    r = recs.copy(); aux(r)[0] -= 1; out.append(("leaf count of the root", r))
     return out
 
 
-@pytest.mark.parametrize("which", range(5))
+@pytest.mark.parametrize("which", range(8))
 def test_tree_checker_rejects_planted_mistakes(which):
     p = datagen.cube(64, 62)
     recs, perm, sc, sb = _radix_tree_records(p)
