@@ -671,10 +671,12 @@ def intersects_extra(ab, dev, topts):
 
 def configs_extra(ab, dev, topts):
     """Each test configuration's shape timed like the headline step (build, Morton order of the
-    queries, one-pass radius query, k-NN), device-resident inputs, best of three: the small cube,
+    queries, radius query in the scheme the tuner picks for that radius, k-NN), device-resident
+    inputs, best of three: the small cube,
     the paper-scale cube and hollow sphere at 1e6 and 1e7 points, the 1e7-box build, and the
     256^3 lattice with 1e6 query sites at r = 1, 2.5, 4 and k = 27."""
     import torch
+    from paper_1908_11807_b300 import autotune
     seed = datagen.SEED0 + 2
     out = {}
 
@@ -688,13 +690,20 @@ def configs_extra(ab, dev, topts):
         row = {"n": int(p_h.shape[0]), "m": int(q_h.shape[0]), "build_ms": round(build_ms, 3),
                "build_mpts_s": round(p_h.shape[0] / build_ms / 1e3, 1), "order_ms": round(order_ms, 3)}
         for r in radii:
-            off, _ = bvh.query_spatial(q, r, order=order, buffer_size=32)  # sizes the result buffer
+            # the row-buffer width for this radius (0: two passes), from its hit-count distribution
+            pick = autotune.pick_buffer(bvh, q, r, order=order)
+            bs = pick["buffer_size"]
+            off, _ = bvh.query_spatial(q, r, order=order, buffer_size=bs)  # sizes the result buffer
             nnz = int(off[-1].item())
             rows = torch.empty(max(nnz, 1), dtype=torch.int32, device=dev)
-            sp_ms = _time_ms(lambda: bvh.query_spatial_async(q, r, buffer_size=32, order=order, indices=rows))
+            if bs > 0:
+                sp_ms = _time_ms(lambda: bvh.query_spatial_async(q, r, buffer_size=bs, order=order, indices=rows))
+            else:
+                sp_ms = _time_ms(lambda: bvh.query_spatial(q, r, order=order))
             bvh.check()
             row[f"radius_{r:.4g}"] = {"ms": round(sp_ms, 3), "mq_s": round(q_h.shape[0] / sp_ms / 1e3, 1),
-                                      "hits_per_query": round(nnz / q_h.shape[0], 2)}
+                                      "hits_per_query": round(nnz / q_h.shape[0], 2), "buffer_size": bs,
+                                      "buffer_candidates_ms": pick["ms"]}
             del rows
         if k:
             kn_ms = _time_ms(lambda: bvh.query_nearest(q, k, order=order))
@@ -819,10 +828,26 @@ def batched_extra(ab, dev):
     qo = np.concatenate([[0], np.cumsum([len(x) for x in qs])]).astype(np.int64)
     P = torch.from_numpy(np.concatenate(pts)).to(dev)
     Q = torch.from_numpy(np.concatenate(qs)).to(dev)
-    b = ab.Batch(po, qo, ks)
+    from paper_1908_11807_b300 import autotune
+    b0 = ab.Batch(po, qo, ks)  # library defaults
+    o0 = b0.run(P, Q, use_graph=True)
+    default_ms = _time_ms(lambda: b0.run(P, Q, use_graph=True, out=(o0[0], o0[1], o0[2])), reps=5)
+    tuned = autotune.tune_batch(po, qo, ks, P, Q)
+    b = ab.Batch(po, qo, ks, block_size=tuned["block_size"], stack_smem=tuned["stack_smem"],
+                 queries_per_warp=tuned["queries_per_warp"])
     out_bufs = b.run(P, Q, use_graph=True)
     graph_ms = _time_ms(lambda: b.run(P, Q, use_graph=True, out=(out_bufs[0], out_bufs[1], out_bufs[2])), reps=5)
+    same = bool(torch.equal(o0[1], out_bufs[1]) and torch.equal(o0[2], out_bufs[2]))
+    del o0
+    b0.destroy()
     eager_ms = _time_ms(lambda: b.run(P, Q, use_graph=False), reps=3)
+    # per-kernel device time of one eager run (the profiler's event pairs cannot sit in a graph)
+    ab.profile_enable(True)
+    ab.profile_report()
+    b.run(P, Q, use_graph=False)
+    torch.cuda.synchronize()
+    per_kernel = {k_: round(ms_, 3) for k_, (_, ms_) in sorted(ab.profile_report().items(), key=lambda x: -x[1][1])}
+    ab.profile_enable(False)
     b.check()
     pd = [P[po[c]:po[c + 1]] for c in range(512)]
     qd = [Q[qo[c]:qo[c + 1]] for c in range(512)]
@@ -836,6 +861,8 @@ def batched_extra(ab, dev):
     mtot = int(qo[-1])
     b.destroy()
     return {"workload": f"512 clouds, {int(po[-1])} points, {mtot} queries, k in {{1,10,32}}",
+            "tuned": tuned, "default_tiles_graph_ms": round(default_ms, 3), "tuned_equals_default": same,
+            "per_kernel_ms": per_kernel,
             "graph_ms": round(graph_ms, 3), "eager_batch_ms": round(eager_ms, 3), "per_cloud_loop_ms": round(loop_ms, 3),
             "graph_mq_s": round(mtot / graph_ms / 1e3, 1), "loop_mq_s": round(mtot / loop_ms / 1e3, 1),
             "speedup_vs_loop": round(loop_ms / graph_ms, 2)}

@@ -109,6 +109,10 @@ typedef struct arborx_opts {
                            k-th-distance bound (exact: that box holds k primitives), so candidates and
                            stack entries beyond it are never inserted or pushed; 0: the traversal starts
                            unbounded, as in Sec. 2.2.2.  Results are identical either way. */
+  int32_t queries_per_warp; /* batched nearest queries (arborx_batch_*): sorted query positions a
+                           persistent warp takes from the work queue per fetch, its lanes serving 32 at
+                           a time (0 = default 32; else 32, 64, 128 or 256).  The single-tree
+                           traversals serve one query per thread and ignore it. */
   arborx_alloc_fn alloc; /* NULL: stream-ordered cudaMallocAsync / cudaFreeAsync */
   arborx_free_fn free;
   void *alloc_ctx;
@@ -408,7 +412,8 @@ typedef struct arborx_batch_s *arborx_batch;
  * queries [h_query_offsets[c], h_query_offsets[c+1]) of the concatenated query array, and wants
  * its k_c = h_k[c] nearest points (1 <= k_c <= 32).  Offsets start at 0 and do not decrease.
  * Allocates every device buffer the runs need (so runs allocate nothing) and synchronises once.
- * opts: block_size, stack_smem and the allocator are used; NULL for defaults. */
+ * opts: block_size, stack_smem, knn_anchor, queries_per_warp and the allocator are used; NULL for
+ * defaults. */
 ARBORX_API int arborx_batch_create(int64_t n_clouds, const int64_t *h_point_offsets, const int64_t *h_query_offsets,
                                    const int32_t *h_k, const arborx_opts *opts, void *stream, arborx_batch *out);
 

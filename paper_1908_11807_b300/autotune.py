@@ -3,9 +3,13 @@
 Picks, for a workload class, the traversal block size, the number of stack
 entries kept in shared memory, the row-buffer estimate of the one-pass spatial
 query (0 = two passes) and the margin of the learned bound, by timing the
-candidates with CUDA events on a sample of the caller's queries.  Choices are
-cached in JSON keyed by (log2 n bucket, k, distribution tag), in
-``$ARBORX_TUNE_CACHE`` or ``~/.cache/arborx_b300/tune.json``.
+candidates with CUDA events on a sample of the caller's queries
+(``tune``, ``tune_margin``); the row-buffer width for one radius from the
+distribution of its hit counts (``pick_buffer``); and the tiles of the batched
+many-cloud query: block size, shared stack entries and queries per warp
+(``tune_batch``).  Choices of ``tune`` and ``tune_batch`` are cached in JSON
+keyed by the workload class, in ``$ARBORX_TUNE_CACHE`` or
+``~/.cache/arborx_b300/tune.json``.
 
 Every candidate returns identical results (the launch parameters and the
 buffer estimate only change speed), so the tuner times nothing but speed.
@@ -131,3 +135,83 @@ def tune_margin(bvh, queries: torch.Tensor, k: int, params: torch.Tensor,
             raise RuntimeError("objective 'nodes' needs a tree built with stats=1")
         best = cand if best is None or cand < best else best
     return best[1]
+
+
+MAX_BUFFER_SIZE = 4096  # ARBORX_MAX_BUFFER_SIZE
+BUFFER_BYTES_CAP = 1 << 32  # row buffers of at most 4 GB (m * width * 4 bytes)
+
+
+def _round4(x: float) -> int:
+    return max(4, 4 * int(math.ceil(x / 4.0)))
+
+
+def pick_buffer(bvh, queries: torch.Tensor, radius: float, order: Optional[torch.Tensor] = None,
+                sample: int = 65536, reps: int = 2) -> dict:
+    """Row-buffer width of the one-pass radius query for this radius (0 = two passes).
+
+    A row that fits its buffer is written once; a row that overflows costs a second traversal,
+    so the useful widths sit at the top of the hit-count distribution.  The candidates are two
+    passes and the median, 99th percentile and largest count of a strided sample of the queries
+    (each rounded up to a multiple of 4, at most 4096 and at most 4 GB of buffer); each is timed
+    on all the queries and the fastest is returned with the timings and the sample's counts."""
+    m = int(queries.shape[0])
+    if m == 0:
+        return {"buffer_size": 0, "ms": {}, "hits": {}}
+    step = max(1, m // sample)
+    qs = queries[::step].contiguous()
+    cnt = torch.diff(bvh.query_spatial_count(qs, radius)).double()
+    hits = {"mean": float(cnt.mean()), "p50": float(cnt.quantile(0.5)), "p99": float(cnt.quantile(0.99)),
+            "max": float(cnt.max())}
+    cap = min(MAX_BUFFER_SIZE, (BUFFER_BYTES_CAP // (4 * m)) // 4 * 4)
+    cands = {0}
+    if cap >= 4:
+        cands |= {min(cap, _round4(hits[q])) for q in ("p50", "p99", "max")}
+    ms = {}
+    for bs in sorted(cands):
+        ms[bs] = round(_time(lambda: bvh.query_spatial(queries, radius, order=order, buffer_size=bs), reps), 4)
+    best = min(ms, key=ms.get)
+    return {"buffer_size": best, "ms": ms, "hits": {k: round(v, 2) for k, v in hits.items()}}
+
+
+DEFAULT_QPW = (32, 64, 128)
+
+
+def batch_cache_key(n_points: int, ks) -> str:
+    mix = "-".join(str(int(k)) for k in sorted(set(int(k) for k in ks)))
+    return f"batch/n2^{int(round(math.log2(max(n_points, 1))))}/c{len(ks)}/k{mix}"
+
+
+def tune_batch(point_offsets, query_offsets, ks, points: torch.Tensor, queries: torch.Tensor,
+               blocks: Iterable[int] = DEFAULT_BLOCKS, stacks: Iterable[int] = DEFAULT_STACKS,
+               qpws: Iterable[int] = DEFAULT_QPW, use_cache: bool = True) -> dict:
+    """Tiles of the batched many-cloud query (block size, shared stack entries, queries per warp)
+    for this batch shape, cached by (total points bucket, cloud count, k mix).  Times one graph
+    replay of the whole batch per candidate: block and stack first (32 queries per warp), then
+    queries per warp at the best of those.  Every candidate returns identical results."""
+    key = batch_cache_key(int(points.shape[0]), ks)
+    if use_cache:
+        hit = _load().get(key)
+        if hit is not None:
+            return hit
+
+    def run_ms(**opts):
+        b = _b.Batch(point_offsets, query_offsets, ks, **opts)
+        out = b.run(points, queries, use_graph=True)
+        t = _time(lambda: b.run(points, queries, use_graph=True, out=(out[0], out[1], out[2])))
+        b.destroy()
+        return t
+
+    best = None
+    for block in blocks:
+        for stack in stacks:
+            cand = (run_ms(block_size=block, stack_smem=stack), block, stack, 32)
+            best = cand if best is None or cand < best else best
+    for qpw in qpws:
+        if qpw == 32:
+            continue
+        cand = (run_ms(block_size=best[1], stack_smem=best[2], queries_per_warp=qpw), best[1], best[2], qpw)
+        best = cand if cand < best else best
+    out = {"block_size": best[1], "stack_smem": best[2], "queries_per_warp": best[3], "ms": round(best[0], 4)}
+    if use_cache:
+        _store(key, out)
+    return out

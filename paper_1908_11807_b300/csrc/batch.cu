@@ -119,6 +119,7 @@ int enqueue(arborx_batch_s *b, const float *pts, const float *qs, cudaStream_t s
     a.err = b->err;
     a.stack_smem = cfg.stack_smem;
     a.anchor = b->opts.knn_anchor;
+    a.queries_per_warp = b->opts.queries_per_warp > 0 ? b->opts.queries_per_warp : 32;
     if (launch_batch_nearest(a, b->classes[i].kc, cfg, s)) return ARBORX_EINVAL;
   }
   return ARBORX_OK;
@@ -147,6 +148,9 @@ int arborx_batch_create(int64_t n_clouds, const int64_t *h_point_offsets, const 
   if (o.block_size != 0 && (o.block_size < 32 || o.block_size > 256 || o.block_size % 32)) return ARBORX_EINVAL;
   if (o.stack_smem < 0 || o.stack_smem > 64) return ARBORX_EINVAL;
   if (o.knn_anchor != 0 && o.knn_anchor != 1) return ARBORX_EINVAL;
+  if (o.queries_per_warp != 0 && o.queries_per_warp != 32 && o.queries_per_warp != 64 &&
+      o.queries_per_warp != 128 && o.queries_per_warp != 256)
+    return ARBORX_EINVAL;
   arborx_batch_s *b = new (std::nothrow) arborx_batch_s();
   if (!b) return ARBORX_ENOMEM;
   b->C = C;

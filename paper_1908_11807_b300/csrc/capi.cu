@@ -161,6 +161,9 @@ bool opts_ok(const arborx_opts &o) {
   if (o.build_method != ARBORX_BUILD_APETREI && o.build_method != ARBORX_BUILD_KARRAS) return false;
   if (o.sorted_rows != 0 && o.sorted_rows != 1) return false;
   if (o.knn_anchor != 0 && o.knn_anchor != 1) return false;
+  if (o.queries_per_warp != 0 && o.queries_per_warp != 32 && o.queries_per_warp != 64 &&
+      o.queries_per_warp != 128 && o.queries_per_warp != 256)
+    return false;
   return true;
 }
 
@@ -413,6 +416,7 @@ int arborx_default_opts(arborx_opts *o) {
   o->stats = 0;
   o->sorted_rows = 0;
   o->knn_anchor = 1;
+  o->queries_per_warp = 0;
   return ARBORX_OK;
 }
 

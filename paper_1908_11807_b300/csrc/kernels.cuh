@@ -133,6 +133,7 @@ struct BatchQueryArgs {
   uint32_t *err;
   int stack_smem;
   int anchor;                // start from the tree's own k-th-distance bound
+  int queries_per_warp;      // sorted positions a warp takes per queue fetch (multiple of 32)
 };
 int launch_batch_nearest(const BatchQueryArgs &a, int kc, const TravCfg &cfg, cudaStream_t s);
 

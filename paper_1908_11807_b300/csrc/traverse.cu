@@ -694,51 +694,55 @@ __global__ void __launch_bounds__(kMaxBlock) k_nearest(const __grid_constant__ N
   if (a.stats) add_stat(a.stats, visited);
 }
 
-// Batched clouds: persistent warps take tiles of 32 sorted query positions from
-// an atomic counter; each query starts at its cloud's subtree root and returns
-// indices local to its cloud.  KC = 0: shared-memory heap for k up to kBatchHeapK.
+// Batched clouds: persistent warps take queries_per_warp sorted query positions
+// at a time from an atomic counter, their lanes serving 32 at a time; each query
+// starts at its cloud's subtree root and returns indices local to its cloud.
+// KC = 0: shared-memory heap for k up to kBatchHeapK.
 template <int KC>
 __global__ void __launch_bounds__(kMaxBlock) k_batch_nearest(const __grid_constant__ BatchQueryArgs a) {
   extern __shared__ unsigned char s_raw[];
   const int B = blockDim.x;
   const uint32_t lane = threadIdx.x & 31;
+  const uint32_t qpw = (uint32_t)a.queries_per_warp;  // a multiple of 32
   while (true) {
     uint32_t base = 0;
-    if (lane == 0) base = atomicAdd(a.queue, 32u);
+    if (lane == 0) base = atomicAdd(a.queue, qpw);
     base = __shfl_sync(0xffffffffu, base, 0);
     if (a.pos_begin + base >= a.pos_end) break;
-    const uint32_t pos = a.pos_begin + base + lane;
-    if (pos < a.pos_end) {
-      const uint32_t qi = __ldg(a.qperm + pos);
-      const uint32_t c = (uint32_t)(__ldg(a.qkeys + pos) >> 30);
-      const int k = __ldg(a.kof + c);
-      const int kk = min(k, (int)__ldg(a.ncount + c));
-      const int32_t slot = __ldg(a.root_slot + c);
-      const float qx = __ldg(a.queries + 3 * (uint64_t)qi);
-      const float qy = __ldg(a.queries + 3 * (uint64_t)qi + 1);
-      const float qz = __ldg(a.queries + 3 * (uint64_t)qi + 2);
-      uint32_t visited = 0;
-      const bool go = finite3(qx, qy, qz) && slot >= 0;
-      float b0 = __int_as_float(0x7f800000);
-      if (a.anchor && go && k > 1) b0 = anchor_bound2(a.rec, a.n, qx, qy, qz, k, (uint32_t)slot);
-      if constexpr (KC > 0) {
-        RegList<KC> L;
-        L.init(b0, k);
-        if (go)
-          knn_traverse<0, true>(a.rec, a.n, qx, qy, qz, L, k, s_raw, B, a.stack_smem, a.err, visited,
-                          (uint32_t)slot);
-        L.write(__ldg(a.row_off + qi), kk, a.out_idx, a.out_d2, (int32_t)__ldg(a.prim_base + c));
-      } else {
-        SmemHeap H;
-        H.hd = reinterpret_cast<float *>(s_raw) + (size_t)2 * a.stack_smem * B + threadIdx.x;
-        H.hi = reinterpret_cast<int32_t *>(s_raw) + (size_t)(2 * a.stack_smem + kBatchHeapK) * B + threadIdx.x;
-        H.s = B;
-        H.k = k;
-        H.init(b0, k);
-        if (go)
-          knn_traverse<kHeapDefer, false>(a.rec, a.n, qx, qy, qz, H, k, s_raw, B, a.stack_smem, a.err, visited,
-                                   (uint32_t)slot);
-        H.write(__ldg(a.row_off + qi), kk, a.out_idx, a.out_d2, (int32_t)__ldg(a.prim_base + c));
+    for (uint32_t j = 0; j < qpw; j += 32) {
+      const uint32_t pos = a.pos_begin + base + j + lane;
+      if (pos < a.pos_end) {
+        const uint32_t qi = __ldg(a.qperm + pos);
+        const uint32_t c = (uint32_t)(__ldg(a.qkeys + pos) >> 30);
+        const int k = __ldg(a.kof + c);
+        const int kk = min(k, (int)__ldg(a.ncount + c));
+        const int32_t slot = __ldg(a.root_slot + c);
+        const float qx = __ldg(a.queries + 3 * (uint64_t)qi);
+        const float qy = __ldg(a.queries + 3 * (uint64_t)qi + 1);
+        const float qz = __ldg(a.queries + 3 * (uint64_t)qi + 2);
+        uint32_t visited = 0;
+        const bool go = finite3(qx, qy, qz) && slot >= 0;
+        float b0 = __int_as_float(0x7f800000);
+        if (a.anchor && go && k > 1) b0 = anchor_bound2(a.rec, a.n, qx, qy, qz, k, (uint32_t)slot);
+        if constexpr (KC > 0) {
+          RegList<KC> L;
+          L.init(b0, k);
+          if (go)
+            knn_traverse<0, true>(a.rec, a.n, qx, qy, qz, L, k, s_raw, B, a.stack_smem, a.err, visited,
+                            (uint32_t)slot);
+          L.write(__ldg(a.row_off + qi), kk, a.out_idx, a.out_d2, (int32_t)__ldg(a.prim_base + c));
+        } else {
+          SmemHeap H;
+          H.hd = reinterpret_cast<float *>(s_raw) + (size_t)2 * a.stack_smem * B + threadIdx.x;
+          H.hi = reinterpret_cast<int32_t *>(s_raw) + (size_t)(2 * a.stack_smem + kBatchHeapK) * B + threadIdx.x;
+          H.s = B;
+          H.k = k;
+          H.init(b0, k);
+          if (go)
+            knn_traverse<kHeapDefer, false>(a.rec, a.n, qx, qy, qz, H, k, s_raw, B, a.stack_smem, a.err, visited,
+                                     (uint32_t)slot);
+          H.write(__ldg(a.row_off + qi), kk, a.out_idx, a.out_d2, (int32_t)__ldg(a.prim_base + c));
+        }
       }
     }
   }
@@ -967,7 +971,11 @@ int launch_batch_nearest(const BatchQueryArgs &args, int kc, const TravCfg &cfg,
   int dev = 0, sms = 148, per_sm = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  prof::Scope ps(s, "batch_nearest");
+  // one profiler name per query class, so that the report splits the batch's time by list width
+  const char *name = kc == 0 ? "batch_nearest_heap" : kc == 1 ? "batch_nearest_k1" : kc == 2 ? "batch_nearest_k2"
+                     : kc == 4 ? "batch_nearest_k4" : kc == 8 ? "batch_nearest_k8" : kc == 10 ? "batch_nearest_k10"
+                     : "batch_nearest_k16";
+  prof::Scope ps(s, name);
 #define ABX_BATCH(KC)                                                                                  \
   do {                                                                                                 \
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_nearest<KC>, block, smem);          \
