@@ -588,6 +588,8 @@ def run_gpu(args):
             line["intersects"] = intersects_extra(ab, dev, topts)
         if "configs" in extras:
             line["configs"] = configs_extra(ab, dev, topts)
+        if "cpu_configs" in extras and not args.no_cpu_baseline:
+            line["cpu_configs"] = cpu_configs_extra()
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, p_h, q_h, r, k, n, m, budget_s=args.cpu_budget)
     if rank == 0:
@@ -722,6 +724,63 @@ def configs_extra(ab, dev, topts):
     out["boxes_1e7"] = {"n": 10_000_000, "build_ms": round(bms, 3), "build_mboxes_s": round(1e7 / bms / 1e3, 1)}
     del b
     _, sites = datagen.lattice_sites(1_000_000, datagen.SEED0 + 3)
+    run("lattice_256", datagen.lattice(), sites, [1.0, 2.5, 4.0], 27)
+    return out
+
+
+def cpu_configs_extra(sample=100_000):
+    """The oracle on the host cores at each test configuration's shape: its CPU BVH (median
+    split, leaf 4, OpenMP) built over all n points and queried with the first `sample` queries
+    (radius for a mean of 10 neighbours, k = 10; the lattice at r = 1, 2.5, 4 and k = 27), and
+    brute force at the small cube.  Rates are of what was timed: build Mpts/s over all n, query
+    Mq/s over the sampled queries."""
+    import oracle
+    seed = datagen.SEED0 + 2
+    out = {"cores": oracle.threads(), "queries_timed": sample}
+
+    def run(name, p_h, q_h, radii, k, brute=False):
+        qs = q_h[:sample]
+        t0 = time.perf_counter()
+        tree = oracle.CpuBVH(p_h)
+        t1 = time.perf_counter()
+        row = {"n": int(p_h.shape[0]), "build_s": round(t1 - t0, 3),
+               "build_mpts_s": round(p_h.shape[0] / (t1 - t0) / 1e6, 2)}
+        for r in radii:
+            t0 = time.perf_counter()
+            off, _ = tree.spatial(qs, r)
+            dt = time.perf_counter() - t0
+            row[f"radius_{r:.4g}"] = {"mq_s": round(len(qs) / dt / 1e6, 4), "s": round(dt, 3),
+                                      "hits_per_query": round(float(off[-1]) / len(qs), 2)}
+        t0 = time.perf_counter()
+        tree.nearest(qs, k)
+        dt = time.perf_counter() - t0
+        row[f"knn_{k}"] = {"mq_s": round(len(qs) / dt / 1e6, 4), "s": round(dt, 3)}
+        del tree
+        if brute:
+            t0 = time.perf_counter()
+            oracle.spatial_brute(p_h, qs, radii[0])
+            dt_s = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            oracle.nearest_brute(p_h, qs, k)
+            dt_k = time.perf_counter() - t0
+            row["brute_force"] = {"radius_mq_s": round(len(qs) / dt_s / 1e6, 4),
+                                  f"knn_{k}_mq_s": round(len(qs) / dt_k / 1e6, 4)}
+        out[name] = row
+
+    p_h, q_h = datagen.workload("cube", 10_000, 10_000, seed)
+    run("cube_1e4", p_h, q_h, [datagen.radius_for_mean(10_000, "cube")], 10, brute=True)
+    for dist in ("cube", "hollow_sphere"):
+        for n in (1_000_000, 10_000_000):
+            p_h, q_h = datagen.workload(dist, n, sample, seed)
+            run(f"{dist}_{n:.0e}".replace("+0", ""), p_h, q_h, [datagen.radius_for_mean(n, dist)], 10)
+    b = datagen.boxes(10_000_000, seed)
+    t0 = time.perf_counter()
+    tree = oracle.CpuBVH(b)
+    dt = time.perf_counter() - t0
+    del tree
+    out["boxes_1e7"] = {"n": 10_000_000, "build_s": round(dt, 3), "build_mboxes_s": round(1e7 / dt / 1e6, 2)}
+    del b
+    _, sites = datagen.lattice_sites(sample, datagen.SEED0 + 3)
     run("lattice_256", datagen.lattice(), sites, [1.0, 2.5, 4.0], 27)
     return out
 
@@ -950,7 +1009,7 @@ def main():
                     help="reference arm: queries of each kind timed per step (default: all m)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the learned-bound and batched measurements")
-    ap.add_argument("--extras", default="query_ordering,learned,mlp,batched,intersects,configs",
+    ap.add_argument("--extras", default="query_ordering,learned,mlp,batched,intersects,configs,cpu_configs",
                     help="comma-separated extra measurements to run (after the headline step)")
     ap.add_argument("--no-tune", action="store_true", help="default launch parameters instead of the autotuner's")
     ap.add_argument("--launch", default=None,
