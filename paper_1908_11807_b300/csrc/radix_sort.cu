@@ -59,7 +59,11 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(const K *__restric
                                                           uint32_t *__restrict__ tile_ctr, uint32_t *__restrict__ err) {
   constexpr int ITEMS = SortTile<K>::items;
   constexpr int TILE = SortTile<K>::tile;
+  // 32-bit keys find the lanes sharing a digit through one shared-memory OR per key (73.3 against
+  // 77.9 us per 1e7-key pass with eight ballots); 64-bit keys keep the ballots (99 against 94 us)
+  constexpr bool kMaskRank = sizeof(K) == 4;
   __shared__ uint32_t s_whist[kSortWarps][kRadix];  // per-warp digit counts, then per-warp offsets
+  __shared__ uint32_t s_match[kMaskRank ? kSortWarps : 1][kRadix + 1];  // lane masks of one item's digits
   __shared__ uint32_t s_dstart[kRadix];             // tile-local start of each digit run
   __shared__ uint32_t s_gofs[kRadix];               // global destination of run start minus s_dstart
   __shared__ uint32_t s_scan[2][kSortWarps];
@@ -70,6 +74,8 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(const K *__restric
   const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);  // dynamic tile order: predecessors already run
   for (int i = tid; i < kSortWarps * kRadix; i += kSortThreads) (&s_whist[0][0])[i] = 0;
+  if (kMaskRank)
+    for (int i = tid; i < kSortWarps * (kRadix + 1); i += kSortThreads) (&s_match[0][0])[i] = 0;
   __syncthreads();
   const uint32_t tile = s_tile;
   const uint32_t tbase = tile * (uint32_t)TILE;
@@ -84,7 +90,8 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(const K *__restric
   }
 
   // warp-level ranking in input order (item-major, lane-minor): the lanes
-  // holding the same digit are found with one ballot per digit bit (cheaper
+  // holding the same digit are found through a shared-memory lane mask per
+  // digit (32-bit keys) or one ballot per digit bit (64-bit keys; both cheaper
   // than match.any when most of the 32 digits differ); the lowest lane of
   // each group adds the group size to the warp's counter and hands the
   // previous count to its peers; items are counted in order
@@ -94,16 +101,27 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(const K *__restric
     const uint32_t pos = wbase + i * 32 + lane;
     const bool valid = pos < n;
     const uint32_t d = valid ? (uint32_t)(k[i] >> shift) & (kRadix - 1) : (uint32_t)kRadix;
-    uint32_t peers = __ballot_sync(0xffffffffu, valid);
-    if (!valid) peers = ~peers;
+    uint32_t peers;
+    if constexpr (kMaskRank) {
+      atomicOr(&s_match[warp][d], 1u << lane);  // lanes holding the same digit meet in one word
+      __syncwarp();
+      peers = s_match[warp][d];
+    } else {
+      peers = __ballot_sync(0xffffffffu, valid);
+      if (!valid) peers = ~peers;
 #pragma unroll
-    for (int b = 0; b < kRadixBits; ++b) {
-      const bool bit = (d >> b) & 1u;
-      const uint32_t bal = __ballot_sync(0xffffffffu, bit);
-      peers &= bit ? bal : ~bal;
+      for (int b = 0; b < kRadixBits; ++b) {
+        const bool bit = (d >> b) & 1u;
+        const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+        peers &= bit ? bal : ~bal;
+      }
     }
     const int leader = __ffs(peers) - 1;
     uint32_t old = 0;
+    if constexpr (kMaskRank) {
+      __syncwarp();  // every lane has read its mask before the leaders clear them
+      if ((int)lane == leader) s_match[warp][d] = 0;
+    }
     if (valid && (int)lane == leader) {  // the warp's own counters, one leader per digit: no atomic needed
       old = s_whist[warp][d];
       s_whist[warp][d] = old + (uint32_t)__popc(peers);

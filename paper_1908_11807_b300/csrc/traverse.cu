@@ -601,7 +601,7 @@ __device__ __forceinline__ float far2_box(float qx, float qy, float qz, float4 l
 // the path the traversal then takes first).  With it as the initial bound the traversal inserts
 // and pushes nothing beyond it; results are unchanged.  +inf when the subtree has fewer than k.
 __device__ __forceinline__ float anchor_bound2(const float4 *__restrict__ rec, uint32_t n, float qx, float qy,
-                                               float qz, int k, uint32_t root_slot = 0) {
+                                               float qz, int k, uint32_t &visited, uint32_t root_slot = 0) {
   float B = __int_as_float(0x7f800000);
   if (n < 2) return B;
   const float4 r0 = __ldg(rec + 2 * (uint64_t)root_slot), r1 = __ldg(rec + 2 * (uint64_t)root_slot + 1);
@@ -614,6 +614,7 @@ __device__ __forceinline__ float anchor_bound2(const float4 *__restrict__ rec, u
     float4 a0, a1, b0, b1;
     ld_slot(rp, a0, a1);
     ld_slot(rp + 2, b0, b1);
+    ++visited;  // counted with the traversal's node loads
     const bool oka = __float_as_int(a1.w) >= k, okb = __float_as_int(b1.w) >= k;
     const float fa = oka ? far2_box(qx, qy, qz, a0, a1) : __int_as_float(0x7f800000);
     const float fb = okb ? far2_box(qx, qy, qz, b0, b1) : __int_as_float(0x7f800000);
@@ -673,7 +674,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_nearest(const __grid_constant__ N
   const int64_t row = (int64_t)qi * kk;
   uint32_t visited = 0;
   // the tree's own bound (k = 1 gains nothing: its first leaf already sets the bound)
-  if (a.anchor && k > 1 && ok) b0 = fminf(b0, anchor_bound2(rec, n, qx, qy, qz, k));
+  if (a.anchor && k > 1 && ok) b0 = fminf(b0, anchor_bound2(rec, n, qx, qy, qz, k, visited));
   if constexpr (KC > 0) {
     RegList<KC> L;
     L.init(b0, k);
@@ -723,7 +724,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_batch_nearest(const __grid_consta
         uint32_t visited = 0;
         const bool go = finite3(qx, qy, qz) && slot >= 0;
         float b0 = __int_as_float(0x7f800000);
-        if (a.anchor && go && k > 1) b0 = anchor_bound2(a.rec, a.n, qx, qy, qz, k, (uint32_t)slot);
+        if (a.anchor && go && k > 1) b0 = anchor_bound2(a.rec, a.n, qx, qy, qz, k, visited, (uint32_t)slot);
         if constexpr (KC > 0) {
           RegList<KC> L;
           L.init(b0, k);
