@@ -908,7 +908,7 @@ def batched_extra(ab, dev):
     default_ms = _time_ms(lambda: b0.run(P, Q, use_graph=True, out=(o0[0], o0[1], o0[2])), reps=5)
     tuned = autotune.tune_batch(po, qo, ks, P, Q)
     b = ab.Batch(po, qo, ks, block_size=tuned["block_size"], stack_smem=tuned["stack_smem"],
-                 queries_per_warp=tuned["queries_per_warp"])
+                 queries_per_warp=tuned["queries_per_warp"], knn_heap_from=tuned["knn_heap_from"])
     out_bufs = b.run(P, Q, use_graph=True)
     graph_ms = _time_ms(lambda: b.run(P, Q, use_graph=True, out=(out_bufs[0], out_bufs[1], out_bufs[2])), reps=5)
     same = bool(torch.equal(o0[1], out_bufs[1]) and torch.equal(o0[2], out_bufs[2]))

@@ -46,6 +46,7 @@ class arborx_opts(ctypes.Structure):
         ("sorted_rows", ctypes.c_int32),
         ("knn_anchor", ctypes.c_int32),
         ("queries_per_warp", ctypes.c_int32),
+        ("knn_heap_from", ctypes.c_int32),
         ("alloc", _ALLOC_FN),
         ("free", _FREE_FN),
         ("alloc_ctx", ctypes.c_void_p),

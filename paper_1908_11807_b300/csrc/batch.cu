@@ -60,12 +60,14 @@ namespace {
 constexpr size_t kAl = 256;
 size_t al(size_t x) { return (x + kAl - 1) & ~(kAl - 1); }
 
-// Query class of a cloud's k: the register-list width for k <= 16, else 0 (the
-// shared-memory heap of up to 32 entries, faster than a 32-entry register list)
-int kc_of(int k) {
-  const int widths[] = {1, 2, 4, 8, 10, 16};
+// Query class of a cloud's k: the register-list width for k below heap_from (17 or 33), else 0
+// (the shared-memory heap of up to 32 entries).  The heap is faster for large clouds, the
+// 32-entry list for small ones (the 512-cloud workload of 1e3..1e5 points: 20.0 against 21.7 ms),
+// so the threshold is an option the batch tuner picks.
+int kc_of(int k, int heap_from) {
+  const int widths[] = {1, 2, 4, 8, 10, 16, 32};
   for (int w : widths)
-    if (k <= w) return w;
+    if (k <= w && k < heap_from) return w;
   return k <= 32 ? 0 : -1;
 }
 
@@ -148,6 +150,7 @@ int arborx_batch_create(int64_t n_clouds, const int64_t *h_point_offsets, const 
   if (o.block_size != 0 && (o.block_size < 32 || o.block_size > 256 || o.block_size % 32)) return ARBORX_EINVAL;
   if (o.stack_smem < 0 || o.stack_smem > 64) return ARBORX_EINVAL;
   if (o.knn_anchor != 0 && o.knn_anchor != 1) return ARBORX_EINVAL;
+  if (o.knn_heap_from != 0 && o.knn_heap_from != 17 && o.knn_heap_from != 33) return ARBORX_EINVAL;
   if (o.queries_per_warp != 0 && o.queries_per_warp != 32 && o.queries_per_warp != 64 &&
       o.queries_per_warp != 128 && o.queries_per_warp != 256)
     return ARBORX_EINVAL;
@@ -163,7 +166,9 @@ int arborx_batch_create(int64_t n_clouds, const int64_t *h_point_offsets, const 
   // internal cloud order: by candidate-list width, then original index
   std::vector<int64_t> order(C);
   for (int64_t c = 0; c < C; ++c) order[c] = c;
-  std::stable_sort(order.begin(), order.end(), [&](int64_t x, int64_t y) { return kc_of(h_k[x]) < kc_of(h_k[y]); });
+  const int heap_from = o.knn_heap_from > 0 ? o.knn_heap_from : 17;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int64_t x, int64_t y) { return kc_of(h_k[x], heap_from) < kc_of(h_k[y], heap_from); });
   std::vector<uint32_t> pt_off(C + 1), q_off(C + 1), cmap(C), sorted_off(C + 1), prim_base(C), ncount(C);
   std::vector<int32_t> kof(C);
   std::vector<int64_t> row_off(M + 1);
@@ -181,7 +186,7 @@ int arborx_batch_create(int64_t n_clouds, const int64_t *h_point_offsets, const 
     prim_base[j] = pt_off[c];
     ncount[j] = nc;
     kof[j] = h_k[c];
-    const int kc = kc_of(h_k[c]);
+    const int kc = kc_of(h_k[c], heap_from);
     if (mc > 0) {
       if (b->classes.empty() || b->classes.back().kc != kc) b->classes.push_back({kc, qpos, qpos});
       b->classes.back().end = qpos + mc;

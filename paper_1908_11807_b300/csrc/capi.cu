@@ -136,6 +136,7 @@ TravCfg trav_cfg(const arborx_bvh_s *h, int which) {
   c.block = h->opts.block_size > 0 ? h->opts.block_size : 128;
   c.stack_smem = h->opts.stack_smem > 0 ? h->opts.stack_smem : 16;
   c.stats_nodes = h->opts.stats ? &h->meta->nodes[which] : nullptr;
+  c.heap_from = h->opts.knn_heap_from;
   return c;
 }
 
@@ -161,6 +162,7 @@ bool opts_ok(const arborx_opts &o) {
   if (o.build_method != ARBORX_BUILD_APETREI && o.build_method != ARBORX_BUILD_KARRAS) return false;
   if (o.sorted_rows != 0 && o.sorted_rows != 1) return false;
   if (o.knn_anchor != 0 && o.knn_anchor != 1) return false;
+  if (o.knn_heap_from != 0 && o.knn_heap_from != 17 && o.knn_heap_from != 33) return false;
   if (o.queries_per_warp != 0 && o.queries_per_warp != 32 && o.queries_per_warp != 64 &&
       o.queries_per_warp != 128 && o.queries_per_warp != 256)
     return false;
@@ -417,6 +419,7 @@ int arborx_default_opts(arborx_opts *o) {
   o->sorted_rows = 0;
   o->knn_anchor = 1;
   o->queries_per_warp = 0;
+  o->knn_heap_from = 0;
   return ARBORX_OK;
 }
 

@@ -35,6 +35,7 @@ struct TravCfg {
   int block;                       // threads per block
   int stack_smem;                  // stack entries per thread kept in shared memory
   unsigned long long *stats_nodes; // nullable: add the internal nodes loaded here
+  int heap_from = 17;              // nearest: k from which the shared-memory heap replaces the register list
 };
 
 void launch_iota(uint32_t *out, uint32_t m, cudaStream_t s);

@@ -26,8 +26,9 @@ constexpr int kMaxBlock = 256;  // traversal block size limit (register budget)
 // measured at 1e7 points / 1e6 queries: the heap beats a 32-entry register list from k = 17
 // (k = 32: 5.1 vs 7.9 ms); an 8-entry deferred-insert buffer beats 4 and 16 entries
 constexpr int kHeapDefer = 8;  // deferred-insert buffer of the shared-memory heap path
-constexpr int kHeapFrom = 17;  // smallest k served by the shared-memory heap
-static_assert(kHeapFrom <= 17, "register lists exist for k <= 16 only");
+// k from which the shared-memory heap serves a single tree's nearest query (opts.knn_heap_from may
+// raise it to 33: register lists exist for every k up to 32)
+constexpr int kHeapFrom = 17;
 constexpr int kBatchHeapK = 32;             // largest k of the batched path (heap class)
 // shared-memory stack entries of the heap paths (deeper entries spill to local memory): the heap
 // takes 8k bytes of shared memory per thread, so a short shared stack buys resident warps
@@ -975,7 +976,7 @@ int launch_batch_nearest(const BatchQueryArgs &args, int kc, const TravCfg &cfg,
   // one profiler name per query class, so that the report splits the batch's time by list width
   const char *name = kc == 0 ? "batch_nearest_heap" : kc == 1 ? "batch_nearest_k1" : kc == 2 ? "batch_nearest_k2"
                      : kc == 4 ? "batch_nearest_k4" : kc == 8 ? "batch_nearest_k8" : kc == 10 ? "batch_nearest_k10"
-                     : "batch_nearest_k16";
+                     : kc == 16 ? "batch_nearest_k16" : "batch_nearest_k32";
   prof::Scope ps(s, name);
 #define ABX_BATCH(KC)                                                                                  \
   do {                                                                                                 \
@@ -992,6 +993,7 @@ int launch_batch_nearest(const BatchQueryArgs &args, int kc, const TravCfg &cfg,
     case 8: ABX_BATCH(8); break;
     case 10: ABX_BATCH(10); break;
     case 16: ABX_BATCH(16); break;
+    case 32: ABX_BATCH(32); break;
     default: return -1;
   }
 #undef ABX_BATCH
@@ -1005,7 +1007,7 @@ int launch_nearest(NearestArgs a, const TravCfg &cfg, cudaStream_t s) {
   const uint32_t threads = a.m + 1;
   int block = cfg.block;
   // large k: candidates in a shared-memory heap (a 64-entry register list measured 2x slower at k = 50)
-  const bool use_heap = k >= kHeapFrom;
+  const bool use_heap = k >= (cfg.heap_from > 0 ? cfg.heap_from : kHeapFrom);
   a.stack_smem = use_heap ? std::min(cfg.stack_smem, kHeapStackSmem) : cfg.stack_smem;
   size_t smem = (size_t)2 * a.stack_smem * block * sizeof(int32_t);
   if (use_heap) {
@@ -1024,7 +1026,8 @@ int launch_nearest(NearestArgs a, const TravCfg &cfg, cudaStream_t s) {
   else if (k <= 4) nearest_kc<4>(grid, block, smem, s, a);
   else if (k <= 8) nearest_kc<8>(grid, block, smem, s, a);
   else if (k <= 10) nearest_kc<10>(grid, block, smem, s, a);
-  else nearest_kc<16>(grid, block, smem, s, a);  // k <= 16 < kHeapFrom
+  else if (k <= 16) nearest_kc<16>(grid, block, smem, s, a);
+  else nearest_kc<32>(grid, block, smem, s, a);  // k <= 32 < heap_from
   return 0;
 }
 

@@ -95,3 +95,18 @@ def test_binding_refuses_cpu_tensors():
     import paper_1908_11807_b300 as ab
     with pytest.raises(TypeError):
         ab.BVH(torch.zeros((10, 3)))
+
+
+def test_option_struct_matches_the_header(L):
+    # the binding's ctypes struct lists the header's fields in the header's order, and the
+    # library fills the documented defaults (no GPU needed)
+    import paper_1908_11807_b300 as ab
+    src = open(HEADER).read()
+    body = src[src.index("typedef struct arborx_opts {"):src.index("} arborx_opts;")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = re.findall(r"\b(\w+)\s*;", body)
+    from paper_1908_11807_b300 import _binding
+    assert fields == [f for f, _ in _binding.arborx_opts._fields_]
+    o = ab.default_opts()
+    assert (o.key_bits, o.sort_queries, o.validate, o.knn_anchor, o.queries_per_warp, o.knn_heap_from) == \
+        (30, 1, 1, 1, 0, 0)

@@ -73,11 +73,12 @@ def test_tune_batch_returns_valid_tiles_with_the_default_results():
     P, Q = dev(pts), dev(qs)
     t = autotune.tune_batch(po, qo, ks, P, Q, blocks=(64, 128), stacks=(4, 16))
     assert t["block_size"] in (64, 128) and t["stack_smem"] in (4, 16)
-    assert t["queries_per_warp"] in autotune.DEFAULT_QPW
+    assert t["queries_per_warp"] in autotune.DEFAULT_QPW and t["knn_heap_from"] in autotune.DEFAULT_HEAP_FROM
     ref = ab.Batch(po, qo, ks)
     o0, i0, d0 = ref.run(P, Q)
-    for qpw in (32, 64, 128, 256):
-        b = ab.Batch(po, qo, ks, block_size=t["block_size"], stack_smem=t["stack_smem"], queries_per_warp=qpw)
+    for qpw, hf in ((32, 17), (64, 33), (128, 17), (256, 33)):
+        b = ab.Batch(po, qo, ks, block_size=t["block_size"], stack_smem=t["stack_smem"], queries_per_warp=qpw,
+                     knn_heap_from=hf)
         o1, i1, d1 = b.run(P, Q, use_graph=True)
         b.check()
         assert torch.equal(o0, o1) and torch.equal(i0, i1) and torch.equal(d0, d1)
@@ -93,8 +94,10 @@ def test_tune_batch_returns_valid_tiles_with_the_default_results():
     ref.destroy()
 
 
-def test_batch_rejects_bad_queries_per_warp():
+def test_batch_rejects_bad_tiles():
     import paper_1908_11807_b300 as ab
     po = np.array([0, 100], np.int64)
     with pytest.raises(ab.ArborXError):
         ab.Batch(po, po, np.array([5], np.int32), queries_per_warp=48)
+    with pytest.raises(ab.ArborXError):
+        ab.Batch(po, po, np.array([5], np.int32), knn_heap_from=20)

@@ -71,6 +71,19 @@ def test_nearest_every_list_width(k):
     assert_nearest_equal(host(ig), host(dg), io, do)
 
 
+@pytest.mark.parametrize("k", [17, 20, 31, 32, 33])
+def test_nearest_register_list_up_to_32(k):
+    # knn_heap_from = 33 serves k <= 32 with a 32-entry register list instead of the heap
+    ab = _ab()
+    p, q = datagen.workload("cube", 3000, 700, 23)
+    io, do = oracle.nearest_brute(p, q, k)
+    for hf in (17, 33):
+        bvh = ab.BVH(dev(p), knn_heap_from=hf)
+        ig, dg = bvh.query_nearest(dev(q), k)
+        bvh.check()
+        assert_nearest_equal(host(ig), host(dg), io, do)
+
+
 @pytest.mark.parametrize("opts", [dict(sort_queries=0), dict(key_bits=63), dict(build_method=1), dict(stack_smem=1),
                                   dict(stack_smem=64, block_size=64), dict(block_size=256, stack_smem=4),
                                   dict(block_size=32), dict(knn_anchor=0), dict(knn_anchor=0, build_method=1)])
