@@ -701,7 +701,9 @@ def configs_extra(ab, dev, topts):
         p = torch.from_numpy(p_h).to(dev)
         q = torch.from_numpy(q_h).to(dev)
         build_ms = _time_ms(lambda: ab.BVH(p, **topts).destroy())
-        bvh = ab.BVH(p, **topts)
+        # the queried tree keeps its sorted leaf order, so that the per-radius pick can also choose
+        # the traversal that takes wholly contained subtrees from it
+        bvh = ab.BVH(p, keep_order=1, **topts)
         order = bvh.query_order(q)
         order_ms = _time_ms(lambda: bvh.query_order(q))
         row = {"n": int(p_h.shape[0]), "m": int(q_h.shape[0]), "build_ms": round(build_ms, 3),
@@ -720,7 +722,9 @@ def configs_extra(ab, dev, topts):
             bvh.check()
             row[f"radius_{r:.4g}"] = {"ms": round(sp_ms, 3), "mq_s": round(q_h.shape[0] / sp_ms / 1e3, 1),
                                       "hits_per_query": round(nnz / q_h.shape[0], 2), "buffer_size": bs,
-                                      "buffer_candidates_ms": pick["ms"]}
+                                      "buffer_candidates_ms": pick["ms"], "emit_subtrees": pick["emit_subtrees"],
+                                      "emit_ms": pick.get("emit_ms")}
+            bvh.emit_subtrees(False)
             del rows
         if k:
             kn_ms = _time_ms(lambda: bvh.query_nearest(q, k, order=order))

@@ -27,6 +27,7 @@ ARBORX_BOXES = 1
 ARBORX_BUILD_APETREI = 0
 ARBORX_BUILD_KARRAS = 1
 ARBORX_MAX_K = 512
+ARBORX_QOPT_EMIT_SUBTREES = 1
 MLP_PARAMS = 4481
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -109,6 +110,7 @@ def lib() -> ctypes.CDLL:
         L.arborx_query_nearest_learned.argtypes = [vp, vp, i64, i32, vp, ctypes.c_float, vp, vp, vp, vp, vp,
                                                    ctypes.POINTER(i64)]
         L.arborx_stats.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_uint64)]
+        L.arborx_set_query_option.argtypes = [vp, i32, i64]
         L.arborx_export_tree.argtypes = [vp, vp, vp, vp, vp, vp]
         L.arborx_sort_pairs.argtypes = [vp, vp, i64, i32, vp]
         L.arborx_sort_pairs_noalloc.argtypes = [vp, vp, i64, i32, vp]
@@ -263,6 +265,13 @@ class BVH:
                 if e.code != ARBORX_EOVERFLOW:
                     raise
             cap = total
+
+    def emit_subtrees(self, on: bool = True) -> None:
+        """Radius and box queries take wholly contained subtrees from the kept sorted leaf order
+        instead of walking them (needs keep_order=1; speed only)."""
+        _check(lib().arborx_set_query_option(self.handle, ARBORX_QOPT_EMIT_SUBTREES, int(bool(on))),
+               "arborx_set_query_option")
+        self._emit = bool(on)
 
     def stats(self) -> dict:
         """Internal nodes loaded and queries traversed since the last call (needs stats=1)."""

@@ -153,7 +153,9 @@ def pick_buffer(bvh, queries: torch.Tensor, radius: float, order: Optional[torch
     so the useful widths sit at the top of the hit-count distribution.  The candidates are two
     passes and the median, 99th percentile and largest count of a strided sample of the queries
     (each rounded up to a multiple of 4, at most 4096 and at most 4 GB of buffer); each is timed
-    on all the queries and the fastest is returned with the timings and the sample's counts."""
+    on all the queries and the fastest is returned with the timings and the sample's counts.  On a
+    tree built with keep_order=1 the subtree-emitting traversal is timed at that width too, and
+    left switched on for the tree (``emit_subtrees``) when it is faster."""
     m = int(queries.shape[0])
     if m == 0:
         return {"buffer_size": 0, "ms": {}, "hits": {}}
@@ -163,6 +165,9 @@ def pick_buffer(bvh, queries: torch.Tensor, radius: float, order: Optional[torch
     hits = {"mean": float(cnt.mean()), "p50": float(cnt.quantile(0.5)), "p99": float(cnt.quantile(0.99)),
             "max": float(cnt.max())}
     cap = min(MAX_BUFFER_SIZE, (BUFFER_BYTES_CAP // (4 * m)) // 4 * 4)
+    keep = bool(getattr(bvh.opts, "keep_order", 0))
+    if keep:
+        bvh.emit_subtrees(False)  # widths are timed with the walking traversal
     cands = {0}
     if cap >= 4:
         cands |= {min(cap, _round4(hits[q])) for q in ("p50", "p99", "max")}
@@ -170,7 +175,18 @@ def pick_buffer(bvh, queries: torch.Tensor, radius: float, order: Optional[torch
     for bs in sorted(cands):
         ms[bs] = round(_time(lambda: bvh.query_spatial(queries, radius, order=order, buffer_size=bs), reps), 4)
     best = min(ms, key=ms.get)
-    return {"buffer_size": best, "ms": ms, "hits": {k: round(v, 2) for k, v in hits.items()}}
+    out = {"buffer_size": best, "ms": ms, "hits": {k: round(v, 2) for k, v in hits.items()}, "emit_subtrees": False}
+    if keep:
+        # a tree that keeps its sorted leaf order can also take contained subtrees whole: timed at
+        # the best width, kept on only if faster
+        bvh.emit_subtrees(True)
+        t = round(_time(lambda: bvh.query_spatial(queries, radius, order=order, buffer_size=best), reps), 4)
+        out["emit_ms"] = t
+        if t < ms[best]:
+            out["emit_subtrees"] = True
+        else:
+            bvh.emit_subtrees(False)
+    return out
 
 
 DEFAULT_QPW = (32, 64, 128)

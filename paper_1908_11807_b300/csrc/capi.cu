@@ -47,6 +47,8 @@ struct arborx_bvh_s {
   size_t sbuf_bytes;
   int buf_bs;
   bool buffered_valid;
+  // radius and box queries emit wholly contained subtrees from the kept leaf order
+  bool emit_subtrees;
 };
 
 namespace {
@@ -137,6 +139,11 @@ TravCfg trav_cfg(const arborx_bvh_s *h, int which) {
   c.stack_smem = h->opts.stack_smem > 0 ? h->opts.stack_smem : 16;
   c.stats_nodes = h->opts.stats ? &h->meta->nodes[which] : nullptr;
   c.heap_from = h->opts.knn_heap_from;
+  if (h->emit_subtrees && h->order && h->n > 0) {  // the kept permutation follows the widened codes
+    c.leafperm = reinterpret_cast<const uint32_t *>(static_cast<const char *>(h->order) +
+                                                    align_up((size_t)h->n * sizeof(uint64_t)));
+    c.numbering = h->opts.build_method == ARBORX_BUILD_KARRAS ? 1 : 0;
+  }
   return c;
 }
 
@@ -1083,6 +1090,17 @@ int arborx_query_intersects(arborx_handle h, const float *d_boxes, int64_t m, in
   h->stat_queries[0] += (uint64_t)m;
   st = sort_rows(h, d_offsets, d_indices, m, capacity, s);
   return st ? st : launch_status();
+}
+
+int arborx_set_query_option(arborx_handle h, int32_t option, int64_t value) {
+  if (!h) return ARBORX_EINVAL;
+  if (option == ARBORX_QOPT_EMIT_SUBTREES) {
+    if (value != 0 && value != 1) return ARBORX_EINVAL;
+    if (value == 1 && !h->opts.keep_order) return ARBORX_ESTATE;
+    h->emit_subtrees = value == 1;
+    return ARBORX_OK;
+  }
+  return ARBORX_EINVAL;
 }
 
 int arborx_stats(arborx_handle h, void *stream, uint64_t out[4]) {

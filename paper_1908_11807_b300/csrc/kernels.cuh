@@ -36,6 +36,8 @@ struct TravCfg {
   int stack_smem;                  // stack entries per thread kept in shared memory
   unsigned long long *stats_nodes; // nullable: add the internal nodes loaded here
   int heap_from = 17;              // nearest: k from which the shared-memory heap replaces the register list
+  const uint32_t *leafperm = nullptr;  // spatial: emit contained subtrees from this sorted leaf order
+  int numbering = 0;                   // 0: internal node p splits leaves p | p+1 (Apetrei); 1: Karras ids
 };
 
 void launch_iota(uint32_t *out, uint32_t m, cudaStream_t s);
@@ -61,6 +63,8 @@ struct SpatialArgs {
   uint32_t *err;
   int stack_smem;
   unsigned long long *stats;
+  const uint32_t *leafperm;  // non-null only in the subtree-emitting kernels
+  int numbering;
 };
 
 // Spatial predicates: box = false, queries are points float[m][3] matched within r2; box = true,

@@ -100,6 +100,15 @@ struct SpatialPred<false> {
         qz(__ldg(a.queries + 3 * (uint64_t)qi + 2)), r2(a.r2) {}
   __device__ __forceinline__ bool valid() const { return finite3(qx, qy, qz); }
   __device__ __forceinline__ bool operator()(float4 lo, float4 hi) const { return dist2_box(qx, qy, qz, lo, hi) <= r2; }
+  // the whole box within r: per axis |fl(q - p)| <= max(|fl(q - lo)|, |fl(q - hi)|) for every p in
+  // it (round-to-nearest subtraction is monotone), so the farthest corner's squared distance,
+  // summed in the same order, bounds the FP32 distance of every point inside
+  __device__ __forceinline__ bool contains(float4 lo, float4 hi) const {
+    const float gx = fmaxf(fabsf(__fsub_rn(qx, lo.x)), fabsf(__fsub_rn(qx, hi.x)));
+    const float gy = fmaxf(fabsf(__fsub_rn(qy, lo.y)), fabsf(__fsub_rn(qy, hi.y)));
+    const float gz = fmaxf(fabsf(__fsub_rn(qz, lo.z)), fabsf(__fsub_rn(qz, hi.z)));
+    return __fadd_rn(__fadd_rn(__fmul_rn(gx, gx), __fmul_rn(gy, gy)), __fmul_rn(gz, gz)) <= r2;
+  }
 };
 
 template <>
@@ -114,9 +123,22 @@ struct SpatialPred<true> {
   __device__ __forceinline__ bool operator()(float4 lo, float4 hi) const {
     return lo.x <= hx && hi.x >= lx && lo.y <= hy && hi.y >= ly && lo.z <= hz && hi.z >= lz;
   }
+  // the node box inside the query box: every primitive box inside it meets the query
+  __device__ __forceinline__ bool contains(float4 lo, float4 hi) const {
+    return lo.x >= lx && hi.x <= hx && lo.y >= ly && hi.y <= hy && lo.z >= lz && hi.z <= hz;
+  }
 };
 
-template <int MODE, bool BOX>
+// First sorted leaf of the internal child on `side` of node p, with child id c and cnt leaves.
+// Apetrei numbering: node p splits leaves p | p + 1, so its left child ends at p and its right
+// child starts at p + 1.  Karras numbering: a node's id is one end of its range, the right end for
+// a left child and the left end for a right child.
+__device__ __forceinline__ int child_first(int numbering, int p, int side, int c, int cnt) {
+  if (numbering == 0) return side == 0 ? p + 1 - cnt : p + 1;
+  return side == 0 ? c - cnt + 1 : c;
+}
+
+template <int MODE, bool BOX, bool EMIT>
 __device__ __forceinline__ void spatial_traverse(const SpatialArgs &a) {
   extern __shared__ int32_t s_stack[];
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -144,12 +166,26 @@ __device__ __forceinline__ void spatial_traverse(const SpatialArgs &a) {
     ++cnt;                                                \
   } while (0)
 
+  // every leaf of a subtree inside the query: its slice [first, first + sc) of the sorted order
+  auto emit_range = [&](int first, int sc) {
+    if (first < 0 || sc < 1 || (uint32_t)first + (uint32_t)sc > n) {  // corrupt tree: read nothing outside
+      set_err(a.err, ERR_STACK);
+      return;
+    }
+    if (MODE == kCount) {
+      cnt += (uint32_t)sc;
+    } else {
+      for (int j = 0; j < sc; ++j) ABX_EMIT((int32_t)__ldg(a.leafperm + first + j));
+    }
+  };
   if (n > 0 && hit.valid()) {
     const float4 r0 = __ldg(rec), r1 = __ldg(rec + 1);
     if (hit(r0, r1)) {
       const int e0 = __float_as_int(r0.w);
       if (e0 < 0) {
         ABX_EMIT(~e0);
+      } else if (EMIT && hit.contains(r0, r1)) {
+        emit_range(0, (int)n);
       } else {
         int32_t *my = s_stack + threadIdx.x;
         const int stride = blockDim.x;
@@ -204,11 +240,14 @@ __device__ __forceinline__ void spatial_traverse(const SpatialArgs &a) {
           // a child slot that meets the predicate: a leaf is a result, an internal node is walked
           // next (the first one) or pushed
           int next = -1;
-          auto take = [&](float4 lo, float4 hi) {
+          auto take = [&](float4 lo, float4 hi, int p, int side) {
             const int e = __float_as_int(lo.w);
             if (hit(lo, hi)) {
               if (e < 0) {
                 ABX_EMIT(~e);
+              } else if (EMIT && hit.contains(lo, hi)) {
+                const int sc = __float_as_int(hi.w);
+                emit_range(child_first(a.numbering, p, side, e, sc), sc);
               } else if (next < 0) {
                 next = e;
               } else {
@@ -216,15 +255,15 @@ __device__ __forceinline__ void spatial_traverse(const SpatialArgs &a) {
               }
             }
           };
-          take(a0, a1);
-          take(b0, b1);
+          take(a0, a1, node, 0);
+          take(b0, b1, node, 1);
           if (nb >= 0) {
-            take(c0, c1);
-            take(d0, d1);
+            take(c0, c1, nb, 0);
+            take(d0, d1, nb, 1);
           }
           if (nc >= 0) {
-            take(e0v, e1v);
-            take(f0, f1);
+            take(e0v, e1v, nc, 0);
+            take(f0, f1, nc, 1);
           }
           if (next < 0) {
             if (sp == 0) break;
@@ -241,15 +280,17 @@ __device__ __forceinline__ void spatial_traverse(const SpatialArgs &a) {
   if (a.stats) add_stat(a.stats, visited);
 }
 
-// Radius queries (points within r) and box queries (boxes met), one kernel name each.
-template <int MODE>
+// Radius queries (points within r) and box queries (boxes met), one kernel name each; EMIT: the
+// variant that takes wholly contained subtrees from the sorted leaf order (more registers, so a
+// separate instantiation that only trees with that query option run).
+template <int MODE, bool EMIT>
 __global__ void __launch_bounds__(kMaxBlock) k_spatial(const __grid_constant__ SpatialArgs a) {
-  spatial_traverse<MODE, false>(a);
+  spatial_traverse<MODE, false, EMIT>(a);
 }
 
-template <int MODE>
+template <int MODE, bool EMIT>
 __global__ void __launch_bounds__(kMaxBlock) k_intersects(const __grid_constant__ SpatialArgs a) {
-  spatial_traverse<MODE, true>(a);
+  spatial_traverse<MODE, true, EMIT>(a);
 }
 
 // Move buffered rows (those that fit) to their CSR place.  A thread takes
@@ -853,8 +894,9 @@ static void spatial_launch(const SpatialArgs &args, bool box, int block, cudaStr
   prof::Scope ps(s, box ? (MODE == kBuffered ? "intersects_buffered" : MODE == kFill ? "intersects_fill"
                                                                                      : "intersects_count")
                         : name);
-  if (box) spatial_launch2(k_intersects<MODE>, args, block, smem, s);
-  else spatial_launch2(k_spatial<MODE>, args, block, smem, s);
+  const bool emit = args.leafperm != nullptr;
+  if (box) spatial_launch2(emit ? k_intersects<MODE, true> : k_intersects<MODE, false>, args, block, smem, s);
+  else spatial_launch2(emit ? k_spatial<MODE, true> : k_spatial<MODE, false>, args, block, smem, s);
 }
 
 static SpatialArgs spatial_args(const float4 *rec, uint32_t n, const float *queries, const uint32_t *qperm, uint32_t m,
@@ -869,6 +911,8 @@ static SpatialArgs spatial_args(const float4 *rec, uint32_t n, const float *quer
   a.err = err;
   a.stack_smem = cfg.stack_smem;
   a.stats = cfg.stats_nodes;
+  a.leafperm = cfg.leafperm;
+  a.numbering = cfg.numbering;
   return a;
 }
 

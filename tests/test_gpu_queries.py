@@ -71,6 +71,58 @@ def test_nearest_every_list_width(k):
     assert_nearest_equal(host(ig), host(dg), io, do)
 
 
+@pytest.mark.parametrize("build_method", [0, 1])
+@pytest.mark.parametrize("name", ["cube_1e4", "duplicates", "flat_plane", "boxes", "paper_hollow"])
+def test_subtree_emission_matches_brute_force(name, build_method):
+    # radius and box rows with wholly contained subtrees taken from the kept leaf order (both
+    # builders' node numberings), through the two-pass, one-pass and one-call forms, at the
+    # workload's radius and at a radius holding hundreds of points per row
+    ab = _ab()
+    p, q, r = CASES[name]()
+    bvh = ab.BVH(dev(p), keep_order=1, build_method=build_method)
+    bvh.emit_subtrees(True)
+    qd = dev(q)
+    for rr in (r, 3 * r):
+        oo, io = oracle.spatial_brute(p, q, rr)
+        og, ig = bvh.query_spatial(qd, rr)
+        assert_spatial_equal(host(og), host(ig), oo, io)
+        og, ig = bvh.query_spatial(qd, rr, buffer_size=16)
+        assert_spatial_equal(host(og), host(ig), oo, io)
+        og, ig = bvh.query_spatial_async(qd, rr, buffer_size=8, capacity=max(int(oo[-1]), 1))
+        assert_spatial_equal(host(og), host(ig)[:int(host(og)[-1])], oo, io)
+        bvh.check()
+    qb = np.concatenate([q - 2 * r, q + 2 * r], 1).astype(np.float32)
+    ob, ib = oracle.intersects_brute(p, qb)
+    og, ig = bvh.query_intersects(dev(qb), buffer_size=16)
+    bvh.check()
+    assert_spatial_equal(host(og), host(ig), ob, ib)
+
+
+def test_subtree_emission_lattice_and_whole_tree():
+    # lattice rows from integer enumeration, and a radius that contains the whole tree (the root
+    # itself is emitted)
+    ab = _ab()
+    side = 24
+    g = np.arange(side, dtype=np.float32)
+    pts = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    sites = pts[np.random.default_rng(55).integers(0, len(pts), 3000)]
+    bvh = ab.BVH(dev(pts), keep_order=1)
+    bvh.emit_subtrees(True)
+    for r in (1.0, 2.5, 4.0, 100.0):
+        oo, io = oracle.spatial_brute(pts, sites, r)
+        og, ig = bvh.query_spatial(dev(sites), r, buffer_size=32)
+        bvh.check()
+        assert_spatial_equal(host(og), host(ig), oo, io)
+
+
+def test_subtree_emission_needs_the_kept_order():
+    ab = _ab()
+    bvh = ab.BVH(dev(datagen.cube(100, 56)))
+    with pytest.raises(ab.ArborXError):
+        bvh.emit_subtrees(True)
+    bvh.emit_subtrees(False)
+
+
 @pytest.mark.parametrize("k", [17, 20, 31, 32, 33])
 def test_nearest_register_list_up_to_32(k):
     # knn_heap_from = 33 serves k <= 32 with a 32-entry register list instead of the heap

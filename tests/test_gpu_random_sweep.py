@@ -31,7 +31,8 @@ def _case(seed):
     opts = dict(sort_queries=int(g.integers(0, 2)), key_bits=int(g.choice([30, 63])),
                 build_method=int(g.integers(0, 2)), sorted_rows=int(g.integers(0, 2)),
                 block_size=int(g.choice([32, 64, 128, 256])), stack_smem=int(g.choice([0, 1, 4, 16])),
-                knn_anchor=int(g.integers(0, 2)), knn_heap_from=int(g.choice([0, 17, 33])))
+                knn_anchor=int(g.integers(0, 2)), knn_heap_from=int(g.choice([0, 17, 33])),
+                keep_order=int(g.integers(0, 2)))
     r = float(g.choice([0.0, g.uniform(0.01, 0.3), 2.0]))
     k = int(g.choice([1, 5, 10, 16, 17, 27, 40]))
     bs = int(g.choice([1, 4, 16, 32]))
@@ -44,6 +45,8 @@ def test_random_case_matches_brute_force(seed):
     import paper_1908_11807_b300 as ab
     p, q, opts, r, k, bs, half = _case(seed)
     bvh = ab.BVH(dev(p), **opts)
+    if opts["keep_order"]:
+        bvh.emit_subtrees(True)  # radius and box rows take contained subtrees whole
     qd = dev(q)
     oo, io = oracle.spatial_brute(p, q, r)
     exact_rows = bool(opts["sorted_rows"])
