@@ -104,12 +104,15 @@ typedef struct arborx_opts {
                            order (two stable radix sorts over the result entries; results up to
                            ARBORX_MAX_PRIMS entries, else ARBORX_EINVAL); 0 (default): traversal order.
                            The paper leaves row order open (rows are sets). */
-  int32_t knn_anchor;   /* 1 (default): a nearest query with no caller-supplied bound first walks from the
-                           root toward the query through subtrees of at least k leaves and starts its
-                           traversal with the farthest-corner distance of the smallest such box as the
-                           k-th-distance bound (exact: that box holds k primitives), so candidates and
-                           stack entries beyond it are never inserted or pushed; 0: the traversal starts
-                           unbounded, as in Sec. 2.2.2.  Results are identical either way. */
+  int32_t knn_anchor;   /* a nearest query with no caller-supplied bound first walks from the root toward
+                           the query through subtrees of at least k leaves and starts its traversal with
+                           the farthest-corner distance of such a box as the k-th-distance bound (exact:
+                           that box holds k primitives), so candidates and stack entries beyond it are
+                           never inserted or pushed.  1 (default): the walk follows the child with the
+                           nearer farthest corner and keeps the smallest seen (best on uniform clouds
+                           at k = 10-16); 2: it follows the child holding the query (best on clustered
+                           clouds and small k); 0: the traversal starts unbounded, as in Sec. 2.2.2.
+                           Results are identical in every case. */
   int32_t queries_per_warp; /* batched nearest queries (arborx_batch_*): sorted query positions a
                            persistent warp takes from the work queue per fetch, its lanes serving 32 at
                            a time (0 = default 32; else 32, 64, 128 or 256).  The single-tree

@@ -1,8 +1,9 @@
 """Autotuner for the query launch parameters.
 
 Picks, for a workload class, the traversal block size, the number of stack
-entries kept in shared memory, the row-buffer estimate of the one-pass spatial
-query (0 = two passes) and the margin of the learned bound, by timing the
+entries kept in shared memory, the walk form of the nearest query's tree bound,
+the row-buffer estimate of the one-pass spatial query (0 = two passes) and the
+margin of the learned bound, by timing the
 candidates with CUDA events on a sample of the caller's queries
 (``tune``, ``tune_margin``); the row-buffer width for one radius from the
 distribution of its hit counts (``pick_buffer``); and the tiles of the batched
@@ -29,6 +30,7 @@ DEFAULT_BLOCKS = (64, 128, 256)
 DEFAULT_STACKS = (4, 8, 16)
 DEFAULT_BUFFERS = (0, 16, 24, 32)
 DEFAULT_MARGINS = (0.0, 0.1, 0.2, 0.35, 0.5, 0.7, 0.9)
+DEFAULT_ANCHORS = (1, 2)  # walk forms of the nearest query's tree bound
 
 
 def cache_path() -> str:
@@ -77,9 +79,10 @@ def _time(fn, reps: int = 3) -> float:
 def tune(points: torch.Tensor, queries: torch.Tensor, radius: float, k: int, tag: str,
          blocks: Iterable[int] = DEFAULT_BLOCKS, stacks: Iterable[int] = DEFAULT_STACKS,
          buffers: Iterable[int] = DEFAULT_BUFFERS, params: Optional[torch.Tensor] = None,
-         margins: Iterable[float] = DEFAULT_MARGINS, use_cache: bool = True) -> dict:
-    """Return {"block_size", "stack_smem", "buffer_size", "margin", "ms"} for this workload
-    class, timing the candidates on (points, queries) unless the cache has them."""
+         margins: Iterable[float] = DEFAULT_MARGINS, anchors: Iterable[int] = DEFAULT_ANCHORS,
+         use_cache: bool = True) -> dict:
+    """Return {"block_size", "stack_smem", "buffer_size", "margin", "knn_anchor", "ms"} for this
+    workload class, timing the candidates on (points, queries) unless the cache has them."""
     key = cache_key(points.shape[0], k, tag)
     if use_cache:
         hit = _load().get(key)
@@ -97,7 +100,15 @@ def tune(points: torch.Tensor, queries: torch.Tensor, radius: float, k: int, tag
                 best = cand
             bvh.destroy()
     _, block, stack = best
-    bvh = _b.BVH(points, block_size=block, stack_smem=stack)
+    # the walk form of the nearest query's tree bound, at the best launch parameters
+    anchor_ms = {}
+    for anchor in anchors:
+        bvh = _b.BVH(points, block_size=block, stack_smem=stack, knn_anchor=anchor)
+        order = bvh.query_order(queries)
+        anchor_ms[anchor] = _time(lambda: bvh.query_nearest(queries, k, order=order))
+        bvh.destroy()
+    anchor = min(anchor_ms, key=anchor_ms.get)
+    bvh = _b.BVH(points, block_size=block, stack_smem=stack, knn_anchor=anchor)
     order = bvh.query_order(queries)
     buf_best = min((_time(lambda: bvh.query_spatial(queries, radius, order=order, buffer_size=bs)), bs)
                    for bs in buffers)[1]
@@ -107,7 +118,7 @@ def tune(points: torch.Tensor, queries: torch.Tensor, radius: float, k: int, tag
                      for mg in margins)[1]
     bvh.destroy()
     out = {"block_size": block, "stack_smem": stack, "buffer_size": buf_best, "margin": margin,
-           "ms_queries": round(best[0], 4)}
+           "knn_anchor": anchor, "ms_queries": round(best[0], 4)}
     if use_cache:
         _store(key, out)
     return out

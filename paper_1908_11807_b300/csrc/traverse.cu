@@ -640,18 +640,24 @@ __device__ __forceinline__ float far2_box(float qx, float qy, float qz, float4 l
 // Exact upper bound on the squared distance to the k-th nearest primitive, taken from the tree
 // before the traversal: a subtree with at least k leaves (the count is the aux word of its child
 // record) holds k primitives no farther than its box's farthest corner, so that distance bounds
-// the k-th.  A greedy walk from the subtree root at root_slot toward the query through children
-// of at least k leaves keeps the smallest such bound (about 20 node loads at 1e7 points, all on
-// the path the traversal then takes first).  With it as the initial bound the traversal inserts
-// and pushes nothing beyond it; results are unchanged.  +inf when the subtree has fewer than k.
+// the k-th.  A greedy walk from the subtree root at root_slot through children of at least k
+// leaves (about 20 node loads at 1e7 points, all on the path the traversal then takes first)
+// yields it, in one of two forms (mode):
+//   1: descend into the child with the nearer farthest corner and keep the smallest farthest
+//      corner of every child of at least k leaves seen (best on uniform clouds at k = 10-16);
+//   2: descend into the child that holds the query (the nearer one when it lies in neither) and
+//      take the farthest corner of the last such child (cheaper; best on clustered clouds and
+//      small k: the 64-Gaussian mixture, k = 10, 11.4 -> 9.2 ms per 1e7 queries).
+// With it as the initial bound the traversal inserts and pushes nothing beyond it; results are
+// unchanged.  +inf when the subtree has fewer than k.
 __device__ __forceinline__ float anchor_bound2(const float4 *__restrict__ rec, uint32_t n, float qx, float qy,
-                                               float qz, int k, uint32_t &visited, uint32_t root_slot = 0) {
-  float B = __int_as_float(0x7f800000);
-  if (n < 2) return B;
-  const float4 r0 = __ldg(rec + 2 * (uint64_t)root_slot), r1 = __ldg(rec + 2 * (uint64_t)root_slot + 1);
-  if (__float_as_int(r1.w) < k) return B;
-  B = far2_box(qx, qy, qz, r0, r1);
-  int node = __float_as_int(r0.w);
+                                               float qz, int k, int mode, uint32_t &visited, uint32_t root_slot = 0) {
+  const float inf = __int_as_float(0x7f800000);
+  if (n < 2) return inf;
+  float4 blo = __ldg(rec + 2 * (uint64_t)root_slot), bhi = __ldg(rec + 2 * (uint64_t)root_slot + 1);
+  if (__float_as_int(bhi.w) < k) return inf;
+  float B = mode == 1 ? far2_box(qx, qy, qz, blo, bhi) : inf;
+  int node = __float_as_int(blo.w);
   for (int level = 0; level < 128; ++level) {
     if (node < 0 || (uint32_t)node >= n - 1) break;  // a leaf, or a corrupt id: never read outside
     const float4 *rp = rec + 4 + 4 * (uint64_t)node;
@@ -660,13 +666,28 @@ __device__ __forceinline__ float anchor_bound2(const float4 *__restrict__ rec, u
     ld_slot(rp + 2, b0, b1);
     ++visited;  // counted with the traversal's node loads
     const bool oka = __float_as_int(a1.w) >= k, okb = __float_as_int(b1.w) >= k;
-    const float fa = oka ? far2_box(qx, qy, qz, a0, a1) : __int_as_float(0x7f800000);
-    const float fb = okb ? far2_box(qx, qy, qz, b0, b1) : __int_as_float(0x7f800000);
-    B = fminf(B, fminf(fa, fb));
-    if (!oka && !okb) break;
-    node = (oka && (fa <= fb || !okb)) ? __float_as_int(a0.w) : __float_as_int(b0.w);
+    bool takea;
+    if (mode == 1) {
+      const float fa = oka ? far2_box(qx, qy, qz, a0, a1) : inf;
+      const float fb = okb ? far2_box(qx, qy, qz, b0, b1) : inf;
+      B = fminf(B, fminf(fa, fb));
+      if (!oka && !okb) break;
+      takea = oka && (fa <= fb || !okb);
+    } else {
+      if (!oka && !okb) break;
+      if (oka && okb) {
+        const bool ia = qx >= a0.x && qx <= a1.x && qy >= a0.y && qy <= a1.y && qz >= a0.z && qz <= a1.z;
+        const bool ib = qx >= b0.x && qx <= b1.x && qy >= b0.y && qy <= b1.y && qz >= b0.z && qz <= b1.z;
+        takea = ia || (!ib && dist2_box(qx, qy, qz, a0, a1) <= dist2_box(qx, qy, qz, b0, b1));
+      } else {
+        takea = oka;
+      }
+      blo = takea ? a0 : b0;
+      bhi = takea ? a1 : b1;
+    }
+    node = takea ? __float_as_int(a0.w) : __float_as_int(b0.w);
   }
-  return B;
+  return mode == 1 ? B : far2_box(qx, qy, qz, blo, bhi);
 }
 
 // Upper bound on the k-th squared distance of query q taken from a finished row
@@ -718,7 +739,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_nearest(const __grid_constant__ N
   const int64_t row = (int64_t)qi * kk;
   uint32_t visited = 0;
   // the tree's own bound (k = 1 gains nothing: its first leaf already sets the bound)
-  if (a.anchor && k > 1 && ok) b0 = fminf(b0, anchor_bound2(rec, n, qx, qy, qz, k, visited));
+  if (a.anchor && k > 1 && ok) b0 = fminf(b0, anchor_bound2(rec, n, qx, qy, qz, k, a.anchor, visited));
   if constexpr (KC > 0) {
     RegList<KC> L;
     L.init(b0, k);
@@ -768,7 +789,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_batch_nearest(const __grid_consta
         uint32_t visited = 0;
         const bool go = finite3(qx, qy, qz) && slot >= 0;
         float b0 = __int_as_float(0x7f800000);
-        if (a.anchor && go && k > 1) b0 = anchor_bound2(a.rec, a.n, qx, qy, qz, k, visited, (uint32_t)slot);
+        if (a.anchor && go && k > 1) b0 = anchor_bound2(a.rec, a.n, qx, qy, qz, k, a.anchor, visited, (uint32_t)slot);
         if constexpr (KC > 0) {
           RegList<KC> L;
           L.init(b0, k);

@@ -138,7 +138,8 @@ def test_nearest_register_list_up_to_32(k):
 
 @pytest.mark.parametrize("opts", [dict(sort_queries=0), dict(key_bits=63), dict(build_method=1), dict(stack_smem=1),
                                   dict(stack_smem=64, block_size=64), dict(block_size=256, stack_smem=4),
-                                  dict(block_size=32), dict(knn_anchor=0), dict(knn_anchor=0, build_method=1)])
+                                  dict(block_size=32), dict(knn_anchor=0), dict(knn_anchor=0, build_method=1), dict(knn_anchor=2),
+                                  dict(knn_anchor=2, build_method=1)])
 def test_options_do_not_change_results(opts):
     ab = _ab()
     p, q = datagen.workload("hollow_sphere", 30_000, 4000, 22)
@@ -169,7 +170,7 @@ def test_anchor_bound_with_ties_at_the_bound(k, build_method):
     ql = np.concatenate([lat[::7], lat[::11] + 0.5]).astype(np.float32)
     for p, qq in ((dup, q), (lat, ql)):
         ref_i, ref_d = oracle.nearest_brute(p, qq, k)
-        for anchor in (1, 0):
+        for anchor in (1, 2, 0):
             bvh = ab.BVH(dev(p), build_method=build_method, knn_anchor=anchor)
             ig, dg = bvh.query_nearest(dev(qq), k)
             bvh.check()
