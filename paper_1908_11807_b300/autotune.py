@@ -214,12 +214,12 @@ DEFAULT_HEAP_FROM = (17, 33)
 def tune_batch(point_offsets, query_offsets, ks, points: torch.Tensor, queries: torch.Tensor,
                blocks: Iterable[int] = DEFAULT_BLOCKS, stacks: Iterable[int] = DEFAULT_STACKS,
                qpws: Iterable[int] = DEFAULT_QPW, heap_froms: Iterable[int] = DEFAULT_HEAP_FROM,
-               use_cache: bool = True) -> dict:
+               anchors: Iterable[int] = DEFAULT_ANCHORS, use_cache: bool = True) -> dict:
     """Tiles of the batched many-cloud query (block size, shared stack entries, queries per warp,
     and the k from which candidates go to the shared-memory heap instead of a register list) for
     this batch shape, cached by (total points bucket, cloud count, k mix).  Times one graph replay
-    of the whole batch per candidate: the heap threshold first (library tiles), then block and
-    stack, then queries per warp.  Every candidate returns identical results."""
+    of the whole batch per candidate: the heap threshold first (library tiles), then the walk form
+    of the tree bound, then block and stack, then queries per warp.  Every candidate returns identical results."""
     key = batch_cache_key(int(points.shape[0]), ks)
     if use_cache:
         hit = _load().get(key)
@@ -234,19 +234,20 @@ def tune_batch(point_offsets, query_offsets, ks, points: torch.Tensor, queries: 
         return t
 
     hf = min((run_ms(knn_heap_from=h), h) for h in heap_froms)[1]
+    an = min((run_ms(knn_heap_from=hf, knn_anchor=a), a) for a in anchors)[1]
     best = None
     for block in blocks:
         for stack in stacks:
-            cand = (run_ms(block_size=block, stack_smem=stack, knn_heap_from=hf), block, stack, 32)
+            cand = (run_ms(block_size=block, stack_smem=stack, knn_heap_from=hf, knn_anchor=an), block, stack, 32)
             best = cand if best is None or cand < best else best
     for qpw in qpws:
         if qpw == 32:
             continue
-        cand = (run_ms(block_size=best[1], stack_smem=best[2], queries_per_warp=qpw, knn_heap_from=hf),
-                best[1], best[2], qpw)
+        cand = (run_ms(block_size=best[1], stack_smem=best[2], queries_per_warp=qpw, knn_heap_from=hf,
+                       knn_anchor=an), best[1], best[2], qpw)
         best = cand if cand < best else best
     out = {"block_size": best[1], "stack_smem": best[2], "queries_per_warp": best[3], "knn_heap_from": hf,
-           "ms": round(best[0], 4)}
+           "knn_anchor": an, "ms": round(best[0], 4)}
     if use_cache:
         _store(key, out)
     return out

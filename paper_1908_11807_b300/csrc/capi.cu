@@ -424,7 +424,7 @@ int arborx_default_opts(arborx_opts *o) {
   o->build_method = ARBORX_BUILD_APETREI;
   o->stats = 0;
   o->sorted_rows = 0;
-  o->knn_anchor = 1;
+  o->knn_anchor = 2;
   o->queries_per_warp = 0;
   o->knn_heap_from = 0;
   return ARBORX_OK;

@@ -644,14 +644,15 @@ __device__ __forceinline__ float far2_box(float qx, float qy, float qz, float4 l
 // leaves (about 20 node loads at 1e7 points, all on the path the traversal then takes first)
 // yields it, in one of two forms (mode):
 //   1: descend into the child with the nearer farthest corner and keep the smallest farthest
-//      corner of every child of at least k leaves seen (best on uniform clouds at k = 10-16);
-//   2: descend into the child that holds the query (the nearer one when it lies in neither) and
-//      take the farthest corner of the last such child (cheaper; best on clustered clouds and
-//      small k: the 64-Gaussian mixture, k = 10, 11.4 -> 9.2 ms per 1e7 queries).
+//      corner of every child of at least k leaves seen (2% faster on the uniform cube at k = 10);
+//   2 (the default): descend into the child that holds the query (the nearer one when it lies in
+//      neither) and take the farthest corner of the last such child (cheaper, and tighter on
+//      clustered clouds: the 64-Gaussian mixture, k = 10, 11.4 -> 9.25 ms per 1e7 queries).
 // With it as the initial bound the traversal inserts and pushes nothing beyond it; results are
 // unchanged.  +inf when the subtree has fewer than k.
+template <int mode>
 __device__ __forceinline__ float anchor_bound2(const float4 *__restrict__ rec, uint32_t n, float qx, float qy,
-                                               float qz, int k, int mode, uint32_t &visited, uint32_t root_slot = 0) {
+                                               float qz, int k, uint32_t &visited, uint32_t root_slot = 0) {
   const float inf = __int_as_float(0x7f800000);
   if (n < 2) return inf;
   float4 blo = __ldg(rec + 2 * (uint64_t)root_slot), bhi = __ldg(rec + 2 * (uint64_t)root_slot + 1);
@@ -667,7 +668,7 @@ __device__ __forceinline__ float anchor_bound2(const float4 *__restrict__ rec, u
     ++visited;  // counted with the traversal's node loads
     const bool oka = __float_as_int(a1.w) >= k, okb = __float_as_int(b1.w) >= k;
     bool takea;
-    if (mode == 1) {
+    if constexpr (mode == 1) {
       const float fa = oka ? far2_box(qx, qy, qz, a0, a1) : inf;
       const float fb = okb ? far2_box(qx, qy, qz, b0, b1) : inf;
       B = fminf(B, fminf(fa, fb));
@@ -708,7 +709,7 @@ __device__ __forceinline__ float neighbour_bound2(const NearestArgs &a, uint32_t
 
 // Threads t <= m also write offsets[t] = t * kk (CSR view of the rows).  Thread
 // t serves sorted position pos = pos_list ? pos_list[t] : t, query qperm[pos].
-template <int KC, bool NBR>
+template <int KC, bool NBR, int ANCHOR>
 __global__ void __launch_bounds__(kMaxBlock) k_nearest(const __grid_constant__ NearestArgs a) {
   extern __shared__ unsigned char s_raw[];
   const float4 *__restrict__ rec = a.rec;
@@ -739,7 +740,9 @@ __global__ void __launch_bounds__(kMaxBlock) k_nearest(const __grid_constant__ N
   const int64_t row = (int64_t)qi * kk;
   uint32_t visited = 0;
   // the tree's own bound (k = 1 gains nothing: its first leaf already sets the bound)
-  if (a.anchor && k > 1 && ok) b0 = fminf(b0, anchor_bound2(rec, n, qx, qy, qz, k, a.anchor, visited));
+  if constexpr (ANCHOR > 0) {  // one instantiation per walk form: each keeps its own register allocation
+    if (k > 1 && ok) b0 = fminf(b0, anchor_bound2<ANCHOR>(rec, n, qx, qy, qz, k, visited));
+  }
   if constexpr (KC > 0) {
     RegList<KC> L;
     L.init(b0, k);
@@ -789,7 +792,10 @@ __global__ void __launch_bounds__(kMaxBlock) k_batch_nearest(const __grid_consta
         uint32_t visited = 0;
         const bool go = finite3(qx, qy, qz) && slot >= 0;
         float b0 = __int_as_float(0x7f800000);
-        if (a.anchor && go && k > 1) b0 = anchor_bound2(a.rec, a.n, qx, qy, qz, k, a.anchor, visited, (uint32_t)slot);
+        if (go && k > 1) {
+          if (a.anchor == 1) b0 = anchor_bound2<1>(a.rec, a.n, qx, qy, qz, k, visited, (uint32_t)slot);
+          else if (a.anchor == 2) b0 = anchor_bound2<2>(a.rec, a.n, qx, qy, qz, k, visited, (uint32_t)slot);
+        }
         if constexpr (KC > 0) {
           RegList<KC> L;
           L.init(b0, k);
@@ -1006,20 +1012,22 @@ void launch_scan(const int32_t *counts, uint32_t m, int64_t *offsets, int64_t *t
   k_scan_down<<<tiles, kScanThreads, 0, s>>>(counts, m, tmp, offsets);
 }
 
-template <int KC, bool NBR>
+template <int KC, bool NBR, int ANCHOR>
 static void nearest_kc2(dim3 grid, int block, size_t smem, cudaStream_t s, const NearestArgs &a) {
   if (smem > 48 * 1024) {
-    cudaFuncSetAttribute(k_nearest<KC, NBR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(k_nearest<KC, NBR>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_nearest<KC, NBR, ANCHOR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_nearest<KC, NBR, ANCHOR>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   }
-  k_nearest<KC, NBR><<<grid, block, smem, s>>>(a);
+  k_nearest<KC, NBR, ANCHOR><<<grid, block, smem, s>>>(a);
 }
 
 template <int KC>
 static void nearest_kc(dim3 grid, int block, size_t smem, cudaStream_t s, const NearestArgs &a) {
   prof::Scope ps(s, "nearest");
-  if (a.nbr_bound) nearest_kc2<KC, true>(grid, block, smem, s, a);
-  else nearest_kc2<KC, false>(grid, block, smem, s, a);
+  if (a.nbr_bound) nearest_kc2<KC, true, 0>(grid, block, smem, s, a);  // bounded by finished neighbours
+  else if (a.anchor == 1 && KC != 1) nearest_kc2<KC, false, 1>(grid, block, smem, s, a);
+  else if (a.anchor == 2 && KC != 1) nearest_kc2<KC, false, 2>(grid, block, smem, s, a);
+  else nearest_kc2<KC, false, 0>(grid, block, smem, s, a);
 }
 
 int launch_batch_nearest(const BatchQueryArgs &args, int kc, const TravCfg &cfg, cudaStream_t s) {

@@ -23,7 +23,7 @@ def test_tune_returns_a_valid_configuration_with_the_default_results():
     pd, qd = dev(p), dev(q)
     t = autotune.tune(pd, qd, r, 10, "cube", use_cache=True)
     assert t["block_size"] in autotune.DEFAULT_BLOCKS and t["stack_smem"] in autotune.DEFAULT_STACKS
-    assert t["buffer_size"] in autotune.DEFAULT_BUFFERS
+    assert t["buffer_size"] in autotune.DEFAULT_BUFFERS and t["knn_anchor"] in autotune.DEFAULT_ANCHORS
     assert autotune.tune(pd, qd, r, 10, "cube") == t  # second call: from the cache
     bvh = ab.BVH(pd, block_size=t["block_size"], stack_smem=t["stack_smem"])
     og, ig = bvh.query_spatial(qd, r, buffer_size=t["buffer_size"])
@@ -74,6 +74,7 @@ def test_tune_batch_returns_valid_tiles_with_the_default_results():
     t = autotune.tune_batch(po, qo, ks, P, Q, blocks=(64, 128), stacks=(4, 16))
     assert t["block_size"] in (64, 128) and t["stack_smem"] in (4, 16)
     assert t["queries_per_warp"] in autotune.DEFAULT_QPW and t["knn_heap_from"] in autotune.DEFAULT_HEAP_FROM
+    assert t["knn_anchor"] in autotune.DEFAULT_ANCHORS
     ref = ab.Batch(po, qo, ks)
     o0, i0, d0 = ref.run(P, Q)
     for qpw, hf in ((32, 17), (64, 33), (128, 17), (256, 33)):
