@@ -452,8 +452,10 @@ def run_gpu(args):
     # launch parameters from the autotuner, tuned on another draw of the same distribution
     tuned = {"block_size": 0, "stack_smem": 0, "buffer_size": 0}
     if args.launch:
-        b_, s_, f_ = (int(x) for x in args.launch.split(","))
-        tuned = {"block_size": b_, "stack_smem": s_, "buffer_size": f_, "source": "--launch"}
+        fields = [int(x) for x in args.launch.split(",")]
+        tuned = {"block_size": fields[0], "stack_smem": fields[1], "buffer_size": fields[2], "source": "--launch"}
+        if len(fields) > 3:
+            tuned["knn_anchor"] = fields[3]
     elif not args.no_tune:
         from paper_1908_11807_b300 import autotune
         # a full-size draw: the walk form of the tree bound ranks differently at lower query density
@@ -1043,7 +1045,7 @@ def main():
                     help="comma-separated extra measurements to run (after the headline step)")
     ap.add_argument("--no-tune", action="store_true", help="default launch parameters instead of the autotuner's")
     ap.add_argument("--launch", default=None,
-                    help="block,stack,buffer: fixed traversal launch parameters (skips the autotuner)")
+                    help="block,stack,buffer[,knn_anchor]: fixed traversal launch parameters (skips the autotuner)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "b300":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
