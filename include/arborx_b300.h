@@ -311,7 +311,10 @@ ARBORX_API int arborx_free(arborx_handle h, void *d_ptr, size_t bytes, void *str
 
 /* Nearest query (Sec. 2.2, "Traversal for nearest queries"): for each query, the kk = min(k, n)
  * primitives first in (d^2, index) order, found by a stack traversal that visits the closer
- * child first and skips a node whose box distance exceeds the current k-th candidate.
+ * child first and skips a node whose box distance exceeds the current k-th candidate.  Unless
+ * opts.knn_anchor = 0, the traversal starts from an exact bound on the k-th distance taken from
+ * the tree (a subtree of at least k leaves near the query, see arborx_opts); candidates in a
+ * register list for k below opts.knn_heap_from, else a shared-memory heap.
  *   k           1 <= k <= ARBORX_MAX_K
  *   d_order     NULL or a traversal order from arborx_query_order (as for the spatial count)
  *   d_offsets   NULL or device int64[m + 1]: written with j * kk (CSR view of the rows)
