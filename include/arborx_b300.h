@@ -104,17 +104,24 @@ typedef struct arborx_opts {
                            order (two stable radix sorts over the result entries; results up to
                            ARBORX_MAX_PRIMS entries, else ARBORX_EINVAL); 0 (default): traversal order.
                            The paper leaves row order open (rows are sets). */
-  int32_t knn_anchor;   /* a nearest query with no caller-supplied bound first walks from the root toward
-                           the query through subtrees of at least k leaves and starts its traversal with
-                           the farthest-corner distance of such a box as the k-th-distance bound (exact:
-                           that box holds k primitives), so candidates and stack entries beyond it are
-                           never inserted or pushed.  2 (default): the walk follows the child holding
-                           the query (the 64-Gaussian mixture, 1e7 points and queries, k = 10: 9.25 ms
-                           against 12.33 unbounded; cube 1e7, k = 8: 0.83 against 1.09 ms); 1: it
-                           follows the child with the nearer farthest corner and keeps the smallest
-                           seen (2% faster on the uniform cube at k = 10, slower elsewhere); 0: the
-                           traversal starts unbounded, as in Sec. 2.2.2.  The tuner picks the form per
-                           workload.  Results are identical in every case. */
+  int32_t knn_anchor;   /* a nearest query with no caller-supplied bound starts its traversal from an
+                           exact bound on the k-th distance taken from the tree: the farthest-corner
+                           distance of a subtree box of at least k leaves near the query (that box
+                           holds k primitives), so candidates and stack entries beyond it are never
+                           inserted or kept.  4 (default): the bound is gathered on the traversal's own
+                           first closest-first descent (the smallest corner distance of the children of
+                           k leaves met there, plus a short walk into the sibling where the descent
+                           leaves the last such subtree); the siblings pushed before the bound was known
+                           and lying beyond it are then dropped from the stack; 3: the same without the
+                           sibling walk (cube 1e7, 1e6 queries, k = 10: 1.015 / 1.033 ms against 1.052
+                           for form 1, 1.083 for form 2 and 1.256 unbounded; the 64-Gaussian mixture:
+                           1.066 / 1.078 against 1.382, 1.122 and 1.501).  These two serve k up to 16;
+                           the 32-wide register list and the heap run form 2 in their place.  2: a walk
+                           from the root through the child holding the query, bound from the last box
+                           of k leaves on it; 1: a walk through the child with the nearer farthest
+                           corner, keeping the smallest seen; 0: the traversal starts unbounded, as in
+                           Sec. 2.2.2.  The tuner picks the form per workload.  Results are identical
+                           in every case. */
   int32_t queries_per_warp; /* batched nearest queries (arborx_batch_*): sorted query positions a
                            persistent warp takes from the work queue per fetch, its lanes serving 32 at
                            a time (0 = default 32; else 32, 64, 128 or 256).  The single-tree
@@ -313,7 +320,8 @@ ARBORX_API int arborx_free(arborx_handle h, void *d_ptr, size_t bytes, void *str
  * primitives first in (d^2, index) order, found by a stack traversal that visits the closer
  * child first and skips a node whose box distance exceeds the current k-th candidate.  Unless
  * opts.knn_anchor = 0, the traversal starts from an exact bound on the k-th distance taken from
- * the tree (a subtree of at least k leaves near the query, see arborx_opts); candidates in a
+ * the tree (a subtree of at least k leaves near the query, found on the traversal's first descent
+ * or by a walk before it, see arborx_opts); candidates in a
  * register list for k below opts.knn_heap_from, else a shared-memory heap.
  *   k           1 <= k <= ARBORX_MAX_K
  *   d_order     NULL or a traversal order from arborx_query_order (as for the spatial count)

@@ -498,6 +498,17 @@ struct SmemHeap {
   }
 };
 
+// Per-axis distance to the farther face of [lo, hi]: for every p in the box, |fl(q - p)| is at
+// most this (round-to-nearest subtraction is monotone), so the sum below bounds the FP32 squared
+// distance of every point in the box, computed in the same order.
+__device__ __forceinline__ float far_gap(float q, float lo, float hi) {
+  return fmaxf(fabsf(__fsub_rn(q, lo)), fabsf(__fsub_rn(q, hi)));
+}
+__device__ __forceinline__ float far2_box(float qx, float qy, float qz, float4 lo, float4 hi) {
+  const float gx = far_gap(qx, lo.x, hi.x), gy = far_gap(qy, lo.y, hi.y), gz = far_gap(qz, lo.z, hi.z);
+  return __fadd_rn(__fadd_rn(__fmul_rn(gx, gx), __fmul_rn(gy, gy)), __fmul_rn(gz, gz));
+}
+
 // DEFER > 0: accepted leaf candidates wait in a DEFER-entry register buffer and
 // enter the list when some lane of the warp has a nearly full buffer, all
 // lanes together (and at the end).  Pruning meanwhile uses the list's bound,
@@ -506,7 +517,7 @@ struct SmemHeap {
 // It pays for the shared-memory heap, whose data-dependent sift loop diverges.
 // PACK: stack entries (node, box distance) as one 64-bit word, one shared-memory access per push or
 // pop (faster with the register lists, slower with the heap, whose sift shares the memory pipe).
-template <int DEFER, bool PACK, class List>
+template <int DEFER, bool PACK, bool TB = false, bool REFINE = false, class List>
 __device__ __forceinline__ void knn_traverse(const float4 *__restrict__ rec, uint32_t n, float qx, float qy, float qz, List &L,
                                              int k, unsigned char *s_stack, int stride, int stack_smem,
                                              uint32_t *err, uint32_t &visited, uint32_t root_slot = 0) {
@@ -551,6 +562,113 @@ __device__ __forceinline__ void knn_traverse(const float4 *__restrict__ rec, uin
       if (j < bc && L.accepts(bd[j], bi[j])) L.insert(bd[j], bi[j], k);
     bc = 0;
   };
+  auto push = [&](int far, float fd) {
+    if (sp < stack_smem) {
+      if constexpr (PACK) {
+        s_st[sp * stride] = ((unsigned long long)__float_as_uint(fd) << 32) | (uint32_t)far;
+      } else {
+        s_node[sp * stride] = far;
+        s_dist[sp * stride] = fd;
+      }
+      ++sp;
+    } else if (sp - stack_smem < kSpill) {
+      if constexpr (PACK) {
+        spl[sp - stack_smem] = ((unsigned long long)__float_as_uint(fd) << 32) | (uint32_t)far;
+      } else {
+        spn[sp - stack_smem] = far;
+        spd[sp - stack_smem] = fd;
+      }
+      ++sp;
+    } else {
+      set_err(err, ERR_STACK);  // cannot happen: capacity exceeds the deepest LBVH
+    }
+  };
+  if constexpr (TB) {
+    // The tree's own bound, gathered on the first closest-first descent (the path the traversal
+    // takes first): every child of at least k leaves met there bounds the k-th distance by its
+    // farthest corner (far2_box).  The descent pushes siblings as the traversal does and stops at
+    // the first node with a leaf child or with no child of k leaves; that node is then handled by
+    // the loop below, with the list's bound set to the smallest corner distance seen.  Siblings
+    // pushed before the bound was known and lying beyond it are dropped from the stack (in order,
+    // so the visiting order is unchanged): they would be popped and discarded later, one lane at
+    // a time, and fill the shared part of the stack.
+    auto compact = [&](float bnd) {
+      int j = 0;
+      for (int i = 0; i < sp; ++i) {
+        const bool si = i < stack_smem, sj = j < stack_smem;
+        if constexpr (PACK) {
+          const unsigned long long e = si ? s_st[i * stride] : spl[i - stack_smem];
+          if (__uint_as_float((uint32_t)(e >> 32)) <= bnd) {
+            if (sj) s_st[j * stride] = e;
+            else spl[j - stack_smem] = e;
+            ++j;
+          }
+        } else {
+          const int nd = si ? s_node[i * stride] : spn[i - stack_smem];
+          const float dd = si ? s_dist[i * stride] : spd[i - stack_smem];
+          if (dd <= bnd) {
+            if (sj) {
+              s_node[j * stride] = nd;
+              s_dist[j * stride] = dd;
+            } else {
+              spn[j - stack_smem] = nd;
+              spd[j - stack_smem] = dd;
+            }
+            ++j;
+          }
+        }
+      }
+      sp = j;
+    };
+    float bt = L.bound();
+    if (k > 1) {
+      if (__float_as_int(r1.w) >= k) bt = fminf(bt, far2_box(qx, qy, qz, r0, r1));
+      while ((uint32_t)node < n - 1) {
+        const float4 *rp = rec + 4 + 4 * (uint64_t)node;
+        float4 a0, a1, b0, b1;
+        ld_slot(rp, a0, a1);
+        ld_slot(rp + 2, b0, b1);
+        const int el = __float_as_int(a0.w), er = __float_as_int(b0.w);
+        const bool oka = __float_as_int(a1.w) >= k, okb = __float_as_int(b1.w) >= k;
+        if (oka) bt = fminf(bt, far2_box(qx, qy, qz, a0, a1));
+        if (okb) bt = fminf(bt, far2_box(qx, qy, qz, b0, b1));
+        if (el < 0 || er < 0 || !(oka || okb)) break;
+        const float dl = dist2_box(qx, qy, qz, a0, a1);
+        const float dr = dist2_box(qx, qy, qz, b0, b1);
+        const bool gl = dl <= bt, gr = dr <= bt;
+        if (!gl && !gr) break;
+        ++visited;
+        if (gl && gr) {
+          const bool lfirst = dl <= dr;
+          if (sp >= stack_smem) compact(bt);
+          push(lfirst ? er : el, lfirst ? dr : dl);
+          node = lfirst ? el : er;
+          if (REFINE && !(lfirst ? oka : okb)) {
+            // the descent leaves the last subtree of k leaves on its path: walk on into the
+            // pushed sibling for a tighter corner (nearer-corner child of k leaves at each level)
+            int y = lfirst ? er : el;
+            for (int lv = 0; lv < 64 && (uint32_t)y < n - 1; ++lv) {
+              const float4 *yp = rec + 4 + 4 * (uint64_t)y;
+              float4 c0, c1, d0, d1;
+              ld_slot(yp, c0, c1);
+              ld_slot(yp + 2, d0, d1);
+              ++visited;
+              const bool ok0 = __float_as_int(c1.w) >= k, ok1 = __float_as_int(d1.w) >= k;
+              if (!ok0 && !ok1) break;
+              const float f0 = ok0 ? far2_box(qx, qy, qz, c0, c1) : __int_as_float(0x7f800000);
+              const float f1 = ok1 ? far2_box(qx, qy, qz, d0, d1) : __int_as_float(0x7f800000);
+              bt = fminf(bt, fminf(f0, f1));
+              y = f0 <= f1 ? __float_as_int(c0.w) : __float_as_int(d0.w);
+            }
+          }
+        } else {
+          node = gl ? el : er;
+        }
+      }
+      compact(bt);
+      L.init(bt, k);
+    }
+  }
   while (true) {
     if ((uint32_t)node >= n - 1) {  // corrupt tree: never read outside the records
       set_err(err, ERR_STACK);
@@ -574,27 +692,7 @@ __device__ __forceinline__ void knn_traverse(const float4 *__restrict__ rec, uin
     if (gl && gr) {
       // visit the closer child next, keep the farther one on the stack
       const bool lfirst = dl <= dr;
-      const int far = lfirst ? er : el;
-      const float fd = lfirst ? dr : dl;
-      if (sp < stack_smem) {
-        if constexpr (PACK) {
-          s_st[sp * stride] = ((unsigned long long)__float_as_uint(fd) << 32) | (uint32_t)far;
-        } else {
-          s_node[sp * stride] = far;
-          s_dist[sp * stride] = fd;
-        }
-        ++sp;
-      } else if (sp - stack_smem < kSpill) {
-        if constexpr (PACK) {
-          spl[sp - stack_smem] = ((unsigned long long)__float_as_uint(fd) << 32) | (uint32_t)far;
-        } else {
-          spn[sp - stack_smem] = far;
-          spd[sp - stack_smem] = fd;
-        }
-        ++sp;
-      } else {
-        set_err(err, ERR_STACK);  // cannot happen: capacity exceeds the deepest LBVH
-      }
+      push(lfirst ? er : el, lfirst ? dr : dl);
       node = lfirst ? el : er;
     } else if (gl) {
       node = el;
@@ -626,17 +724,6 @@ __device__ __forceinline__ void knn_traverse(const float4 *__restrict__ rec, uin
   if constexpr (DEFER > 0) flush();
 }
 
-// Per-axis distance to the farther face of [lo, hi]: for every p in the box, |fl(q - p)| is at
-// most this (round-to-nearest subtraction is monotone), so the sum below bounds the FP32 squared
-// distance of every point in the box, computed in the same order.
-__device__ __forceinline__ float far_gap(float q, float lo, float hi) {
-  return fmaxf(fabsf(__fsub_rn(q, lo)), fabsf(__fsub_rn(q, hi)));
-}
-__device__ __forceinline__ float far2_box(float qx, float qy, float qz, float4 lo, float4 hi) {
-  const float gx = far_gap(qx, lo.x, hi.x), gy = far_gap(qy, lo.y, hi.y), gz = far_gap(qz, lo.z, hi.z);
-  return __fadd_rn(__fadd_rn(__fmul_rn(gx, gx), __fmul_rn(gy, gy)), __fmul_rn(gz, gz));
-}
-
 // Exact upper bound on the squared distance to the k-th nearest primitive, taken from the tree
 // before the traversal: a subtree with at least k leaves (the count is the aux word of its child
 // record) holds k primitives no farther than its box's farthest corner, so that distance bounds
@@ -645,11 +732,12 @@ __device__ __forceinline__ float far2_box(float qx, float qy, float qz, float4 l
 // yields it, in one of two forms (mode):
 //   1: descend into the child with the nearer farthest corner and keep the smallest farthest
 //      corner of every child of at least k leaves seen (2% faster on the uniform cube at k = 10);
-//   2 (the default): descend into the child that holds the query (the nearer one when it lies in
-//      neither) and take the farthest corner of the last such child (cheaper, and tighter on
-//      clustered clouds: the 64-Gaussian mixture, k = 10, 11.4 -> 9.25 ms per 1e7 queries).
+//   2: descend into the child that holds the query (the nearer one when it lies in neither) and
+//      take the farthest corner of the last such child (cheaper, and tighter on clustered clouds:
+//      the 64-Gaussian mixture, k = 10, 11.4 -> 9.25 ms per 1e7 queries).
 // With it as the initial bound the traversal inserts and pushes nothing beyond it; results are
-// unchanged.  +inf when the subtree has fewer than k.
+// unchanged.  +inf when the subtree has fewer than k.  The first-descent forms in knn_traverse
+// (TB) gather the same kind of bound without a separate walk.
 template <int mode>
 __device__ __forceinline__ float anchor_bound2(const float4 *__restrict__ rec, uint32_t n, float qx, float qy,
                                                float qz, int k, uint32_t &visited, uint32_t root_slot = 0) {
@@ -740,13 +828,15 @@ __global__ void __launch_bounds__(kMaxBlock) k_nearest(const __grid_constant__ N
   const int64_t row = (int64_t)qi * kk;
   uint32_t visited = 0;
   // the tree's own bound (k = 1 gains nothing: its first leaf already sets the bound)
-  if constexpr (ANCHOR > 0) {  // one instantiation per walk form: each keeps its own register allocation
+  if constexpr (ANCHOR == 1 || ANCHOR == 2) {  // one instantiation per walk form: each keeps its own registers
     if (k > 1 && ok) b0 = fminf(b0, anchor_bound2<ANCHOR>(rec, n, qx, qy, qz, k, visited));
   }
+  constexpr bool kFused = ANCHOR >= 3;  // the bound taken on the traversal's own first descent
+  constexpr bool kRefine = ANCHOR == 4;
   if constexpr (KC > 0) {
     RegList<KC> L;
     L.init(b0, k);
-    if (ok && n > 0) knn_traverse<0, true>(rec, n, qx, qy, qz, L, k, s_raw, B, stack_smem, err, visited);
+    if (ok && n > 0) knn_traverse<0, true, kFused, kRefine>(rec, n, qx, qy, qz, L, k, s_raw, B, stack_smem, err, visited);
     if (a.miss_list) append_flagged(ok && L.bound_idx() == INT_MAX, pos, a.miss_list, a.miss_count);
     L.write(row, kk, out_idx, out_d2);
   } else {
@@ -756,7 +846,8 @@ __global__ void __launch_bounds__(kMaxBlock) k_nearest(const __grid_constant__ N
     H.s = B;
     H.k = k;
     H.init(b0, k);
-    if (ok && n > 0) knn_traverse<kHeapDefer, false>(rec, n, qx, qy, qz, H, k, s_raw, B, stack_smem, err, visited);
+    if (ok && n > 0)
+      knn_traverse<kHeapDefer, false, kFused, kRefine>(rec, n, qx, qy, qz, H, k, s_raw, B, stack_smem, err, visited);
     if (a.miss_list) append_flagged(ok && H.bound_idx() == INT_MAX, pos, a.miss_list, a.miss_count);
     H.write(row, kk, out_idx, out_d2);
   }
@@ -766,8 +857,9 @@ __global__ void __launch_bounds__(kMaxBlock) k_nearest(const __grid_constant__ N
 // Batched clouds: persistent warps take queries_per_warp sorted query positions
 // at a time from an atomic counter, their lanes serving 32 at a time; each query
 // starts at its cloud's subtree root and returns indices local to its cloud.
-// KC = 0: shared-memory heap for k up to kBatchHeapK.
-template <int KC>
+// KC = 0: shared-memory heap for k up to kBatchHeapK.  FD: 0, or the first-descent form (3, 4) of
+// the tree's own bound; with 0 the walk form a.anchor (0, 1, 2) is taken at run time.
+template <int KC, int FD>
 __global__ void __launch_bounds__(kMaxBlock) k_batch_nearest(const __grid_constant__ BatchQueryArgs a) {
   extern __shared__ unsigned char s_raw[];
   const int B = blockDim.x;
@@ -792,16 +884,16 @@ __global__ void __launch_bounds__(kMaxBlock) k_batch_nearest(const __grid_consta
         uint32_t visited = 0;
         const bool go = finite3(qx, qy, qz) && slot >= 0;
         float b0 = __int_as_float(0x7f800000);
-        if (go && k > 1) {
+        if (FD == 0 && go && k > 1) {
           if (a.anchor == 1) b0 = anchor_bound2<1>(a.rec, a.n, qx, qy, qz, k, visited, (uint32_t)slot);
-          else if (a.anchor == 2) b0 = anchor_bound2<2>(a.rec, a.n, qx, qy, qz, k, visited, (uint32_t)slot);
+          else if (a.anchor >= 2) b0 = anchor_bound2<2>(a.rec, a.n, qx, qy, qz, k, visited, (uint32_t)slot);
         }
         if constexpr (KC > 0) {
           RegList<KC> L;
           L.init(b0, k);
           if (go)
-            knn_traverse<0, true>(a.rec, a.n, qx, qy, qz, L, k, s_raw, B, a.stack_smem, a.err, visited,
-                            (uint32_t)slot);
+            knn_traverse<0, true, (FD >= 3), (FD == 4)>(a.rec, a.n, qx, qy, qz, L, k, s_raw, B, a.stack_smem,
+                                                       a.err, visited, (uint32_t)slot);
           L.write(__ldg(a.row_off + qi), kk, a.out_idx, a.out_d2, (int32_t)__ldg(a.prim_base + c));
         } else {
           SmemHeap H;
@@ -1021,13 +1113,30 @@ static void nearest_kc2(dim3 grid, int block, size_t smem, cudaStream_t s, const
   k_nearest<KC, NBR, ANCHOR><<<grid, block, smem, s>>>(a);
 }
 
+// The first-descent forms (3, 4) serve register lists of 2 to 16; the 32-wide list and the heap take
+// the query-path walk (form 2) in their place: measured faster there (cube 1e7, 1e6 queries:
+// k = 32 3.40 against 3.60 ms, k = 50 6.84 against 7.07 ms).
+template <int KC>
+constexpr bool kFirstDescent = KC >= 2 && KC <= 16;
+
 template <int KC>
 static void nearest_kc(dim3 grid, int block, size_t smem, cudaStream_t s, const NearestArgs &a) {
   prof::Scope ps(s, "nearest");
-  if (a.nbr_bound) nearest_kc2<KC, true, 0>(grid, block, smem, s, a);  // bounded by finished neighbours
-  else if (a.anchor == 1 && KC != 1) nearest_kc2<KC, false, 1>(grid, block, smem, s, a);
-  else if (a.anchor == 2 && KC != 1) nearest_kc2<KC, false, 2>(grid, block, smem, s, a);
-  else nearest_kc2<KC, false, 0>(grid, block, smem, s, a);
+  if (a.nbr_bound) {
+    nearest_kc2<KC, true, 0>(grid, block, smem, s, a);  // bounded by finished neighbours
+  } else if (KC == 1 || a.anchor == 0) {
+    nearest_kc2<KC, false, 0>(grid, block, smem, s, a);  // k = 1: its first leaf already sets the bound
+  } else if (a.anchor == 1) {
+    nearest_kc2<KC, false, 1>(grid, block, smem, s, a);
+  } else {
+    if constexpr (kFirstDescent<KC>) {
+      if (a.anchor == 3) nearest_kc2<KC, false, 3>(grid, block, smem, s, a);
+      else if (a.anchor == 4) nearest_kc2<KC, false, 4>(grid, block, smem, s, a);
+      else nearest_kc2<KC, false, 2>(grid, block, smem, s, a);
+    } else {
+      nearest_kc2<KC, false, 2>(grid, block, smem, s, a);
+    }
+  }
 }
 
 int launch_batch_nearest(const BatchQueryArgs &args, int kc, const TravCfg &cfg, cudaStream_t s) {
@@ -1041,8 +1150,8 @@ int launch_batch_nearest(const BatchQueryArgs &args, int kc, const TravCfg &cfg,
     smem += (size_t)2 * kBatchHeapK * block * sizeof(int32_t);
     if (smem > 227 * 1024) return -1;
     if (smem > 48 * 1024) {
-      cudaFuncSetAttribute(k_batch_nearest<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      cudaFuncSetAttribute(k_batch_nearest<0>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      cudaFuncSetAttribute(k_batch_nearest<0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(k_batch_nearest<0, 0>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     }
   }
   int dev = 0, sms = 148, per_sm = 1;
@@ -1053,25 +1162,23 @@ int launch_batch_nearest(const BatchQueryArgs &args, int kc, const TravCfg &cfg,
                      : kc == 4 ? "batch_nearest_k4" : kc == 8 ? "batch_nearest_k8" : kc == 10 ? "batch_nearest_k10"
                      : kc == 16 ? "batch_nearest_k16" : "batch_nearest_k32";
   prof::Scope ps(s, name);
-#define ABX_BATCH(KC)                                                                                  \
-  do {                                                                                                 \
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_nearest<KC>, block, smem);          \
-    const uint32_t need = ceil_div<uint32_t>(a.pos_end - a.pos_begin, (uint32_t)block);                \
-    const uint32_t grid = std::max<uint32_t>(1u, std::min<uint32_t>(need, (uint32_t)(sms * std::max(per_sm, 1)))); \
-    k_batch_nearest<KC><<<grid, block, smem, s>>>(a);                                                   \
-  } while (0)
+  const uint32_t need = ceil_div<uint32_t>(a.pos_end - a.pos_begin, (uint32_t)block);
+  auto go = [&](auto kern) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, smem);
+    const uint32_t grid = std::max<uint32_t>(1u, std::min<uint32_t>(need, (uint32_t)(sms * std::max(per_sm, 1))));
+    kern<<<grid, block, smem, s>>>(a);
+  };
   switch (kc) {
-    case 0: ABX_BATCH(0); break;
-    case 1: ABX_BATCH(1); break;
-    case 2: ABX_BATCH(2); break;
-    case 4: ABX_BATCH(4); break;
-    case 8: ABX_BATCH(8); break;
-    case 10: ABX_BATCH(10); break;
-    case 16: ABX_BATCH(16); break;
-    case 32: ABX_BATCH(32); break;
+    case 0: go(k_batch_nearest<0, 0>); break;
+    case 1: go(k_batch_nearest<1, 0>); break;
+    case 2: a.anchor == 3 ? go(k_batch_nearest<2, 3>) : a.anchor == 4 ? go(k_batch_nearest<2, 4>) : go(k_batch_nearest<2, 0>); break;
+    case 4: a.anchor == 3 ? go(k_batch_nearest<4, 3>) : a.anchor == 4 ? go(k_batch_nearest<4, 4>) : go(k_batch_nearest<4, 0>); break;
+    case 8: a.anchor == 3 ? go(k_batch_nearest<8, 3>) : a.anchor == 4 ? go(k_batch_nearest<8, 4>) : go(k_batch_nearest<8, 0>); break;
+    case 10: a.anchor == 3 ? go(k_batch_nearest<10, 3>) : a.anchor == 4 ? go(k_batch_nearest<10, 4>) : go(k_batch_nearest<10, 0>); break;
+    case 16: a.anchor == 3 ? go(k_batch_nearest<16, 3>) : a.anchor == 4 ? go(k_batch_nearest<16, 4>) : go(k_batch_nearest<16, 0>); break;
+    case 32: go(k_batch_nearest<32, 0>); break;  // a first-descent form runs as the query-path walk here
     default: return -1;
   }
-#undef ABX_BATCH
   return 0;
 }
 

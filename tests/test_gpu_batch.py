@@ -60,6 +60,26 @@ def test_batch_small_matches_per_cloud_oracle(use_graph):
         _check_against_oracle(pts, qs, ks, host(off), host(idx), host(d2), range(len(ks)))
 
 
+@pytest.mark.parametrize("opts", [dict(knn_anchor=0), dict(knn_anchor=1), dict(knn_anchor=3),
+                                  dict(knn_anchor=4, knn_heap_from=33), dict(knn_anchor=3, stack_smem=1),
+                                  dict(knn_anchor=4, queries_per_warp=64)])
+def test_batch_tree_bound_forms_match_per_cloud_oracle(opts):
+    # every form of the tree's own bound, from each cloud's subtree root: the walks, the two
+    # first-descent forms (register lists up to 16; wider classes take the query-path walk) and
+    # the unbounded start; stack_smem 1 sends the first descent's compaction through the local part
+    ab = _ab()
+    sizes = [0, 1, 2, 5, 33, 1000, 2500, 3000, 17, 900, 1, 4096, 0, 700]
+    qsizes = [10, 7, 0, 20, 40, 1000, 500, 3000, 50, 900, 3, 800, 0, 700]
+    ks = [1, 1, 10, 32, 10, 10, 32, 1, 32, 16, 10, 2, 5, 8]
+    pts, qs, po, qo, ks = _make(sizes, qsizes, ks, 6)
+    b = ab.Batch(po, qo, ks, **opts)
+    P = dev(np.concatenate(pts).astype(np.float32))
+    Q = dev(np.concatenate(qs).astype(np.float32))
+    off, idx, d2 = b.run(P, Q, use_graph=False)
+    b.check()
+    _check_against_oracle(pts, qs, ks, host(off), host(idx), host(d2), range(len(ks)))
+
+
 def test_batch_many_clouds_sampled():
     # 512 clouds, sizes log-uniform in [1e3, 1e5], cube / hollow sphere, k in {1, 10, 32}
     ab = _ab()
