@@ -465,7 +465,7 @@ def run_gpu(args):
     # validate=0: the build runs without a host round trip; non-finite input is reported by
     # arborx_check, which runs after every step outside the timed interval
     topts = {"block_size": tuned["block_size"], "stack_smem": tuned["stack_smem"], "validate": 0,
-             "knn_anchor": int(tuned.get("knn_anchor") or 2)}
+             "knn_anchor": int(tuned.get("knn_anchor") or 3)}
     bsz = int(tuned["buffer_size"] or 0)
 
     # one-pass spatial rows go straight into a preallocated buffer (no host round trip inside the
@@ -821,13 +821,15 @@ def learned_extra(ab, dev):
     q_tune = torch.from_numpy(datagen.gaussian_mixture(m, seed, datagen.STREAM_HELDOUT)).to(dev)
     out = {"workload": "gaussian mixture (64 components), n=1e7 points, m=1e7 queries, 1e6 training labels",
            "plain": "the library's default nearest query: its traversal starts from the tree's own bound "
-                    "(knn_anchor = 2, the walk through the child holding the query); also timed: the "
-                    "paper's unbounded start (knn_anchor = 0) and the far-corner walk (knn_anchor = 1)",
+                    "(knn_anchor = 3: gathered on the first descent for k up to 10, the walk through the "
+                    "child holding the query for wider lists); also timed: the paper's unbounded start "
+                    "(knn_anchor = 0), the far-corner walk (1) and the query-path walk (2)",
            "margin_tuned_on": "a held-out draw of 1e7 queries from the same mixture (not the timed set)",
            "unit": "ms per query batch"}
     bvh = ab.BVH(p)
     bvh_paper = ab.BVH(p, knn_anchor=0)
     bvh_far = ab.BVH(p, knn_anchor=1)
+    bvh_path = ab.BVH(p, knn_anchor=2)
     order = bvh.query_order(q)
     for k in (10, 50):
         g = np.random.default_rng(seed)
@@ -852,9 +854,10 @@ def learned_extra(ab, dev):
         exact_ms = _time_ms(lambda: bvh.query_nearest_bounded(q, k, b2, order=order))
         del b2
         # the paper's traversal as published: no initial bound at all (knn_anchor = 0); and the tree
-        # bound's other walk form (knn_anchor = 1, the far-corner walk)
+        # bound's walk forms (knn_anchor = 1, the far-corner walk; 2, the query-path walk)
         paper_ms = _time_ms(lambda: bvh_paper.query_nearest(q, k, order=order))
         far_ms = _time_ms(lambda: bvh_far.query_nearest(q, k, order=order))
+        path_ms = _time_ms(lambda: bvh_path.query_nearest(q, k, order=order))
         out[f"k{k}"] = {"plain_ms": round(plain_ms, 3), "learned_ms": round(learned_ms, 3),
                         "speedup": round(plain_ms / learned_ms, 3), "identical_results": same,
                         "plain_mq_s": round(m / plain_ms / 1e3, 1), "learned_mq_s": round(m / learned_ms / 1e3, 1),
@@ -864,12 +867,15 @@ def learned_extra(ab, dev):
                         "unbounded_start_ms": round(paper_ms, 3),
                         "learned_speedup_over_unbounded_start": round(paper_ms / learned_ms, 3),
                         "far_corner_tree_bound_ms": round(far_ms, 3),
-                        "learned_speedup_over_far_corner_tree_bound": round(far_ms / learned_ms, 3)}
+                        "learned_speedup_over_far_corner_tree_bound": round(far_ms / learned_ms, 3),
+                        "query_path_tree_bound_ms": round(path_ms, 3),
+                        "learned_speedup_over_query_path_tree_bound": round(path_ms / learned_ms, 3)}
         del pi, pd, li, ld
     del q_tune
     bvh.destroy()
     bvh_paper.destroy()
     bvh_far.destroy()
+    bvh_path.destroy()
     return out
 
 

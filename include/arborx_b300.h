@@ -108,20 +108,18 @@ typedef struct arborx_opts {
                            exact bound on the k-th distance taken from the tree: the farthest-corner
                            distance of a subtree box of at least k leaves near the query (that box
                            holds k primitives), so candidates and stack entries beyond it are never
-                           inserted or kept.  4 (default): the bound is gathered on the traversal's own
+                           inserted or kept.  3 (default): the bound is gathered on the traversal's own
                            first closest-first descent (the smallest corner distance of the children of
-                           k leaves met there, plus a short walk into the sibling where the descent
-                           leaves the last such subtree); the siblings pushed before the bound was known
-                           and lying beyond it are then dropped from the stack; 3: the same without the
-                           sibling walk (cube 1e7, 1e6 queries, k = 10: 1.015 / 1.033 ms against 1.052
-                           for form 1, 1.083 for form 2 and 1.256 unbounded; the 64-Gaussian mixture:
-                           1.066 / 1.078 against 1.382, 1.122 and 1.501).  These two serve k up to 16;
-                           the 32-wide register list and the heap run form 2 in their place.  2: a walk
-                           from the root through the child holding the query, bound from the last box
-                           of k leaves on it; 1: a walk through the child with the nearer farthest
-                           corner, keeping the smallest seen; 0: the traversal starts unbounded, as in
-                           Sec. 2.2.2.  The tuner picks the form per workload.  Results are identical
-                           in every case. */
+                           k leaves met there), and the siblings pushed before it was known and lying
+                           beyond it are then dropped from the stack (cube 1e7, 1e6 queries, k = 4:
+                           0.558 ms against 0.597 / 0.614 for forms 2 / 1 and 0.747 unbounded; k = 10:
+                           0.993 against 0.998 / 0.996 and 1.125).  It serves k up to 10; wider register
+                           lists and the heap run form 2 in its place.  2: a walk from the root through
+                           the child holding the query, bound from the last box of k leaves on it (the
+                           64-Gaussian mixture, k = 16: 1.618 against 1.845 for form 1); 1: a walk
+                           through the child with the nearer farthest corner, keeping the smallest seen;
+                           0: the traversal starts unbounded, as in Sec. 2.2.2.  The tuner picks the
+                           form per workload.  Results are identical in every case. */
   int32_t queries_per_warp; /* batched nearest queries (arborx_batch_*): sorted query positions a
                            persistent warp takes from the work queue per fetch, its lanes serving 32 at
                            a time (0 = default 32; else 32, 64, 128 or 256).  The single-tree

@@ -30,7 +30,7 @@ DEFAULT_BLOCKS = (64, 128, 256)
 DEFAULT_STACKS = (4, 8, 16)
 DEFAULT_BUFFERS = (0, 16, 24, 32)
 DEFAULT_MARGINS = (0.0, 0.1, 0.2, 0.35, 0.5, 0.7, 0.9)
-DEFAULT_ANCHORS = (1, 2, 3, 4)  # forms of the nearest query's tree bound (two walks, two first-descent forms)
+DEFAULT_ANCHORS = (1, 2, 3)  # forms of the nearest query's tree bound (two walks, the first descent)
 
 
 def cache_path() -> str:

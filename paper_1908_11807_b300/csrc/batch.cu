@@ -149,7 +149,7 @@ int arborx_batch_create(int64_t n_clouds, const int64_t *h_point_offsets, const 
   else arborx_default_opts(&o);
   if (o.block_size != 0 && (o.block_size < 32 || o.block_size > 256 || o.block_size % 32)) return ARBORX_EINVAL;
   if (o.stack_smem < 0 || o.stack_smem > 64) return ARBORX_EINVAL;
-  if (o.knn_anchor < 0 || o.knn_anchor > 4) return ARBORX_EINVAL;
+  if (o.knn_anchor < 0 || o.knn_anchor > 3) return ARBORX_EINVAL;
   if (o.knn_heap_from != 0 && o.knn_heap_from != 17 && o.knn_heap_from != 33) return ARBORX_EINVAL;
   if (o.queries_per_warp != 0 && o.queries_per_warp != 32 && o.queries_per_warp != 64 &&
       o.queries_per_warp != 128 && o.queries_per_warp != 256)

@@ -168,7 +168,7 @@ bool opts_ok(const arborx_opts &o) {
   if ((o.alloc == nullptr) != (o.free == nullptr)) return false;
   if (o.build_method != ARBORX_BUILD_APETREI && o.build_method != ARBORX_BUILD_KARRAS) return false;
   if (o.sorted_rows != 0 && o.sorted_rows != 1) return false;
-  if (o.knn_anchor < 0 || o.knn_anchor > 4) return false;
+  if (o.knn_anchor < 0 || o.knn_anchor > 3) return false;
   if (o.knn_heap_from != 0 && o.knn_heap_from != 17 && o.knn_heap_from != 33) return false;
   if (o.queries_per_warp != 0 && o.queries_per_warp != 32 && o.queries_per_warp != 64 &&
       o.queries_per_warp != 128 && o.queries_per_warp != 256)
@@ -424,7 +424,7 @@ int arborx_default_opts(arborx_opts *o) {
   o->build_method = ARBORX_BUILD_APETREI;
   o->stats = 0;
   o->sorted_rows = 0;
-  o->knn_anchor = 4;
+  o->knn_anchor = 3;
   o->queries_per_warp = 0;
   o->knn_heap_from = 0;
   return ARBORX_OK;

@@ -115,7 +115,7 @@ struct NearestArgs {
   uint32_t *err;
   int stack_smem;            // set by launch_nearest
   unsigned long long *stats; // set by launch_nearest
-  int anchor;                // 0, or the form (1 to 4) of the tree's own k-th-distance bound
+  int anchor;                // 0, or the form (1 to 3) of the tree's own k-th-distance bound
 };
 int launch_nearest(NearestArgs a, const TravCfg &cfg, cudaStream_t s);
 
@@ -137,7 +137,7 @@ struct BatchQueryArgs {
   float *out_d2;            // nullable
   uint32_t *err;
   int stack_smem;
-  int anchor;                // 0, or the form (1 to 4) of the tree's own k-th-distance bound
+  int anchor;                // 0, or the form (1 to 3) of the tree's own k-th-distance bound
   int queries_per_warp;      // sorted positions a warp takes per queue fetch (multiple of 32)
 };
 int launch_batch_nearest(const BatchQueryArgs &a, int kc, const TravCfg &cfg, cudaStream_t s);

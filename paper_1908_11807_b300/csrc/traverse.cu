@@ -517,7 +517,7 @@ __device__ __forceinline__ float far2_box(float qx, float qy, float qz, float4 l
 // It pays for the shared-memory heap, whose data-dependent sift loop diverges.
 // PACK: stack entries (node, box distance) as one 64-bit word, one shared-memory access per push or
 // pop (faster with the register lists, slower with the heap, whose sift shares the memory pipe).
-template <int DEFER, bool PACK, bool TB = false, bool REFINE = false, class List>
+template <int DEFER, bool PACK, bool TB = false, class List>
 __device__ __forceinline__ void knn_traverse(const float4 *__restrict__ rec, uint32_t n, float qx, float qy, float qz, List &L,
                                              int k, unsigned char *s_stack, int stride, int stack_smem,
                                              uint32_t *err, uint32_t &visited, uint32_t root_slot = 0) {
@@ -643,24 +643,6 @@ __device__ __forceinline__ void knn_traverse(const float4 *__restrict__ rec, uin
           if (sp >= stack_smem) compact(bt);
           push(lfirst ? er : el, lfirst ? dr : dl);
           node = lfirst ? el : er;
-          if (REFINE && !(lfirst ? oka : okb)) {
-            // the descent leaves the last subtree of k leaves on its path: walk on into the
-            // pushed sibling for a tighter corner (nearer-corner child of k leaves at each level)
-            int y = lfirst ? er : el;
-            for (int lv = 0; lv < 64 && (uint32_t)y < n - 1; ++lv) {
-              const float4 *yp = rec + 4 + 4 * (uint64_t)y;
-              float4 c0, c1, d0, d1;
-              ld_slot(yp, c0, c1);
-              ld_slot(yp + 2, d0, d1);
-              ++visited;
-              const bool ok0 = __float_as_int(c1.w) >= k, ok1 = __float_as_int(d1.w) >= k;
-              if (!ok0 && !ok1) break;
-              const float f0 = ok0 ? far2_box(qx, qy, qz, c0, c1) : __int_as_float(0x7f800000);
-              const float f1 = ok1 ? far2_box(qx, qy, qz, d0, d1) : __int_as_float(0x7f800000);
-              bt = fminf(bt, fminf(f0, f1));
-              y = f0 <= f1 ? __float_as_int(c0.w) : __float_as_int(d0.w);
-            }
-          }
         } else {
           node = gl ? el : er;
         }
@@ -797,8 +779,14 @@ __device__ __forceinline__ float neighbour_bound2(const NearestArgs &a, uint32_t
 
 // Threads t <= m also write offsets[t] = t * kk (CSR view of the rows).  Thread
 // t serves sorted position pos = pos_list ? pos_list[t] : t, query qperm[pos].
+// Nearest kernels: block size up to kMaxBlock, one resident block per SM assumed (minBlocks 1), so
+// that the compiler schedules for speed rather than for occupancy: the k-NN traversals use a few
+// more registers (k = 10: 52 against 48) and run faster (cube 1e7, 1e6 queries: k = 10 1.051 ->
+// 0.996 ms, k = 16 1.683 -> 1.545 ms, k = 50 6.84 -> 6.60 ms; the 512-cloud batch 19.9 -> 19.0 ms).
+// The spatial kernels keep the plain bound (mixed: lattice r = 4 faster, two-pass and box queries
+// slower).
 template <int KC, bool NBR, int ANCHOR>
-__global__ void __launch_bounds__(kMaxBlock) k_nearest(const __grid_constant__ NearestArgs a) {
+__global__ void __launch_bounds__(kMaxBlock, 1) k_nearest(const __grid_constant__ NearestArgs a) {
   extern __shared__ unsigned char s_raw[];
   const float4 *__restrict__ rec = a.rec;
   const float *__restrict__ queries = a.queries;
@@ -831,12 +819,11 @@ __global__ void __launch_bounds__(kMaxBlock) k_nearest(const __grid_constant__ N
   if constexpr (ANCHOR == 1 || ANCHOR == 2) {  // one instantiation per walk form: each keeps its own registers
     if (k > 1 && ok) b0 = fminf(b0, anchor_bound2<ANCHOR>(rec, n, qx, qy, qz, k, visited));
   }
-  constexpr bool kFused = ANCHOR >= 3;  // the bound taken on the traversal's own first descent
-  constexpr bool kRefine = ANCHOR == 4;
+  constexpr bool kFused = ANCHOR == 3;  // the bound taken on the traversal's own first descent
   if constexpr (KC > 0) {
     RegList<KC> L;
     L.init(b0, k);
-    if (ok && n > 0) knn_traverse<0, true, kFused, kRefine>(rec, n, qx, qy, qz, L, k, s_raw, B, stack_smem, err, visited);
+    if (ok && n > 0) knn_traverse<0, true, kFused>(rec, n, qx, qy, qz, L, k, s_raw, B, stack_smem, err, visited);
     if (a.miss_list) append_flagged(ok && L.bound_idx() == INT_MAX, pos, a.miss_list, a.miss_count);
     L.write(row, kk, out_idx, out_d2);
   } else {
@@ -847,7 +834,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_nearest(const __grid_constant__ N
     H.k = k;
     H.init(b0, k);
     if (ok && n > 0)
-      knn_traverse<kHeapDefer, false, kFused, kRefine>(rec, n, qx, qy, qz, H, k, s_raw, B, stack_smem, err, visited);
+      knn_traverse<kHeapDefer, false, kFused>(rec, n, qx, qy, qz, H, k, s_raw, B, stack_smem, err, visited);
     if (a.miss_list) append_flagged(ok && H.bound_idx() == INT_MAX, pos, a.miss_list, a.miss_count);
     H.write(row, kk, out_idx, out_d2);
   }
@@ -857,10 +844,11 @@ __global__ void __launch_bounds__(kMaxBlock) k_nearest(const __grid_constant__ N
 // Batched clouds: persistent warps take queries_per_warp sorted query positions
 // at a time from an atomic counter, their lanes serving 32 at a time; each query
 // starts at its cloud's subtree root and returns indices local to its cloud.
-// KC = 0: shared-memory heap for k up to kBatchHeapK.  FD: 0, or the first-descent form (3, 4) of
-// the tree's own bound; with 0 the walk form a.anchor (0, 1, 2) is taken at run time.
+// KC = 0: shared-memory heap for k up to kBatchHeapK.  FD: 0, or the first-descent form (3) of the
+// tree's own bound; with 0 the walk form a.anchor (0, 1, 2; 3 on classes it does not serve) is
+// taken at run time.
 template <int KC, int FD>
-__global__ void __launch_bounds__(kMaxBlock) k_batch_nearest(const __grid_constant__ BatchQueryArgs a) {
+__global__ void __launch_bounds__(kMaxBlock, 1) k_batch_nearest(const __grid_constant__ BatchQueryArgs a) {
   extern __shared__ unsigned char s_raw[];
   const int B = blockDim.x;
   const uint32_t lane = threadIdx.x & 31;
@@ -892,8 +880,8 @@ __global__ void __launch_bounds__(kMaxBlock) k_batch_nearest(const __grid_consta
           RegList<KC> L;
           L.init(b0, k);
           if (go)
-            knn_traverse<0, true, (FD >= 3), (FD == 4)>(a.rec, a.n, qx, qy, qz, L, k, s_raw, B, a.stack_smem,
-                                                       a.err, visited, (uint32_t)slot);
+            knn_traverse<0, true, (FD == 3)>(a.rec, a.n, qx, qy, qz, L, k, s_raw, B, a.stack_smem, a.err,
+                                             visited, (uint32_t)slot);
           L.write(__ldg(a.row_off + qi), kk, a.out_idx, a.out_d2, (int32_t)__ldg(a.prim_base + c));
         } else {
           SmemHeap H;
@@ -1113,11 +1101,11 @@ static void nearest_kc2(dim3 grid, int block, size_t smem, cudaStream_t s, const
   k_nearest<KC, NBR, ANCHOR><<<grid, block, smem, s>>>(a);
 }
 
-// The first-descent forms (3, 4) serve register lists of 2 to 16; the 32-wide list and the heap take
-// the query-path walk (form 2) in their place: measured faster there (cube 1e7, 1e6 queries:
-// k = 32 3.40 against 3.60 ms, k = 50 6.84 against 7.07 ms).
+// The first-descent form (3) serves register lists of 2 to 10; wider lists and the heap take the
+// query-path walk (form 2) in its place, measured as fast or faster there (cube 1e7, 1e6 queries:
+// k = 16 1.546 against 1.557 ms, the 64-Gaussian mixture 1.618 against 1.637 ms).
 template <int KC>
-constexpr bool kFirstDescent = KC >= 2 && KC <= 16;
+constexpr bool kFirstDescent = KC >= 2 && KC <= 10;
 
 template <int KC>
 static void nearest_kc(dim3 grid, int block, size_t smem, cudaStream_t s, const NearestArgs &a) {
@@ -1131,7 +1119,6 @@ static void nearest_kc(dim3 grid, int block, size_t smem, cudaStream_t s, const 
   } else {
     if constexpr (kFirstDescent<KC>) {
       if (a.anchor == 3) nearest_kc2<KC, false, 3>(grid, block, smem, s, a);
-      else if (a.anchor == 4) nearest_kc2<KC, false, 4>(grid, block, smem, s, a);
       else nearest_kc2<KC, false, 2>(grid, block, smem, s, a);
     } else {
       nearest_kc2<KC, false, 2>(grid, block, smem, s, a);
@@ -1171,12 +1158,12 @@ int launch_batch_nearest(const BatchQueryArgs &args, int kc, const TravCfg &cfg,
   switch (kc) {
     case 0: go(k_batch_nearest<0, 0>); break;
     case 1: go(k_batch_nearest<1, 0>); break;
-    case 2: a.anchor == 3 ? go(k_batch_nearest<2, 3>) : a.anchor == 4 ? go(k_batch_nearest<2, 4>) : go(k_batch_nearest<2, 0>); break;
-    case 4: a.anchor == 3 ? go(k_batch_nearest<4, 3>) : a.anchor == 4 ? go(k_batch_nearest<4, 4>) : go(k_batch_nearest<4, 0>); break;
-    case 8: a.anchor == 3 ? go(k_batch_nearest<8, 3>) : a.anchor == 4 ? go(k_batch_nearest<8, 4>) : go(k_batch_nearest<8, 0>); break;
-    case 10: a.anchor == 3 ? go(k_batch_nearest<10, 3>) : a.anchor == 4 ? go(k_batch_nearest<10, 4>) : go(k_batch_nearest<10, 0>); break;
-    case 16: a.anchor == 3 ? go(k_batch_nearest<16, 3>) : a.anchor == 4 ? go(k_batch_nearest<16, 4>) : go(k_batch_nearest<16, 0>); break;
-    case 32: go(k_batch_nearest<32, 0>); break;  // a first-descent form runs as the query-path walk here
+    case 2: a.anchor == 3 ? go(k_batch_nearest<2, 3>) : go(k_batch_nearest<2, 0>); break;
+    case 4: a.anchor == 3 ? go(k_batch_nearest<4, 3>) : go(k_batch_nearest<4, 0>); break;
+    case 8: a.anchor == 3 ? go(k_batch_nearest<8, 3>) : go(k_batch_nearest<8, 0>); break;
+    case 10: a.anchor == 3 ? go(k_batch_nearest<10, 3>) : go(k_batch_nearest<10, 0>); break;
+    case 16: go(k_batch_nearest<16, 0>); break;  // the first-descent form runs as the query-path walk here
+    case 32: go(k_batch_nearest<32, 0>); break;
     default: return -1;
   }
   return 0;

@@ -109,4 +109,4 @@ def test_option_struct_matches_the_header(L):
     assert fields == [f for f, _ in _binding.arborx_opts._fields_]
     o = ab.default_opts()
     assert (o.key_bits, o.sort_queries, o.validate, o.knn_anchor, o.queries_per_warp, o.knn_heap_from) == \
-        (30, 1, 1, 4, 0, 0)
+        (30, 1, 1, 3, 0, 0)

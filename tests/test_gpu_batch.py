@@ -60,12 +60,12 @@ def test_batch_small_matches_per_cloud_oracle(use_graph):
         _check_against_oracle(pts, qs, ks, host(off), host(idx), host(d2), range(len(ks)))
 
 
-@pytest.mark.parametrize("opts", [dict(knn_anchor=0), dict(knn_anchor=1), dict(knn_anchor=3),
-                                  dict(knn_anchor=4, knn_heap_from=33), dict(knn_anchor=3, stack_smem=1),
-                                  dict(knn_anchor=4, queries_per_warp=64)])
+@pytest.mark.parametrize("opts", [dict(knn_anchor=0), dict(knn_anchor=1), dict(knn_anchor=2), dict(knn_anchor=3),
+                                  dict(knn_anchor=3, knn_heap_from=33), dict(knn_anchor=3, stack_smem=1),
+                                  dict(knn_anchor=3, queries_per_warp=64)])
 def test_batch_tree_bound_forms_match_per_cloud_oracle(opts):
-    # every form of the tree's own bound, from each cloud's subtree root: the walks, the two
-    # first-descent forms (register lists up to 16; wider classes take the query-path walk) and
+    # every form of the tree's own bound, from each cloud's subtree root: the walks, the
+    # first-descent form (register lists up to 10; wider classes take the query-path walk) and
     # the unbounded start; stack_smem 1 sends the first descent's compaction through the local part
     ab = _ab()
     sizes = [0, 1, 2, 5, 33, 1000, 2500, 3000, 17, 900, 1, 4096, 0, 700]

@@ -31,7 +31,7 @@ def _case(seed):
     opts = dict(sort_queries=int(g.integers(0, 2)), key_bits=int(g.choice([30, 63])),
                 build_method=int(g.integers(0, 2)), sorted_rows=int(g.integers(0, 2)),
                 block_size=int(g.choice([32, 64, 128, 256])), stack_smem=int(g.choice([0, 1, 4, 16])),
-                knn_anchor=int(g.integers(0, 5)), knn_heap_from=int(g.choice([0, 17, 33])),
+                knn_anchor=int(g.integers(0, 4)), knn_heap_from=int(g.choice([0, 17, 33])),
                 keep_order=int(g.integers(0, 2)))
     r = float(g.choice([0.0, g.uniform(0.01, 0.3), 2.0]))
     k = int(g.choice([1, 5, 10, 16, 17, 27, 40]))
