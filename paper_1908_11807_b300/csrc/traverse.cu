@@ -22,6 +22,7 @@ namespace abx {
 namespace {
 
 constexpr int kSpill = 96;     // local-memory stack entries beyond the shared part
+constexpr int kVec4MinSlots = 80;  // one-pass row buffers from this width write hits 16 bytes at a time
 constexpr int kMaxBlock = 256;  // traversal block size limit (register budget)
 // measured at 1e7 points / 1e6 queries: the heap beats a 32-entry register list from k = 17
 // (k = 32: 5.1 vs 7.9 ms); an 8-entry deferred-insert buffer beats 4 and 16 entries
@@ -138,7 +139,7 @@ __device__ __forceinline__ int child_first(int numbering, int p, int side, int c
   return side == 0 ? c - cnt + 1 : c;
 }
 
-template <int MODE, bool BOX, bool EMIT>
+template <int MODE, bool BOX, bool EMIT, bool VEC>
 __device__ __forceinline__ void spatial_traverse(const SpatialArgs &a) {
   extern __shared__ int32_t s_stack[];
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -153,17 +154,31 @@ __device__ __forceinline__ void spatial_traverse(const SpatialArgs &a) {
   if (MODE == kBuffered) base = (int64_t)qi * a.bs;
   uint32_t cnt = 0;
   uint32_t visited = 0;  // internal nodes loaded (statistics)
+  // VEC (1P rows of at least kVec4MinSlots slots, a multiple of 4, 16-byte aligned buffer): the
+  // newest hits wait in h0..h3 (h3 the newest) and each complete group of four goes out as one
+  // 16-byte store, a quarter of the store transactions of one scalar store per hit
+  constexpr bool vec4 = VEC && MODE == kBuffered;
+  int32_t h0 = 0, h1 = 0, h2 = 0, h3 = 0;
 
-#define ABX_EMIT(v)                                       \
-  do {                                                    \
-    if (MODE == kFill) {                                  \
-      const int64_t pos_ = base + cnt;                    \
-      if (pos_ < a.capacity) a.indices[pos_] = (v);       \
-      else set_err(a.err, ERR_CSR);                       \
-    } else if (MODE == kBuffered) {                       \
-      if (cnt < (uint32_t)a.bs) a.buf[base + cnt] = (v);  \
-    }                                                     \
-    ++cnt;                                                \
+#define ABX_EMIT(v)                                                      \
+  do {                                                                   \
+    if (MODE == kFill) {                                                 \
+      const int64_t pos_ = base + cnt;                                   \
+      if (pos_ < a.capacity) a.indices[pos_] = (v);                      \
+      else set_err(a.err, ERR_CSR);                                      \
+    } else if (MODE == kBuffered) {                                      \
+      if constexpr (vec4) {                                              \
+        h0 = h1;                                                         \
+        h1 = h2;                                                         \
+        h2 = h3;                                                         \
+        h3 = (v);                                                        \
+        if ((cnt & 3u) == 3u && cnt < (uint32_t)a.bs)                    \
+          *reinterpret_cast<int4 *>(a.buf + base + cnt - 3) = make_int4(h0, h1, h2, h3); \
+      } else if (cnt < (uint32_t)a.bs) {                                 \
+        a.buf[base + cnt] = (v);                                         \
+      }                                                                  \
+    }                                                                    \
+    ++cnt;                                                               \
   } while (0)
 
   // every leaf of a subtree inside the query: its slice [first, first + sc) of the sorted order
@@ -275,6 +290,22 @@ __device__ __forceinline__ void spatial_traverse(const SpatialArgs &a) {
     }
   }
 #undef ABX_EMIT
+  if constexpr (vec4) {  // the last, incomplete group of four: h(4-r) .. h3 at slots g .. g + r - 1
+    const uint32_t r = cnt & 3u, g = cnt - r;
+    if (r > 0 && g < (uint32_t)a.bs) {
+      int32_t *o = a.buf + base + g;
+      if (r == 3) {
+        o[0] = h1;
+        o[1] = h2;
+        o[2] = h3;
+      } else if (r == 2) {
+        o[0] = h2;
+        o[1] = h3;
+      } else {
+        o[0] = h3;
+      }
+    }
+  }
   if (MODE != kFill) a.counts[qi] = (int32_t)cnt;
   if (MODE == kBuffered) append_flagged(cnt > (uint32_t)a.bs, qi, a.ovf_list, a.ovf_count);
   if (a.stats) add_stat(a.stats, visited);
@@ -283,14 +314,16 @@ __device__ __forceinline__ void spatial_traverse(const SpatialArgs &a) {
 // Radius queries (points within r) and box queries (boxes met), one kernel name each; EMIT: the
 // variant that takes wholly contained subtrees from the sorted leaf order (more registers, so a
 // separate instantiation that only trees with that query option run).
-template <int MODE, bool EMIT>
+// VEC: the one-pass form with 16-byte hit stores, for wide rows (a separate instantiation: with
+// few hits per row its extra work outweighs the saved stores).
+template <int MODE, bool EMIT, bool VEC = false>
 __global__ void __launch_bounds__(kMaxBlock) k_spatial(const __grid_constant__ SpatialArgs a) {
-  spatial_traverse<MODE, false, EMIT>(a);
+  spatial_traverse<MODE, false, EMIT, VEC>(a);
 }
 
-template <int MODE, bool EMIT>
+template <int MODE, bool EMIT, bool VEC = false>
 __global__ void __launch_bounds__(kMaxBlock) k_intersects(const __grid_constant__ SpatialArgs a) {
-  spatial_traverse<MODE, true, EMIT>(a);
+  spatial_traverse<MODE, true, EMIT, VEC>(a);
 }
 
 // Move buffered rows (those that fit) to their CSR place.  A thread takes
@@ -1002,6 +1035,13 @@ static void spatial_launch(const SpatialArgs &args, bool box, int block, cudaStr
                                                                                      : "intersects_count")
                         : name);
   const bool emit = args.leafperm != nullptr;
+  if constexpr (MODE == kBuffered) {
+    if (args.buf_vec4) {
+      if (box) spatial_launch2(emit ? k_intersects<MODE, true, true> : k_intersects<MODE, false, true>, args, block, smem, s);
+      else spatial_launch2(emit ? k_spatial<MODE, true, true> : k_spatial<MODE, false, true>, args, block, smem, s);
+      return;
+    }
+  }
   if (box) spatial_launch2(emit ? k_intersects<MODE, true> : k_intersects<MODE, false>, args, block, smem, s);
   else spatial_launch2(emit ? k_spatial<MODE, true> : k_spatial<MODE, false>, args, block, smem, s);
 }
@@ -1051,6 +1091,10 @@ void launch_spatial_buffered(const float4 *rec, uint32_t n, const float *queries
   a.counts = counts;
   a.buf = buf;
   a.bs = bs;
+  // 16-byte hit stores pay from about 40 hits per row (cube 1e7, 1e6 queries: mean 80 hits with
+  // 136 slots 2.14 -> 1.90 ms, the lattice r = 4 with 260 slots 6.48 -> 4.90 ms, mean 40 with 72
+  // slots 1.272 / 1.274 ms, mean 10 with 32 slots 0.581 -> 0.642 ms)
+  a.buf_vec4 = bs >= kVec4MinSlots && bs % 4 == 0 && (reinterpret_cast<uintptr_t>(buf) & 15u) == 0;
   a.ovf_list = ovf_list;
   a.ovf_count = ovf_count;
   spatial_launch<kBuffered>(a, box, cfg.block, s, "spatial_buffered");

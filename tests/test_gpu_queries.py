@@ -333,6 +333,39 @@ def test_one_pass_spatial_matches_brute_force(name, bs):
     assert_spatial_equal(host(og), host(ig), oo, io)
 
 
+@pytest.mark.parametrize("bs", [80, 84, 128, 130])
+@pytest.mark.parametrize("emit", [False, True])
+def test_one_pass_wide_rows(bs, emit):
+    # row buffers from 80 slots write hits four at a time (a separate kernel form; 130 is not a
+    # multiple of 4 and keeps one store per hit): rows that fit, that end in a partial group of
+    # 1..3 and that overflow into the second traversal, for radius and box rows, with and without
+    # subtree emission
+    ab = _ab()
+    p = datagen.cube(20_000, 64)
+    q = datagen.cube(1500, 65)
+    r = datagen.radius_for_mean(20_000, "cube") * (100 / 10) ** (1 / 3)  # about 100 hits per row
+    bvh = ab.BVH(dev(p), keep_order=int(emit))
+    if emit:
+        bvh.emit_subtrees(True)
+    qd = dev(q)
+    oo, io = oracle.spatial_brute(p, q, r)
+    counts = np.diff(oo)
+    assert (counts < bs).any() and (counts > bs).any()
+    assert {int(c) % 4 for c in counts[counts < bs]} == {0, 1, 2, 3}
+    og, ig = bvh.query_spatial(qd, r, buffer_size=bs)
+    bvh.check()
+    assert_spatial_equal(host(og), host(ig), oo, io)
+    og, ig = bvh.query_spatial_async(qd, r, buffer_size=bs, capacity=int(oo[-1]))
+    bvh.check()
+    assert_spatial_equal(host(og), host(ig)[:int(host(og)[-1])], oo, io)
+    half = np.float32(0.8 * r)
+    qb = np.concatenate([q - half, q + half], 1).astype(np.float32)
+    ob, ib = oracle.intersects_brute(p, qb)
+    og, ig = bvh.query_intersects(dev(qb), buffer_size=bs)
+    bvh.check()
+    assert_spatial_equal(host(og), host(ig), ob, ib)
+
+
 def test_one_pass_spatial_edge_cases():
     ab = _ab()
     import ctypes

@@ -35,7 +35,7 @@ def _case(seed):
                 keep_order=int(g.integers(0, 2)))
     r = float(g.choice([0.0, g.uniform(0.01, 0.3), 2.0]))
     k = int(g.choice([1, 5, 10, 16, 17, 27, 40]))
-    bs = int(g.choice([1, 4, 16, 32]))
+    bs = int(g.choice([1, 4, 16, 32, 84]))
     half = float(g.uniform(0.0, 0.2))
     return p.astype(np.float32), q, opts, r, k, bs, half
 
