@@ -117,6 +117,7 @@ struct NearestArgs {
   int stack_smem;            // set by launch_nearest
   unsigned long long *stats; // set by launch_nearest
   int anchor;                // 0, or the form (1 to 3) of the tree's own k-th-distance bound
+  int out_pairs;             // set by launch_nearest: both outputs 8-byte aligned (rows in pair stores)
 };
 int launch_nearest(NearestArgs a, const TravCfg &cfg, cudaStream_t s);
 

@@ -453,7 +453,24 @@ struct RegList {
     if (c < key[0]) key[0] = c;
   }
   __device__ __forceinline__ void write(int64_t row, int kk, int32_t *out_idx, float *out_d2,
-                                        int32_t base = 0) const {
+                                        int32_t base = 0, bool pairs = false) const {
+    if constexpr (KC % 2 == 0) {
+      // a full-width list (k = KC, so no filler slots) into 8-byte aligned rows: two entries per
+      // store, half the store transactions (the scalar row stores cost 45 of 996 us at k = 10)
+      if (pairs && off == 0 && kk == KC) {
+#pragma unroll
+        for (int j = 0; j < KC; j += 2) {
+          const int32_t i0 = (int32_t)(uint32_t)key[j], i1 = (int32_t)(uint32_t)key[j + 1];
+          const bool r0 = i0 != INT_MAX, r1 = i1 != INT_MAX;
+          *reinterpret_cast<int2 *>(out_idx + row + j) = make_int2(r0 ? i0 - base : -1, r1 ? i1 - base : -1);
+          if (out_d2)
+            *reinterpret_cast<float2 *>(out_d2 + row + j) =
+                make_float2(r0 ? __uint_as_float((uint32_t)(key[j] >> 32)) : __int_as_float(0x7f800000),
+                            r1 ? __uint_as_float((uint32_t)(key[j + 1] >> 32)) : __int_as_float(0x7f800000));
+        }
+        return;
+      }
+    }
 #pragma unroll
     for (int j = 0; j < KC; ++j) {
       const int o = j - off;
@@ -858,7 +875,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_nearest(const __grid_constant_
     L.init(b0, k);
     if (ok && n > 0) knn_traverse<0, true, kFused>(rec, n, qx, qy, qz, L, k, s_raw, B, stack_smem, err, visited);
     if (a.miss_list) append_flagged(ok && L.bound_idx() == INT_MAX, pos, a.miss_list, a.miss_count);
-    L.write(row, kk, out_idx, out_d2);
+    L.write(row, kk, out_idx, out_d2, 0, a.out_pairs != 0);
   } else {
     SmemHeap H;
     H.hd = reinterpret_cast<float *>(s_raw) + (size_t)2 * stack_smem * B + threadIdx.x;
@@ -1216,6 +1233,8 @@ int launch_batch_nearest(const BatchQueryArgs &args, int kc, const TravCfg &cfg,
 int launch_nearest(NearestArgs a, const TravCfg &cfg, cudaStream_t s) {
   a.kk = (int)std::min<int64_t>(a.k, a.n);
   a.stats = cfg.stats_nodes;
+  a.out_pairs = (reinterpret_cast<uintptr_t>(a.out_idx) & 7u) == 0 &&
+                (a.out_d2 == nullptr || (reinterpret_cast<uintptr_t>(a.out_d2) & 7u) == 0);
   const int k = a.k;
   const uint32_t threads = a.m + 1;
   int block = cfg.block;

@@ -61,6 +61,34 @@ def test_nearest_matches_brute_force(name, k):
     assert_nearest_equal(host(ig), host(dg), io, do)
 
 
+@pytest.mark.parametrize("k", [2, 10, 16])
+@pytest.mark.parametrize("shift", [(0, 0), (1, 0), (0, 1), (1, 1)])
+def test_nearest_rows_into_unaligned_buffers(k, shift):
+    # full-width rows go out two entries per store into 8-byte aligned outputs; caller buffers
+    # that start 4 bytes off take the one-entry stores (the C interface, with offset pointers)
+    ab = _ab()
+    import ctypes
+    import torch
+    p, q = datagen.workload("cube", 3000, 700, 24)
+    bvh = ab.BVH(dev(p))
+    m = len(q)
+    io, do = oracle.nearest_brute(p, q, k)
+    idx = torch.full((m * k + 2,), 7, dtype=torch.int32, device="cuda")
+    d2 = torch.full((m * k + 2,), 7.0, dtype=torch.float32, device="cuda")
+    qd = dev(q)
+    st = ab.lib().arborx_query_nearest(bvh.handle, ctypes.c_void_p(qd.data_ptr()), m, k, None, None, None,
+                                       ctypes.c_void_p(idx.data_ptr() + 4 * shift[0]),
+                                       ctypes.c_void_p(d2.data_ptr() + 4 * shift[1]))
+    assert st == 0
+    torch.cuda.synchronize()
+    bvh.check()
+    gi = host(idx)[shift[0]:shift[0] + m * k].reshape(m, k)
+    gd = host(d2)[shift[1]:shift[1] + m * k].reshape(m, k)
+    assert_nearest_equal(gi, gd, io, do)
+    assert host(idx)[shift[0] + m * k] == 7 and (shift[0] == 0 or host(idx)[0] == 7)  # nothing outside
+    assert host(d2)[shift[1] + m * k] == 7.0 and (shift[1] == 0 or host(d2)[0] == 7.0)
+
+
 @pytest.mark.parametrize("k", [2, 3, 4, 5, 8, 9, 16, 17, 31, 32, 33, 64, 100, 256, 512])
 def test_nearest_every_list_width(k):
     ab = _ab()
