@@ -57,7 +57,7 @@ struct SpatialArgs {
   int64_t capacity;
   int32_t *buf;  // 1P row buffers [m][bs]
   int bs;
-  int buf_vec4;  // 1: a wide row buffer (bs a multiple of 4, buf 16-byte aligned): 16-byte hit stores
+  int buf_vec4;  // 1: bs a multiple of 4 and buf 16-byte aligned: hits go out in 16-byte stores
   uint32_t *ovf_list;  // 1P queries with more than bs results
   uint32_t *ovf_count;
   const uint32_t *m_dev;  // nullable: device-side query count

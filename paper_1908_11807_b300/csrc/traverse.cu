@@ -22,7 +22,6 @@ namespace abx {
 namespace {
 
 constexpr int kSpill = 96;     // local-memory stack entries beyond the shared part
-constexpr int kVec4MinSlots = 80;  // one-pass row buffers from this width write hits 16 bytes at a time
 constexpr int kMaxBlock = 256;  // traversal block size limit (register budget)
 // measured at 1e7 points / 1e6 queries: the heap beats a 32-entry register list from k = 17
 // (k = 32: 5.1 vs 7.9 ms); an 8-entry deferred-insert buffer beats 4 and 16 entries
@@ -154,9 +153,9 @@ __device__ __forceinline__ void spatial_traverse(const SpatialArgs &a) {
   if (MODE == kBuffered) base = (int64_t)qi * a.bs;
   uint32_t cnt = 0;
   uint32_t visited = 0;  // internal nodes loaded (statistics)
-  // VEC (1P rows of at least kVec4MinSlots slots, a multiple of 4, 16-byte aligned buffer): the
-  // newest hits wait in h0..h3 (h3 the newest) and each complete group of four goes out as one
-  // 16-byte store, a quarter of the store transactions of one scalar store per hit
+  // VEC (1P rows whose width is a multiple of 4, 16-byte aligned buffer): the newest hits wait in
+  // h0..h3 (h3 the newest) and each complete group of four goes out as one 16-byte store, a
+  // quarter of the store transactions of one scalar store per hit
   constexpr bool vec4 = VEC && MODE == kBuffered;
   int32_t h0 = 0, h1 = 0, h2 = 0, h3 = 0;
 
@@ -314,8 +313,8 @@ __device__ __forceinline__ void spatial_traverse(const SpatialArgs &a) {
 // Radius queries (points within r) and box queries (boxes met), one kernel name each; EMIT: the
 // variant that takes wholly contained subtrees from the sorted leaf order (more registers, so a
 // separate instantiation that only trees with that query option run).
-// VEC: the one-pass form with 16-byte hit stores, for wide rows (a separate instantiation: with
-// few hits per row its extra work outweighs the saved stores).
+// VEC: the one-pass form with 16-byte hit stores (a separate instantiation: the same code behind
+// a run-time flag in one kernel was slower at 10 hits per row, 0.581 -> 0.642 ms).
 template <int MODE, bool EMIT, bool VEC = false>
 __global__ void __launch_bounds__(kMaxBlock) k_spatial(const __grid_constant__ SpatialArgs a) {
   spatial_traverse<MODE, false, EMIT, VEC>(a);
@@ -1108,10 +1107,10 @@ void launch_spatial_buffered(const float4 *rec, uint32_t n, const float *queries
   a.counts = counts;
   a.buf = buf;
   a.bs = bs;
-  // 16-byte hit stores pay from about 40 hits per row (cube 1e7, 1e6 queries: mean 80 hits with
-  // 136 slots 2.14 -> 1.90 ms, the lattice r = 4 with 260 slots 6.48 -> 4.90 ms, mean 40 with 72
-  // slots 1.272 / 1.274 ms, mean 10 with 32 slots 0.581 -> 0.642 ms)
-  a.buf_vec4 = bs >= kVec4MinSlots && bs % 4 == 0 && (reinterpret_cast<uintptr_t>(buf) & 15u) == 0;
+  // 16-byte hit stores (cube 1e7, 1e6 queries: mean 10 hits with 32 slots 0.579 -> 0.577 ms, 20
+  // with 40 0.875 -> 0.853, 40 with 72 1.266 -> 1.195, 80 with 136 2.141 -> 1.79; the lattice
+  // r = 4 with 260 slots 6.54 -> 4.53 ms)
+  a.buf_vec4 = bs % 4 == 0 && (reinterpret_cast<uintptr_t>(buf) & 15u) == 0;
   a.ovf_list = ovf_list;
   a.ovf_count = ovf_count;
   spatial_launch<kBuffered>(a, box, cfg.block, s, "spatial_buffered");

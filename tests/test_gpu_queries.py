@@ -364,9 +364,9 @@ def test_one_pass_spatial_matches_brute_force(name, bs):
 @pytest.mark.parametrize("bs", [80, 84, 128, 130])
 @pytest.mark.parametrize("emit", [False, True])
 def test_one_pass_wide_rows(bs, emit):
-    # row buffers from 80 slots write hits four at a time (a separate kernel form; 130 is not a
-    # multiple of 4 and keeps one store per hit): rows that fit, that end in a partial group of
-    # 1..3 and that overflow into the second traversal, for radius and box rows, with and without
+    # row buffers whose width is a multiple of 4 write hits four at a time (a separate kernel
+    # form; 130 keeps one store per hit): wide rows that fit, that end in a partial group of 1..3
+    # and that overflow into the second traversal, for radius and box rows, with and without
     # subtree emission
     ab = _ab()
     p = datagen.cube(20_000, 64)
