@@ -13,6 +13,7 @@
 #include <climits>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "kernels.cuh"
 #include "prof.cuh"
@@ -567,8 +568,8 @@ __device__ __forceinline__ float far2_box(float qx, float qy, float qz, float4 l
 // PACK: stack entries (node, box distance) as one 64-bit word, one shared-memory access per push or
 // pop (faster with the register lists, slower with the heap, whose sift shares the memory pipe).
 template <int DEFER, bool PACK, bool TB = false, class List>
-__device__ __forceinline__ void knn_traverse(const float4 *__restrict__ rec, uint32_t n, float qx, float qy, float qz, List &L,
-                                             int k, unsigned char *s_stack, int stride, int stack_smem,
+__device__ __forceinline__ void knn_traverse(const float4 *__restrict__ rec, uint32_t n, float qx, float qy, float qz,
+                                             List &L, int k, unsigned char *s_stack, int stride, int stack_smem,
                                              uint32_t *err, uint32_t &visited, uint32_t root_slot = 0) {
   const float4 r0 = __ldg(rec + 2 * (uint64_t)root_slot), r1 = __ldg(rec + 2 * (uint64_t)root_slot + 1);
   const int e0 = __float_as_int(r0.w);
@@ -1051,15 +1052,18 @@ static void spatial_launch(const SpatialArgs &args, bool box, int block, cudaStr
                                                                                      : "intersects_count")
                         : name);
   const bool emit = args.leafperm != nullptr;
+  auto go = [&](auto vec) {  // vec: std::integral_constant<bool, ...>, the 16-byte hit-store form
+    constexpr bool V = decltype(vec)::value;
+    if (box) spatial_launch2(emit ? k_intersects<MODE, true, V> : k_intersects<MODE, false, V>, args, block, smem, s);
+    else spatial_launch2(emit ? k_spatial<MODE, true, V> : k_spatial<MODE, false, V>, args, block, smem, s);
+  };
   if constexpr (MODE == kBuffered) {
     if (args.buf_vec4) {
-      if (box) spatial_launch2(emit ? k_intersects<MODE, true, true> : k_intersects<MODE, false, true>, args, block, smem, s);
-      else spatial_launch2(emit ? k_spatial<MODE, true, true> : k_spatial<MODE, false, true>, args, block, smem, s);
+      go(std::true_type{});
       return;
     }
   }
-  if (box) spatial_launch2(emit ? k_intersects<MODE, true> : k_intersects<MODE, false>, args, block, smem, s);
-  else spatial_launch2(emit ? k_spatial<MODE, true> : k_spatial<MODE, false>, args, block, smem, s);
+  go(std::false_type{});
 }
 
 static SpatialArgs spatial_args(const float4 *rec, uint32_t n, const float *queries, const uint32_t *qperm, uint32_t m,
