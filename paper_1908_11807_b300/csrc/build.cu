@@ -139,6 +139,43 @@ __device__ __forceinline__ uint64_t morton<uint64_t>(float cx, float cy, float c
          spread21(quantise<21>(cz, sc[2], sc[5]));
 }
 
+// 10-bit quantisation without the division in the common case.  rs = fl(2^10 * fl(1 / ext)) for a
+// normal extent ext well inside the float range (NaN otherwise, which sends every call to the
+// exact form).  Then f = fl(x * rs) = 2^10 * fl(x * fl(1 / ext)), and against the exact
+// u = fl(x / ext) two roundings of relative size 2^-24 each separate them from x / ext on one side
+// and one on the other: |f - 2^10 u| <= 2^10 (x / ext) 1.5 * 2^-23 <= 1.9e-4 for f <= 2^10.  When
+// f lies at least kQuantEps (2^-11, 2.6 times that bound) inside an open cell (c, c + 1) with
+// 0 <= c <= 1023, 2^10 u lies in the same cell, u is inside (0, 1) so neither clamp applies, and
+// floor(2^10 u) = c: the exact result.  Anything else (a cell edge within the margin, outside
+// the box, a flat axis, NaN) takes quantise<10>.
+constexpr float kQuantEps = 0x1p-11f;
+
+__device__ __forceinline__ float quant_scale10(float L, float H) {
+  const float ext = __fsub_rn(H, L);
+  return (ext >= 0x1p-116f && ext <= 0x1p116f) ? __fmul_rn(__frcp_rn(ext), 1024.0f) : __int_as_float(0x7fffffff);
+}
+
+__device__ __forceinline__ uint32_t quantise10_fast(float c, float L, float H, float rs) {
+  const float f = __fmul_rn(__fsub_rn(c, L), rs);
+  const float cell = floorf(f);
+  const float fr = __fsub_rn(f, cell);
+  if (fr >= kQuantEps && fr <= 1.0f - kQuantEps && cell >= 0.0f && cell <= 1023.0f) return (uint32_t)cell;
+  return quantise<10>(c, L, H);
+}
+
+__device__ __forceinline__ uint32_t morton_fast10(float cx, float cy, float cz, const float *sc, const float *rs) {
+  return (spread10(quantise10_fast(cx, sc[0], sc[3], rs[0])) << 2) |
+         (spread10(quantise10_fast(cy, sc[1], sc[4], rs[1])) << 1) | spread10(quantise10_fast(cz, sc[2], sc[5], rs[2]));
+}
+
+// 30-bit codes take the division-free form; 63-bit codes (21 bits per axis, where the margin
+// would exceed the cell) the exact one
+template <typename K>
+__device__ __forceinline__ K morton_block(float cx, float cy, float cz, const float *sc, const float *rs) {
+  if constexpr (sizeof(K) == 4) return morton_fast10(cx, cy, cz, sc, rs);
+  else return morton<K>(cx, cy, cz, sc);
+}
+
 template <typename K>
 __device__ __forceinline__ void hist_add(uint32_t (*s_h)[kRadix], int passes, K code) {
   for (int p = 0; p < passes; ++p) atomicAdd(&s_h[p][(uint32_t)(code >> (p * kRadixBits)) & (kRadix - 1)], 1u);
@@ -158,9 +195,11 @@ __global__ void __launch_bounds__(256) k_morton(const float *__restrict__ prims,
   if (threadIdx.x < 6) s_sc[threadIdx.x] = ord2f(meta->bounds_ord[threadIdx.x]);
   __syncthreads();
   if (write_scene && blockIdx.x == 0 && threadIdx.x < 6) meta->scene[threadIdx.x] = s_sc[threadIdx.x];
-  float sc[6];
+  float sc[6], rs[3];
 #pragma unroll
   for (int a = 0; a < 6; ++a) sc[a] = s_sc[a];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) rs[a] = quant_scale10(sc[a], sc[3 + a]);
 
   constexpr int PER = KIND == 0 ? 3 : 6;  // floats per primitive
   constexpr int GP = 12 / PER;            // primitives per 3-float4 group
@@ -183,7 +222,7 @@ __global__ void __launch_bounds__(256) k_morton(const float *__restrict__ prims,
         cy = __fmul_rn(__fadd_rn(v[6 * j + 1], v[6 * j + 4]), 0.5f);
         cz = __fmul_rn(__fadd_rn(v[6 * j + 2], v[6 * j + 5]), 0.5f);
       }
-      out[j] = morton<K>(cx, cy, cz, sc) >> drop;
+      out[j] = morton_block<K>(cx, cy, cz, sc, rs) >> drop;
       hist_add<K>(s_h, passes, out[j]);
     }
 #pragma unroll
@@ -199,7 +238,7 @@ __global__ void __launch_bounds__(256) k_morton(const float *__restrict__ prims,
       cy = __fmul_rn(__fadd_rn(p[1], p[4]), 0.5f);
       cz = __fmul_rn(__fadd_rn(p[2], p[5]), 0.5f);
     }
-    const K code = morton<K>(cx, cy, cz, sc) >> drop;
+    const K code = morton_block<K>(cx, cy, cz, sc, rs) >> drop;
     codes[i] = code;
     hist_add<K>(s_h, passes, code);
   }

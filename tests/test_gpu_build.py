@@ -17,7 +17,38 @@ def _ab():
     return ab
 
 
+def _cell_edges(n: int, seed: int) -> np.ndarray:
+    """Points on and within a few ulps of the 10-bit Morton cell edges L + j (H - L) / 1024 of
+    a scene box with extents 1, 3 and fl(0.7) (reciprocals inexact for the last two), and at
+    fractions of a cell on both sides of the division-free form's acceptance margin, plus the
+    box's two corners, which fix the scene box.  Coordinates near an edge must take the exact
+    division and the others the multiply; either way the codes must equal the oracle's."""
+    rng = np.random.default_rng(seed)
+    lo = np.array([0.0, -1.25, 0.1], np.float32)
+    hi = np.array([1.0, 1.75, np.float32(0.1) + np.float32(0.7)], np.float32)
+    cols = []
+    for a in range(3):
+        ext = np.float64(hi[a]) - np.float64(lo[a])
+        edges = (np.float64(lo[a]) + np.arange(1025) * ext / 1024).astype(np.float32)
+        vals = [edges]
+        # inside the cells: on both sides of the division-free form's 2^-11 acceptance margin
+        for frac in (2.0 ** -12, 2.0 ** -11, 1.5 * 2.0 ** -11, 2.0 ** -10, 0.5, 1 - 2.0 ** -10, 1 - 1.5 * 2.0 ** -11,
+                     1 - 2.0 ** -11, 1 - 2.0 ** -12):
+            vals.append((np.float64(lo[a]) + (np.arange(1024) + frac) * ext / 1024).astype(np.float32))
+        for s in (1, 2, 3):
+            up, dn = edges.copy(), edges.copy()
+            for _ in range(s):
+                up = np.nextafter(up, np.float32(np.inf))
+                dn = np.nextafter(dn, np.float32(-np.inf))
+            vals += [up, dn]
+        v = np.clip(np.concatenate(vals), lo[a], hi[a]).astype(np.float32)
+        cols.append(rng.choice(v, n))
+    pts = np.stack(cols, 1).astype(np.float32)
+    return np.concatenate([pts, lo[None], hi[None]]).astype(np.float32)
+
+
 CLOUDS = {
+    "cell_edges": lambda: _cell_edges(20_000, 17),
     "cube_1e4": lambda: datagen.cube(10_000, datagen.SEED0 + 1),
     "hollow_sphere_2e4": lambda: datagen.hollow_sphere(20_000, datagen.SEED0 + 2),
     "gaussian_3e4": lambda: datagen.gaussian_mixture(30_000, datagen.SEED0 + 5),
@@ -163,10 +194,15 @@ def test_apetrei_and_karras_build_the_same_tree(n):
     assert trees[0][1] == trees[1][1]
 
 
-def test_query_order_is_stable_morton_order():
+@pytest.mark.parametrize("cloud", ["cube", "cell_edges"])
+def test_query_order_is_stable_morton_order(cloud):
     ab = _ab()
-    p = datagen.cube(20_000, 78)
-    q = np.concatenate([datagen.cube(5000, 79) * 1.2 - 0.1, p[:100]]).astype(np.float32)  # some outside
+    if cloud == "cube":
+        p = datagen.cube(20_000, 78)
+        q = np.concatenate([datagen.cube(5000, 79) * 1.2 - 0.1, p[:100]]).astype(np.float32)  # some outside
+    else:
+        p = _cell_edges(20_000, 78)
+        q = np.concatenate([_cell_edges(20_000, 79), _cell_edges(2000, 80) * 1.1 - 0.05]).astype(np.float32)
     bvh = ab.BVH(dev(p))
     order = host(bvh.query_order(dev(q))).astype(np.int64)
     sb, _ = oracle.scene_box(p)
