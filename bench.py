@@ -244,6 +244,7 @@ def kernel_bytes(name, n, m, k, nnz, nodes):
         "spatial_fill": 28 * m + 4 * nnz + 64 * nodes.get("spatial", 0) // 2,
         "spatial_buffered": 20 * m + 4 * nnz + 64 * nodes.get("spatial", 0),  # one pass, rows to the buffer
         "compact": 8 * nnz + 12 * m,                                           # buffer -> CSR
+        "scan_compact": 8 * nnz + 12 * m,  # counts read, offsets written, rows buffer -> CSR (one kernel)
         "nearest": m * (16 + 8 * k + 8) + 64 * nodes.get("nearest", 0),
     }
     return table.get(name)

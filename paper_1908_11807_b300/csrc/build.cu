@@ -93,6 +93,25 @@ __global__ void k_init_meta(DevMeta *meta) {
   else if (t >= 16 && t < 18) meta->queries[t - 16] = 0ull;
 }
 
+// k_init_meta over block 0 and, over the whole grid, zero `words` 16-byte words at `zero` (the
+// build's counters and sort workspace), in one launch
+__global__ void __launch_bounds__(256) k_init_meta_zero(DevMeta *meta, uint4 *__restrict__ zero, uint64_t words) {
+  if (blockIdx.x == 0 && threadIdx.x < 32) {
+    const int t = threadIdx.x;
+    if (t < 3) meta->bounds_ord[t] = 0xffffffffu;
+    else if (t < 6) meta->bounds_ord[t] = 0u;
+    else if (t == 6) meta->nonfinite = 0;
+    else if (t == 7) meta->err = 0;
+    else if (t >= 8 && t < 11) meta->scene[t - 8] = __int_as_float(0x7f800000);
+    else if (t >= 11 && t < 14) meta->scene[t - 8] = __int_as_float(0xff800000);
+    else if (t >= 14 && t < 16) meta->nodes[t - 14] = 0ull;
+    else if (t >= 16 && t < 18) meta->queries[t - 16] = 0ull;
+  }
+  const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += (uint64_t)gridDim.x * blockDim.x)
+    zero[i] = z;
+}
+
 // ------------------------------------------------------------ Morton codes
 
 template <int BITS>
@@ -772,6 +791,13 @@ void launch_iota_on_timeout(uint32_t *order, uint32_t m, const uint32_t *err, cu
 }
 
 void launch_init_meta(DevMeta *meta, cudaStream_t s) { k_init_meta<<<1, 32, 0, s>>>(meta); }
+
+void launch_init_meta_zero(DevMeta *meta, void *zero, size_t bytes, cudaStream_t s) {
+  const uint64_t words = bytes / 16;  // bytes: a multiple of 16 at a 16-byte aligned address
+  const uint32_t blocks =
+      (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(ceil_div<uint64_t>(words, 256), (uint64_t)sm_count() * 4));
+  k_init_meta_zero<<<blocks, 256, 0, s>>>(meta, static_cast<uint4 *>(zero), words);
+}
 
 void launch_bounds(const float *prims, int64_t n, int kind, DevMeta *meta, cudaStream_t s) {
   const uint64_t nf = (uint64_t)n * (kind == 0 ? 3 : 6);

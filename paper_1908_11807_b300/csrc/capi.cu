@@ -211,22 +211,11 @@ int build_work(arborx_bvh_s *h, const float *d_prims, cudaStream_t s, void *scra
   const int key_bits = h->opts.key_bits;
   const int passes = sort_passes(key_bits);
   const int64_t n_int = n > 0 ? n - 1 : 0;
-  launch_init_meta(h->meta, s);
   if (n == 0) {
+    launch_init_meta(h->meta, s);
     // empty tree: the root record must still be readable; mark it empty by n == 0
     cudaMemsetAsync(h->rec, 0, 2 * sizeof(float4), s);
     return launch_status();
-  }
-  launch_bounds(d_prims, n, h->kind, h->meta, s);
-  int st = launch_status();
-  if (st) return st;
-  if (h->opts.validate) {
-    uint32_t nonfinite = 0;
-    if (cudaMemcpyAsync(&nonfinite, &h->meta->nonfinite, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) !=
-            cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
-      return ARBORX_ECUDA;
-    if (nonfinite) return ARBORX_EINVAL;
   }
 
   const bool karras = h->opts.build_method == ARBORX_BUILD_KARRAS;
@@ -238,7 +227,10 @@ int build_work(arborx_bvh_s *h, const float *d_prims, cudaStream_t s, void *scra
   const size_t scratch_bytes = build_scratch_bytes<K>(h);
   const bool own = scratch == nullptr;
   if (own) scratch = dev_alloc(h->opts, scratch_bytes, s);
-  if (!scratch) return ARBORX_ENOMEM;
+  if (!scratch) {
+    launch_init_meta(h->meta, s);  // the handle's error word and statistics start clean all the same
+    return ARBORX_ENOMEM;
+  }
   Carver c(scratch);
   K *kA = c.take<K>(n);
   K *kB = c.take<K>(n);
@@ -249,8 +241,23 @@ int build_work(arborx_bvh_s *h, const float *d_prims, cudaStream_t s, void *scra
   char *zero_base = c.base + c.off;
   uint32_t *arrival = c.take<uint32_t>(arrival_words);
   uint32_t *wsbase = c.take<uint32_t>(ws_words);
-  cudaMemsetAsync(zero_base, 0, zero_bytes, s);
+  launch_init_meta_zero(h->meta, zero_base, zero_bytes, s);  // the tree's meta block and the zeroed scratch
   if (karras) cudaMemsetAsync(links, 0xff, link_words * sizeof(int32_t), s);  // unset links read as -1
+  launch_bounds(d_prims, n, h->kind, h->meta, s);
+  int st = launch_status();
+  if (!st && h->opts.validate) {
+    uint32_t nonfinite = 0;
+    if (cudaMemcpyAsync(&nonfinite, &h->meta->nonfinite, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      st = ARBORX_ECUDA;
+    else if (nonfinite)
+      st = ARBORX_EINVAL;
+  }
+  if (st) {
+    if (own) dev_free(h->opts, scratch, scratch_bytes, s);
+    return st;
+  }
   const SortWs ws = sort_ws_carve<K>(wsbase, n, key_bits);
 
   launch_morton<K>(d_prims, un, h->kind, h->meta, kA, ws.hist, passes, true, s);
@@ -325,14 +332,24 @@ struct QueryWs {
   size_t sort_words;
   int32_t *counts;
   int64_t *scan_tmp;
-  uint32_t *miss;  // miss list + counter (learned bound fallback)
+  uint32_t *miss;     // miss list + counter (learned bound fallback)
+  uint64_t *sc_ws;    // look-back status of the fused scan and compaction; follows miss[m + 32]
+  size_t sc_words;
 };
+
+// Zero the overflow counter (miss[m]) and the fused scan's look-back words in one memset: they
+// are adjacent in the workspace.
+void zero_ovf_and_scan(const QueryWs &q, int64_t m, cudaStream_t s) {
+  char *a = reinterpret_cast<char *>(q.miss + m);
+  char *b = reinterpret_cast<char *>(q.sc_ws + q.sc_words);
+  cudaMemsetAsync(a, 0, (size_t)(b - a), s);
+}
 
 size_t query_ws_bytes(int64_t m, size_t *sort_words) {
   *sort_words = sort_ws_words<uint32_t>(m, kQueryKeyBits);
   return 4 * align_up((size_t)m * sizeof(uint32_t)) + align_up(*sort_words * sizeof(uint32_t)) +
          align_up((size_t)m * sizeof(int32_t)) + align_up(scan_tmp_words((uint32_t)m) * sizeof(int64_t)) +
-         align_up(((size_t)m + 32) * sizeof(uint32_t));
+         align_up(((size_t)m + 32) * sizeof(uint32_t)) + align_up(scan_compact_ws_words((uint32_t)m) * sizeof(uint64_t));
 }
 
 int get_query_ws(arborx_bvh_s *h, int64_t m, cudaStream_t s, QueryWs *q) {
@@ -354,6 +371,8 @@ int get_query_ws(arborx_bvh_s *h, int64_t m, cudaStream_t s, QueryWs *q) {
   q->counts = c.take<int32_t>(m);
   q->scan_tmp = c.take<int64_t>(scan_tmp_words((uint32_t)m));
   q->miss = c.take<uint32_t>(m + 32);
+  q->sc_words = scan_compact_ws_words((uint32_t)m);
+  q->sc_ws = c.take<uint64_t>(q->sc_words);
   return ARBORX_OK;
 }
 
@@ -966,11 +985,11 @@ int arborx_query_spatial_buffered(arborx_handle h, const float *d_queries, int64
   if (st) return st;
   const float r2 = radius * radius;  // one IEEE single rounding
   uint32_t *ovf_count = q.miss + m;
-  cudaMemsetAsync(ovf_count, 0, sizeof(uint32_t), s);
+  zero_ovf_and_scan(q, m, s);
   launch_spatial_buffered(h->rec, (uint32_t)h->n, d_queries, perm, (uint32_t)m, r2, q.counts, h->sbuf, buffer_size,
                           q.miss, ovf_count, &h->meta->err, trav_cfg(h, 0), s);
-  launch_scan(q.counts, (uint32_t)m, d_offsets, q.scan_tmp, s);
-  launch_compact(h->sbuf, buffer_size, q.counts, d_offsets, (uint32_t)m, d_indices, capacity, &h->meta->err, s);
+  launch_scan_compact(q.counts, (uint32_t)m, h->sbuf, buffer_size, d_offsets, d_indices, capacity, q.sc_ws,
+                      &h->meta->err, s);
   launch_spatial_fill(h->rec, (uint32_t)h->n, d_queries, q.miss, (uint32_t)m, r2, d_offsets, d_indices, capacity,
                       &h->meta->err, trav_cfg(h, 0), s, ovf_count);
   h->stat_queries[0] += (uint64_t)m;
@@ -1079,12 +1098,12 @@ int arborx_query_intersects(arborx_handle h, const float *d_boxes, int64_t m, in
   st = order_queries(h, d_boxes, m, s, q, &perm, d_order, ARBORX_BOXES);
   if (st) return st;
   uint32_t *ovf_count = q.miss + m;
-  cudaMemsetAsync(ovf_count, 0, sizeof(uint32_t), s);
+  zero_ovf_and_scan(q, m, s);
   const TravCfg cfg = trav_cfg(h, 0);
   launch_spatial_buffered(h->rec, (uint32_t)h->n, d_boxes, perm, (uint32_t)m, 0.0f, q.counts, h->sbuf, buffer_size,
                           q.miss, ovf_count, &h->meta->err, cfg, s, true);
-  launch_scan(q.counts, (uint32_t)m, d_offsets, q.scan_tmp, s);
-  launch_compact(h->sbuf, buffer_size, q.counts, d_offsets, (uint32_t)m, d_indices, capacity, &h->meta->err, s);
+  launch_scan_compact(q.counts, (uint32_t)m, h->sbuf, buffer_size, d_offsets, d_indices, capacity, q.sc_ws,
+                      &h->meta->err, s);
   launch_spatial_fill(h->rec, (uint32_t)h->n, d_boxes, q.miss, (uint32_t)m, 0.0f, d_offsets, d_indices, capacity,
                       &h->meta->err, cfg, s, ovf_count, true);
   h->stat_queries[0] += (uint64_t)m;

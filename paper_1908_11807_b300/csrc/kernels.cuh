@@ -7,6 +7,8 @@ namespace abx {
 
 // ---- construction (build.cu)
 void launch_init_meta(DevMeta *meta, cudaStream_t s);
+// launch_init_meta and a zero fill of `bytes` (a multiple of 16) at the 16-byte aligned `zero`
+void launch_init_meta_zero(DevMeta *meta, void *zero, size_t bytes, cudaStream_t s);
 void launch_bounds(const float *prims, int64_t n, int kind, DevMeta *meta, cudaStream_t s);
 template <typename K>
 void launch_morton(const float *prims, uint32_t n, int kind, DevMeta *meta, K *codes, uint32_t *hist, int passes,
@@ -84,6 +86,11 @@ void launch_spatial_buffered(const float4 *rec, uint32_t n, const float *queries
                              uint32_t *err, const TravCfg &cfg, cudaStream_t s, bool box = false);
 void launch_compact(const int32_t *buf, int bs, const int32_t *counts, const int64_t *offsets, uint32_t m,
                     int32_t *indices, int64_t capacity, uint32_t *err, cudaStream_t s);
+// one-pass rows -> CSR in one kernel: exclusive scan of counts[m] into offsets[m+1] and the rows
+// of at most bs results copied from buf; ws: scan_compact_ws_words(m) uint64 words, all zero
+size_t scan_compact_ws_words(uint32_t m);
+void launch_scan_compact(const int32_t *counts, uint32_t m, const int32_t *buf, int bs, int64_t *offsets,
+                         int32_t *indices, int64_t capacity, uint64_t *ws, uint32_t *err, cudaStream_t s);
 // exclusive scan counts[m] -> offsets[m+1]; tmp holds scan_tmp_words(m) int64
 size_t scan_tmp_words(uint32_t m);
 void launch_scan(const int32_t *counts, uint32_t m, int64_t *offsets, int64_t *tmp, cudaStream_t s);

@@ -441,6 +441,26 @@ def test_async_one_pass_spatial_matches(name, bs):
     assert_spatial_equal(host(off), host(idx)[:nnz], oo, io)
 
 
+@pytest.mark.parametrize("bs", [10, 28])
+def test_async_one_pass_many_scan_tiles(bs):
+    # the single-call form scans and compacts in one kernel with a look-back over query tiles
+    # (hundreds of them at 300k queries, so look-back windows of 32 tiles are crossed); its CSR
+    # must equal the two-pass query's exactly (both bs % 4 forms of the row copy)
+    ab = _ab()
+    p = datagen.cube(200_000, 66)
+    q = datagen.cube(300_000, 67)
+    r = datagen.radius_for_mean(200_000, "cube")
+    bvh = ab.BVH(dev(p))
+    qd = dev(q)
+    order = bvh.query_order(qd)
+    og, ig = bvh.query_spatial(qd, r, order=order)
+    nnz = int(ig.numel())
+    off, idx = bvh.query_spatial_async(qd, r, buffer_size=bs, order=order, capacity=nnz)
+    bvh.check()
+    assert np.array_equal(host(off), host(og))
+    assert np.array_equal(host(idx)[:nnz], host(ig))
+
+
 def test_async_one_pass_spatial_capacity_and_graph():
     ab = _ab()
     import torch
