@@ -76,6 +76,20 @@ def _time(fn, reps: int = 3) -> float:
     return best
 
 
+DEFAULT_ANCHOR = 3     # the library's own tree-bound form (the traversal's first descent)
+ANCHOR_MARGIN = 0.01   # another form replaces it only when faster by more than this fraction
+
+
+def pick_anchor(ms: dict) -> int:
+    """The tree-bound form to use given the measured time of each: the library default unless
+    another form is faster by more than ANCHOR_MARGIN, so that near-ties (forms within timing
+    noise of each other) do not flip the choice from one tuning run to the next."""
+    best = min(ms, key=ms.get)
+    if DEFAULT_ANCHOR in ms and ms[best] >= (1.0 - ANCHOR_MARGIN) * ms[DEFAULT_ANCHOR]:
+        return DEFAULT_ANCHOR
+    return best
+
+
 def tune(points: torch.Tensor, queries: torch.Tensor, radius: float, k: int, tag: str,
          blocks: Iterable[int] = DEFAULT_BLOCKS, stacks: Iterable[int] = DEFAULT_STACKS,
          buffers: Iterable[int] = DEFAULT_BUFFERS, params: Optional[torch.Tensor] = None,
@@ -107,7 +121,7 @@ def tune(points: torch.Tensor, queries: torch.Tensor, radius: float, k: int, tag
         order = bvh.query_order(queries)
         anchor_ms[anchor] = _time(lambda: bvh.query_nearest(queries, k, order=order))
         bvh.destroy()
-    anchor = min(anchor_ms, key=anchor_ms.get)
+    anchor = pick_anchor(anchor_ms)
     bvh = _b.BVH(points, block_size=block, stack_smem=stack, knn_anchor=anchor)
     order = bvh.query_order(queries)
     buf_best = min((_time(lambda: bvh.query_spatial(queries, radius, order=order, buffer_size=bs)), bs)
@@ -234,7 +248,7 @@ def tune_batch(point_offsets, query_offsets, ks, points: torch.Tensor, queries: 
         return t
 
     hf = min((run_ms(knn_heap_from=h), h) for h in heap_froms)[1]
-    an = min((run_ms(knn_heap_from=hf, knn_anchor=a), a) for a in anchors)[1]
+    an = pick_anchor({a: run_ms(knn_heap_from=hf, knn_anchor=a) for a in anchors})
     best = None
     for block in blocks:
         for stack in stacks:
