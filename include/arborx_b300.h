@@ -273,6 +273,25 @@ ARBORX_API int arborx_query_spatial_buffered(arborx_handle h, const float *d_que
                                              int32_t buffer_size, const uint32_t *d_order, void *stream,
                                              int64_t *d_offsets, int32_t *d_indices, int64_t capacity);
 
+/* The one-pass spatial query of arborx_query_spatial_buffered and the nearest query of
+ * arborx_query_nearest over the same queries (Sec. 2.2: the two traversals share the tree and the
+ * query order but nothing else), in one call: after the query order, the nearest traversal runs on
+ * a second stream owned by the handle, forked from `stream` by an event and joined back into it,
+ * so that it overlaps the spatial query's counting traversal tail, compaction and overflow pass.
+ * Results equal those of the two calls made one after the other; work enqueued on `stream` after
+ * this call sees both.  The handle creates its second stream and two events on its first such
+ * call (make that call outside stream capture); arborx_destroy releases them.  No host
+ * synchronisation.
+ *   radius, buffer_size, d_offsets, d_indices, capacity  as for arborx_query_spatial_buffered
+ *   k, d_nn_offsets, d_nn_indices, d_nn_dist2             as d_offsets, d_indices, d_dist2 of
+ *                                                         arborx_query_nearest
+ *   d_order      NULL or a traversal order from arborx_query_order (shared by both traversals)
+ * Errors: those of the two calls; ARBORX_ECUDA when the stream or events cannot be created. */
+ARBORX_API int arborx_query_spatial_nearest(arborx_handle h, const float *d_queries, int64_t m, float radius,
+                                            int32_t buffer_size, int32_t k, const uint32_t *d_order, void *stream,
+                                            int64_t *d_offsets, int32_t *d_indices, int64_t capacity,
+                                            int64_t *d_nn_offsets, int32_t *d_nn_indices, float *d_nn_dist2);
+
 /* Traversal order of a set of query boxes: as arborx_query_order, with each box's centre
  * 0.5 (lo + hi) in place of the point (a NaN centre sorts first).
  *   d_boxes  device float[m][6] (lo.x, lo.y, lo.z, hi.x, hi.y, hi.z)

@@ -94,6 +94,8 @@ def lib() -> ctypes.CDLL:
                                                           ctypes.POINTER(i64)]
         L.arborx_query_spatial_buffered_fill.argtypes = [vp, vp, i64, ctypes.c_float, vp, vp, vp, i64]
         L.arborx_query_spatial_buffered.argtypes = [vp, vp, i64, ctypes.c_float, i32, vp, vp, vp, vp, i64]
+        L.arborx_query_spatial_nearest.argtypes = [vp, vp, i64, ctypes.c_float, i32, i32, vp, vp, vp, vp, i64, vp,
+                                                   vp, vp]
         L.arborx_query_order_boxes.argtypes = [vp, vp, i64, vp, vp]
         L.arborx_selftest_bounded_wait.argtypes = [vp]
         L.arborx_rebuild.argtypes = [vp, vp, vp]
@@ -301,6 +303,32 @@ class BVH:
                "arborx_query_spatial_buffered")
         self._async_keep = (q, order)  # inputs stay alive while the stream works
         return offsets, indices
+
+    def query_spatial_nearest(self, queries: torch.Tensor, radius: float, k: int, buffer_size: int = 32,
+                              order: Optional[torch.Tensor] = None, capacity: Optional[int] = None,
+                              indices: Optional[torch.Tensor] = None, return_dist2: bool = True):
+        """The one-pass spatial query of ``query_spatial_async`` and the nearest query of
+        ``query_nearest`` over the same queries in one call, the nearest traversal running
+        concurrently on a second stream of the handle: (offsets, indices, nearest indices,
+        nearest squared distances or None).  No host synchronisation."""
+        q = _as_f32_cuda(queries, 3, "queries")
+        m = q.shape[0]
+        offsets = torch.empty(m + 1, dtype=torch.int64, device=q.device)
+        if indices is None:
+            cap = int(m * buffer_size if capacity is None else capacity)
+            indices = torch.empty(max(cap, 1), dtype=torch.int32, device=q.device)
+        else:
+            cap = indices.numel() if capacity is None else int(capacity)
+            if indices.dtype != torch.int32 or not indices.is_cuda or indices.numel() < cap:
+                raise ValueError("indices must be an int32 CUDA tensor of at least `capacity` entries")
+        kk = min(int(k), self.n)
+        kidx = torch.empty((m, kk), dtype=torch.int32, device=q.device)
+        kd2 = torch.empty((m, kk), dtype=torch.float32, device=q.device) if return_dist2 else None
+        _check(lib().arborx_query_spatial_nearest(self.handle, _ptr(q), m, ctypes.c_float(radius), int(buffer_size),
+                                                  int(k), _ptr(order), _stream(), _ptr(offsets), _ptr(indices), cap,
+                                                  None, _ptr(kidx), _ptr(kd2)), "arborx_query_spatial_nearest")
+        self._async_keep = (q, order)  # inputs stay alive while the streams work
+        return offsets, indices, kidx, kd2
 
     def query_spatial_count(self, queries: torch.Tensor, radius: float,
                             offsets: Optional[torch.Tensor] = None,

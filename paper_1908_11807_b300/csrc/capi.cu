@@ -49,6 +49,9 @@ struct arborx_bvh_s {
   bool buffered_valid;
   // radius and box queries emit wholly contained subtrees from the kept leaf order
   bool emit_subtrees;
+  // second stream of arborx_query_spatial_nearest (forked from and joined to the caller's stream)
+  cudaStream_t side;
+  cudaEvent_t ev_fork, ev_join;
 };
 
 namespace {
@@ -323,6 +326,12 @@ void release(arborx_bvh_s *h) {
   dev_free(h->opts, h->order, h->order_bytes, h->stream);
   dev_free(h->opts, h->persist, h->persist_bytes, h->stream);
   h->qws = h->order = h->persist = nullptr;
+  // the stream and events are released once the work queued on them is done
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->side) cudaStreamDestroy(h->side);
+  h->ev_fork = h->ev_join = nullptr;
+  h->side = nullptr;
 }
 
 // Query workspace: codes A/B, perm A/B, sort workspace, counts, scan tiles.
@@ -600,6 +609,22 @@ int arborx_free(arborx_handle h, void *d_ptr, size_t bytes, void *stream) {
   return launch_status();
 }
 
+namespace {
+
+// The nearest query's traversal once the order is known (uses none of the query workspace).
+int nearest_work(arborx_bvh_s *h, const uint32_t *perm, const float *d_queries, int64_t m, int32_t k, cudaStream_t s,
+                 int64_t *d_offsets, int32_t *d_indices, float *d_dist2) {
+  NearestArgs a = nearest_args(h, d_queries, perm, m, k);
+  a.offsets = d_offsets;
+  a.out_idx = d_indices;
+  a.out_d2 = d_dist2;
+  if (launch_nearest(a, trav_cfg(h, 1), s)) return ARBORX_EINVAL;
+  h->stat_queries[1] += (uint64_t)m;
+  return launch_status();
+}
+
+}  // namespace
+
 int arborx_query_nearest(arborx_handle h, const float *d_queries, int64_t m, int32_t k, const uint32_t *d_order,
                          void *stream, int64_t *d_offsets, int32_t *d_indices, float *d_dist2) {
   if (!h || m < 0 || m >= ARBORX_MAX_QUERIES || k < 1 || k > ARBORX_MAX_K || (m > 0 && !d_queries))
@@ -618,13 +643,7 @@ int arborx_query_nearest(arborx_handle h, const float *d_queries, int64_t m, int
   const uint32_t *perm;
   st = order_queries(h, d_queries, m, s, q, &perm, d_order);
   if (st) return st;
-  NearestArgs a = nearest_args(h, d_queries, perm, m, k);
-  a.offsets = d_offsets;
-  a.out_idx = d_indices;
-  a.out_d2 = d_dist2;
-  if (launch_nearest(a, trav_cfg(h, 1), s)) return ARBORX_EINVAL;
-  h->stat_queries[1] += (uint64_t)m;
-  return launch_status();
+  return nearest_work(h, perm, d_queries, m, k, s, d_offsets, d_indices, d_dist2);
 }
 
 int arborx_export_tree(arborx_handle h, void *stream, float *d_records, float *d_scene, uint64_t *d_codes,
@@ -960,6 +979,40 @@ int arborx_query_spatial_buffered_fill(arborx_handle h, const float *d_queries, 
   return st ? st : launch_status();
 }
 
+namespace {
+
+// The one-call one-pass spatial query after the row buffer is sized and the order known.
+int spatial_buffered_work(arborx_bvh_s *h, const QueryWs &q, const uint32_t *perm, const float *d_queries, int64_t m,
+                          float radius, int32_t buffer_size, cudaStream_t s, int64_t *d_offsets, int32_t *d_indices,
+                          int64_t capacity) {
+  const float r2 = radius * radius;  // one IEEE single rounding
+  uint32_t *ovf_count = q.miss + m;
+  zero_ovf_and_scan(q, m, s);
+  launch_spatial_buffered(h->rec, (uint32_t)h->n, d_queries, perm, (uint32_t)m, r2, q.counts, h->sbuf, buffer_size,
+                          q.miss, ovf_count, &h->meta->err, trav_cfg(h, 0), s);
+  launch_scan_compact(q.counts, (uint32_t)m, h->sbuf, buffer_size, d_offsets, d_indices, capacity, q.sc_ws,
+                      &h->meta->err, s);
+  launch_spatial_fill(h->rec, (uint32_t)h->n, d_queries, q.miss, (uint32_t)m, r2, d_offsets, d_indices, capacity,
+                      &h->meta->err, trav_cfg(h, 0), s, ovf_count);
+  h->stat_queries[0] += (uint64_t)m;
+  const int st = sort_rows(h, d_offsets, d_indices, m, capacity, s);
+  return st ? st : launch_status();
+}
+
+// Grow the handle's one-pass row buffer to m rows of buffer_size slots.
+int size_row_buffer(arborx_bvh_s *h, int64_t m, int32_t buffer_size, cudaStream_t s) {
+  const size_t need = (size_t)m * buffer_size * sizeof(int32_t);
+  if (need > h->sbuf_bytes) {
+    dev_free(h->opts, h->sbuf, h->sbuf_bytes, s);
+    h->sbuf = (int32_t *)dev_alloc(h->opts, need, s);
+    h->sbuf_bytes = h->sbuf ? need : 0;
+    if (!h->sbuf) return ARBORX_ENOMEM;
+  }
+  return ARBORX_OK;
+}
+
+}  // namespace
+
 int arborx_query_spatial_buffered(arborx_handle h, const float *d_queries, int64_t m, float radius,
                                   int32_t buffer_size, const uint32_t *d_order, void *stream, int64_t *d_offsets,
                                   int32_t *d_indices, int64_t capacity) {
@@ -973,28 +1026,56 @@ int arborx_query_spatial_buffered(arborx_handle h, const float *d_queries, int64
   QueryWs q;
   int st = get_query_ws(h, m, s, &q);
   if (st) return st;
-  const size_t need = (size_t)m * buffer_size * sizeof(int32_t);
-  if (need > h->sbuf_bytes) {
-    dev_free(h->opts, h->sbuf, h->sbuf_bytes, s);
-    h->sbuf = (int32_t *)dev_alloc(h->opts, need, s);
-    h->sbuf_bytes = h->sbuf ? need : 0;
-    if (!h->sbuf) return ARBORX_ENOMEM;
-  }
+  st = size_row_buffer(h, m, buffer_size, s);
+  if (st) return st;
   const uint32_t *perm;
   st = order_queries(h, d_queries, m, s, q, &perm, d_order);
   if (st) return st;
-  const float r2 = radius * radius;  // one IEEE single rounding
-  uint32_t *ovf_count = q.miss + m;
-  zero_ovf_and_scan(q, m, s);
-  launch_spatial_buffered(h->rec, (uint32_t)h->n, d_queries, perm, (uint32_t)m, r2, q.counts, h->sbuf, buffer_size,
-                          q.miss, ovf_count, &h->meta->err, trav_cfg(h, 0), s);
-  launch_scan_compact(q.counts, (uint32_t)m, h->sbuf, buffer_size, d_offsets, d_indices, capacity, q.sc_ws,
-                      &h->meta->err, s);
-  launch_spatial_fill(h->rec, (uint32_t)h->n, d_queries, q.miss, (uint32_t)m, r2, d_offsets, d_indices, capacity,
-                      &h->meta->err, trav_cfg(h, 0), s, ovf_count);
-  h->stat_queries[0] += (uint64_t)m;
-  st = sort_rows(h, d_offsets, d_indices, m, capacity, s);
-  return st ? st : launch_status();
+  return spatial_buffered_work(h, q, perm, d_queries, m, radius, buffer_size, s, d_offsets, d_indices, capacity);
+}
+
+int arborx_query_spatial_nearest(arborx_handle h, const float *d_queries, int64_t m, float radius,
+                                 int32_t buffer_size, int32_t k, const uint32_t *d_order, void *stream,
+                                 int64_t *d_offsets, int32_t *d_indices, int64_t capacity, int64_t *d_nn_offsets,
+                                 int32_t *d_nn_indices, float *d_nn_dist2) {
+  if (!h || m < 0 || m >= ARBORX_MAX_QUERIES || !d_offsets || (m > 0 && !d_queries) || !finite_radius(radius) ||
+      buffer_size < 1 || buffer_size > ARBORX_MAX_BUFFER_SIZE || capacity < 0 || (capacity > 0 && !d_indices) ||
+      k < 1 || k > ARBORX_MAX_K)
+    return ARBORX_EINVAL;
+  const int64_t kk = k < h->n ? k : h->n;
+  if (m > 0 && kk > 0 && !d_nn_indices) return ARBORX_EINVAL;
+  const cudaStream_t s = (cudaStream_t)stream;
+  h->stream = s;
+  h->count_valid = false;
+  h->buffered_valid = false;
+  QueryWs q;
+  int st = get_query_ws(h, m, s, &q);
+  if (st) return st;
+  st = size_row_buffer(h, m, buffer_size, s);
+  if (st) return st;
+  const uint32_t *perm;
+  st = order_queries(h, d_queries, m, s, q, &perm, d_order);
+  if (st) return st;
+  if (m == 0 || kk == 0) {  // nothing to traverse for the nearest query
+    if (d_nn_offsets) cudaMemsetAsync(d_nn_offsets, 0, (size_t)(m + 1) * sizeof(int64_t), s);
+    return spatial_buffered_work(h, q, perm, d_queries, m, radius, buffer_size, s, d_offsets, d_indices, capacity);
+  }
+  if (!h->side) {
+    if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess)
+      return ARBORX_ECUDA;
+  }
+  // fork: the nearest traversal on the handle's second stream, the spatial query on `stream`
+  if (cudaEventRecord(h->ev_fork, s) != cudaSuccess || cudaStreamWaitEvent(h->side, h->ev_fork, 0) != cudaSuccess)
+    return ARBORX_ECUDA;
+  const int st_nn = nearest_work(h, perm, d_queries, m, k, h->side, d_nn_offsets, d_nn_indices, d_nn_dist2);
+  const int st_sp =
+      spatial_buffered_work(h, q, perm, d_queries, m, radius, buffer_size, s, d_offsets, d_indices, capacity);
+  // join: `stream` waits for the nearest traversal, so later work on it sees both results
+  if (cudaEventRecord(h->ev_join, h->side) != cudaSuccess || cudaStreamWaitEvent(s, h->ev_join, 0) != cudaSuccess)
+    return ARBORX_ECUDA;
+  return st_nn ? st_nn : st_sp;
 }
 
 namespace {

@@ -495,3 +495,67 @@ def test_async_one_pass_spatial_capacity_and_graph():
     bvh.check()
     assert np.array_equal(host(goff), host(og))
     assert np.array_equal(host(out_idx)[:nnz], host(ig))
+
+
+@pytest.mark.parametrize("name", ["cube_1e4", "paper_hollow", "duplicates", "boxes", "gaussian_2e4"])
+@pytest.mark.parametrize("bs,k,given_order", [(10, 10, True), (32, 1, False), (28, 50, True)])
+def test_spatial_nearest_in_one_call(name, bs, k, given_order):
+    # the two traversals forked onto two streams give what the two calls give one after the
+    # other, and the brute-force rows; later work on the caller's stream sees both results
+    import torch
+    ab = _ab()
+    p, q, r = CASES[name]()
+    bvh = ab.BVH(dev(p))
+    qd = dev(q)
+    order = bvh.query_order(qd) if given_order else None
+    off, idx, kidx, kd2 = bvh.query_spatial_nearest(qd, r, k, buffer_size=bs, order=order, capacity=len(q) * 64)
+    ksum = kidx.to(torch.int64).sum()  # enqueued on the caller's stream right after the call
+    bvh.check()
+    off_s, idx_s = bvh.query_spatial_async(qd, r, buffer_size=bs, order=order, capacity=len(q) * 64)
+    ki_s, kd_s = bvh.query_nearest(qd, k, order=order)
+    nnz = int(off[-1])
+    assert np.array_equal(host(off), host(off_s))
+    assert np.array_equal(host(idx)[:nnz], host(idx_s)[:nnz])
+    assert np.array_equal(host(kidx), host(ki_s)) and np.array_equal(host(kd2), host(kd_s))
+    assert int(ksum) == int(ki_s.to(torch.int64).sum())
+    oo, io = oracle.spatial_brute(p, q, r)
+    assert_spatial_equal(host(off), host(idx)[:nnz], oo, io)
+    ko, do = oracle.nearest_brute(p, q, k)
+    assert_nearest_equal(host(kidx), host(kd2), ko, do)
+
+
+def test_spatial_nearest_in_one_call_edges_and_graph():
+    import torch
+    ab = _ab()
+    p, q, r = CASES["cube_1e4"]()
+    qd = dev(q)
+    # empty query set, and an empty tree
+    bvh = ab.BVH(dev(p))
+    off, idx, kidx, kd2 = bvh.query_spatial_nearest(qd[:0], r, 10, buffer_size=8, capacity=0)
+    assert host(off).tolist() == [0] and kidx.shape == (0, 10)
+    empty = ab.BVH(torch.zeros((0, 3), device="cuda"))
+    off, idx, kidx, kd2 = empty.query_spatial_nearest(qd, r, 5, buffer_size=8)
+    empty.check()
+    assert not host(off).any() and kidx.shape == (len(q), 0)
+    # more than n neighbours: rows of n
+    small = ab.BVH(dev(p[:7]))
+    _, _, kidx, kd2 = small.query_spatial_nearest(qd, r, 12, buffer_size=8)
+    ko, do = oracle.nearest_brute(p[:7], q, 12)
+    assert_nearest_equal(host(kidx), host(kd2), ko, do)
+    # the first call creates the handle's second stream; later calls can be captured and replayed
+    order = bvh.query_order(qd)
+    out_idx = torch.empty(len(q) * 16, dtype=torch.int32, device="cuda")
+    bvh.query_spatial_nearest(qd, r, 10, buffer_size=16, order=order, indices=out_idx)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        goff, _, gki, gkd = bvh.query_spatial_nearest(qd, r, 10, buffer_size=16, order=order, indices=out_idx)
+    out_idx.fill_(-7)
+    gki.fill_(-7)
+    g.replay()
+    torch.cuda.synchronize()
+    bvh.check()
+    og, ig = bvh.query_spatial(qd, r, order=order)
+    ki, kd = bvh.query_nearest(qd, 10, order=order)
+    assert np.array_equal(host(goff), host(og)) and np.array_equal(host(out_idx)[:ig.numel()], host(ig))
+    assert np.array_equal(host(gki), host(ki)) and np.array_equal(host(gkd), host(kd))
