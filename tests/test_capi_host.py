@@ -88,6 +88,9 @@ def test_invalid_arguments_rejected_without_device(L):
     assert L.arborx_order(None, 0, 0, None, None, None) == b.ARBORX_OK
     # rebuild needs a handle
     assert L.arborx_rebuild(None, None, None) == b.ARBORX_EINVAL
+    # spatial and nearest in one call: a handle, then the checks of both queries
+    assert L.arborx_query_spatial_nearest(None, None, 0, ctypes.c_float(1.0), 8, 10, None, None,
+                                          ctypes.c_void_p(16), None, 0, None, None, None) == b.ARBORX_EINVAL
 
 
 def test_binding_refuses_cpu_tensors():

@@ -537,6 +537,10 @@ def test_spatial_nearest_in_one_call_edges_and_graph():
     off, idx, kidx, kd2 = empty.query_spatial_nearest(qd, r, 5, buffer_size=8)
     empty.check()
     assert not host(off).any() and kidx.shape == (len(q), 0)
+    # argument checks of both queries (buffer size, k), before any work is enqueued
+    for bs, kk in ((0, 10), (4097, 10), (8, 0), (8, 513)):
+        with pytest.raises(ab.ArborXError):
+            bvh.query_spatial_nearest(qd, r, kk, buffer_size=bs)
     # more than n neighbours: rows of n
     small = ab.BVH(dev(p[:7]))
     _, _, kidx, kd2 = small.query_spatial_nearest(qd, r, 12, buffer_size=8)
