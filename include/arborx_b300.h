@@ -330,6 +330,14 @@ ARBORX_API int arborx_query_intersects(arborx_handle h, const float *d_boxes, in
  * `stream`; takes about a second. */
 ARBORX_API int arborx_selftest_bounded_wait(void *stream);
 
+/* Self-test of the one-call spatial query's scan (not in the paper): the scan-and-compaction
+ * kernel of arborx_query_spatial_buffered runs over two tiles of empty rows with its tile counter
+ * preset so that its only block takes the second tile and looks back at a first tile that never
+ * publishes; the look-back gives up at its iteration cap.  Returns ARBORX_ETIMEOUT (the expected
+ * result; the device stays usable), ARBORX_ENOMEM or ARBORX_ECUDA.  Synchronises `stream`; takes
+ * about a second. */
+ARBORX_API int arborx_selftest_scan_wait(void *stream);
+
 /* Release memory returned by arborx_query_spatial (stream-ordered on `stream`). */
 ARBORX_API int arborx_free(arborx_handle h, void *d_ptr, size_t bytes, void *stream);
 

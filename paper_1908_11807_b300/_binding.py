@@ -98,6 +98,7 @@ def lib() -> ctypes.CDLL:
                                                    vp, vp]
         L.arborx_query_order_boxes.argtypes = [vp, vp, i64, vp, vp]
         L.arborx_selftest_bounded_wait.argtypes = [vp]
+        L.arborx_selftest_scan_wait.argtypes = [vp]
         L.arborx_rebuild.argtypes = [vp, vp, vp]
         L.arborx_order.argtypes = [vp, i64, i32, ctypes.POINTER(arborx_opts), vp, vp]
         L.arborx_query_intersects.argtypes = [vp, vp, i64, i32, vp, vp, vp, vp, i64]

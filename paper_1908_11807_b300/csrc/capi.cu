@@ -724,6 +724,32 @@ int arborx_selftest_bounded_wait(void *stream) {
   return err_bits_to_status(bits);
 }
 
+int arborx_selftest_scan_wait(void *stream) {
+  const cudaStream_t s = (cudaStream_t)stream;
+  arborx_opts o;
+  arborx_default_opts(&o);
+  constexpr uint32_t m = 4096;  // two tiles of the one-call scan
+  const size_t ws_words = scan_compact_ws_words(m);
+  const size_t bytes = align_up(m * sizeof(int32_t)) + align_up((m + 1) * sizeof(int64_t)) +
+                       align_up(ws_words * sizeof(uint64_t)) + align_up(sizeof(uint32_t));
+  void *tmp = dev_alloc(o, bytes, s);
+  if (!tmp) return ARBORX_ENOMEM;
+  Carver c(tmp);
+  int32_t *counts = c.take<int32_t>(m);
+  int64_t *offsets = c.take<int64_t>(m + 1);
+  uint64_t *ws = c.take<uint64_t>(ws_words);
+  uint32_t *err = c.take<uint32_t>(1);
+  uint32_t bits = 0;
+  cudaMemsetAsync(err, 0, sizeof(uint32_t), s);
+  launch_scan_compact_wait_probe(counts, offsets, ws, err, s);
+  cudaMemcpyAsync(&bits, err, sizeof bits, cudaMemcpyDeviceToHost, s);
+  dev_free(o, tmp, bytes, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return ARBORX_ECUDA;
+  const int st = launch_status();
+  if (st) return st;
+  return err_bits_to_status(bits);
+}
+
 // ------------------------------------------------------------ learned bound
 
 int arborx_mlp_forward(arborx_handle h, const float *d_params, const float *d_queries, int64_t m, int32_t tensor_cores,

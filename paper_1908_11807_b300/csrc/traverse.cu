@@ -1312,6 +1312,17 @@ void launch_scan_compact(const int32_t *counts, uint32_t m, const int32_t *buf, 
     k_scan_compact<false><<<tiles, kScThreads, 0, s>>>(counts, m, buf, bs, offsets, indices, capacity, ws, ctr, err);
 }
 
+void launch_scan_compact_wait_probe(int32_t *counts, int64_t *offsets, uint64_t *ws, uint32_t *err, cudaStream_t s) {
+  // two tiles of empty rows; the tile counter starts at 1, so the single block takes tile 1 and
+  // looks back at tile 0, whose status word nobody publishes
+  const uint32_t m = 2 * kScTile;
+  cudaMemsetAsync(counts, 0, (size_t)m * sizeof(int32_t), s);
+  cudaMemsetAsync(ws, 0, scan_compact_ws_words(m) * sizeof(uint64_t), s);
+  cudaMemsetAsync(reinterpret_cast<uint32_t *>(ws + 2), 1, 1, s);  // the tile counter (after the 2 status words): 1
+  k_scan_compact<false><<<1, kScThreads, 0, s>>>(counts, m, counts, 1, offsets, nullptr, 0, ws,
+                                                reinterpret_cast<uint32_t *>(ws + 2), err);
+}
+
 size_t scan_tmp_words(uint32_t m) { return (size_t)ceil_div<uint32_t>(m > 0 ? m : 1, (uint32_t)kScanTile) + 1; }
 
 void launch_scan(const int32_t *counts, uint32_t m, int64_t *offsets, int64_t *tmp, cudaStream_t s) {
