@@ -556,14 +556,27 @@ __global__ void __launch_bounds__(kApBlock) k_apetrei_local(const float *__restr
   }
   __syncthreads();
 #pragma unroll 1
-  for (int j = 1; j < kApLevels; ++j) {
+  // two table levels per barrier: levels j and j + 1 both from level j - 1 (the same loads as one
+  // level at a time, half the barriers)
+  static_assert(kApLevels % 2 == 1 && kApSegLevels % 2 == 1, "levels are built in pairs");
+  for (int j = 1; j < kApLevels; j += 2) {
     const int h = 1 << (j - 1);
-    if (tid + 2 * h - 1 <= last) s_dmin[j][tid] = min(s_dmin[j - 1][tid], s_dmin[j - 1][tid + h]);
+    if (tid + 2 * h - 1 <= last) {
+      const int m01 = min(s_dmin[j - 1][tid], s_dmin[j - 1][tid + h]);
+      s_dmin[j][tid] = m01;
+      if (tid + 4 * h - 1 <= last) s_dmin[j + 1][tid] = min(m01, min(s_dmin[j - 1][tid + 2 * h], s_dmin[j - 1][tid + 3 * h]));
+    }
     if (j < kApSegLevels && tid + 2 * h <= kApSegs) {
       float4 a = s_seg[j - 1][0][tid], b = s_seg[j - 1][1][tid];
       box_union(a, b, s_seg[j - 1][0][tid + h], s_seg[j - 1][1][tid + h]);
       s_seg[j][0][tid] = a;
       s_seg[j][1][tid] = b;
+      if (tid + 4 * h <= kApSegs) {
+        box_union(a, b, s_seg[j - 1][0][tid + 2 * h], s_seg[j - 1][1][tid + 2 * h]);
+        box_union(a, b, s_seg[j - 1][0][tid + 3 * h], s_seg[j - 1][1][tid + 3 * h]);
+        s_seg[j + 1][0][tid] = a;
+        s_seg[j + 1][1][tid] = b;
+      }
     }
     __syncthreads();
   }
