@@ -470,7 +470,6 @@ __global__ void __launch_bounds__(kApBlock) k_apetrei_local(const float *__restr
                                                            int32_t *__restrict__ other, float4 *__restrict__ rec,
                                                            Frontier *__restrict__ front, uint32_t *__restrict__ err) {
   constexpr int C = kApChunk;
-  __shared__ K s_code[C + 2];                          // codes of positions c0 - 1 .. c0 + C
   __shared__ int32_t s_dmin[kApLevels][C + 1];         // [j][x]: min d over positions c0-1+x .. +2^j-1
   __shared__ float4 s_leaf[2][C];                      // leaf boxes (lo, hi)
   __shared__ float4 s_pre[2][C], s_suf[2][C];          // unions from segment start to t / t to segment end
@@ -510,16 +509,13 @@ __global__ void __launch_bounds__(kApBlock) k_apetrei_local(const float *__restr
       hi = make_float4(q[3], q[4], q[5], 0.0f);
     }
   }
-  for (int i = tid; i < C + 2; i += kApBlock) {
-    const int x = c0 - 1 + i;
-    if (x >= 0 && x < N) s_code[i] = codes[x];
-  }
-  if (tid < 2) s_front[tid].l = -1;
-  __syncthreads();
-  // d at positions c0 - 1 + x (-1 outside [0, N - 2])
+  if (tid < 2) s_front[tid].l = -1;  // read after the barrier below
+  // d at positions c0 - 1 + x (-1 outside [0, N - 2]), straight from the codes in global memory
+  // (each code is read by two neighbouring threads, the second time from L1), so no barrier
+  // stands between the code loads and the table
   auto dl = [&](int pos) -> int {
     if (pos < 0 || pos >= N - 1) return -1;
-    const K ci = s_code[pos - c0 + 1], cj = s_code[pos - c0 + 2];
+    const K ci = __ldg(codes + pos), cj = __ldg(codes + pos + 1);
     if (ci != cj) return clz_key<K>(ci ^ cj);
     return (int)(8 * sizeof(K)) + __clz((uint32_t)(pos ^ (pos + 1)));
   };
