@@ -96,7 +96,9 @@ def tune(points: torch.Tensor, queries: torch.Tensor, radius: float, k: int, tag
          margins: Iterable[float] = DEFAULT_MARGINS, anchors: Iterable[int] = DEFAULT_ANCHORS,
          use_cache: bool = True) -> dict:
     """Return {"block_size", "stack_smem", "buffer_size", "margin", "knn_anchor", "ms"} for this
-    workload class, timing the candidates on (points, queries) unless the cache has them."""
+    workload class, timing the candidates on (points, queries) unless the cache has them.  The
+    row-buffer widths timed are ``buffers`` and the widths ``pick_buffer`` derives from the
+    queries' own hit counts."""
     key = cache_key(points.shape[0], k, tag)
     if use_cache:
         hit = _load().get(key)
@@ -124,8 +126,16 @@ def tune(points: torch.Tensor, queries: torch.Tensor, radius: float, k: int, tag
     anchor = pick_anchor(anchor_ms)
     bvh = _b.BVH(points, block_size=block, stack_smem=stack, knn_anchor=anchor)
     order = bvh.query_order(queries)
-    buf_best = min((_time(lambda: bvh.query_spatial(queries, radius, order=order, buffer_size=bs)), bs)
-                   for bs in buffers)[1]
+    # the fixed widths and those of the query set's own hit counts (the median, 99th percentile and
+    # largest count of a sample, rounded up to a multiple of 4), each timed in the single-call
+    # one-pass form the step runs (0: the two-pass query)
+    buf_ms = {}
+    for bs in sorted(set(buffers) | buffer_candidates(bvh, queries, radius)):
+        if bs == 0:
+            buf_ms[bs] = _time(lambda: bvh.query_spatial(queries, radius, order=order))
+        else:
+            buf_ms[bs] = _time(lambda: bvh.query_spatial_async(queries, radius, buffer_size=bs, order=order))
+    buf_best = min(buf_ms, key=buf_ms.get)
     margin = None
     if params is not None:
         margin = min((_time(lambda: bvh.query_nearest_learned(queries, k, params, mg, order=order)), mg)
@@ -170,6 +180,29 @@ def _round4(x: float) -> int:
     return max(4, 4 * int(math.ceil(x / 4.0)))
 
 
+def _hit_stats(bvh, queries: torch.Tensor, radius: float, sample: int = 65536) -> dict:
+    """Mean, median, 99th percentile and largest hit count over a strided sample of the queries."""
+    step = max(1, int(queries.shape[0]) // sample)
+    cnt = torch.diff(bvh.query_spatial_count(queries[::step].contiguous(), radius)).double()
+    return {"mean": float(cnt.mean()), "p50": float(cnt.quantile(0.5)), "p99": float(cnt.quantile(0.99)),
+            "max": float(cnt.max())}
+
+
+def buffer_candidates(bvh, queries: torch.Tensor, radius: float, hits: Optional[dict] = None) -> set:
+    """Row-buffer widths worth timing for this radius: two passes (0) and the median, 99th
+    percentile and largest hit count of a sample, each rounded up to a multiple of 4, at most 4096
+    and at most 4 GB of buffer."""
+    m = int(queries.shape[0])
+    if m == 0:
+        return {0}
+    hits = hits or _hit_stats(bvh, queries, radius)
+    cap = min(MAX_BUFFER_SIZE, (BUFFER_BYTES_CAP // (4 * m)) // 4 * 4)
+    cands = {0}
+    if cap >= 4:
+        cands |= {min(cap, _round4(hits[q])) for q in ("p50", "p99", "max")}
+    return cands
+
+
 def pick_buffer(bvh, queries: torch.Tensor, radius: float, order: Optional[torch.Tensor] = None,
                 sample: int = 65536, reps: int = 2) -> dict:
     """Row-buffer width of the one-pass radius query for this radius (0 = two passes).
@@ -184,18 +217,11 @@ def pick_buffer(bvh, queries: torch.Tensor, radius: float, order: Optional[torch
     m = int(queries.shape[0])
     if m == 0:
         return {"buffer_size": 0, "ms": {}, "hits": {}}
-    step = max(1, m // sample)
-    qs = queries[::step].contiguous()
-    cnt = torch.diff(bvh.query_spatial_count(qs, radius)).double()
-    hits = {"mean": float(cnt.mean()), "p50": float(cnt.quantile(0.5)), "p99": float(cnt.quantile(0.99)),
-            "max": float(cnt.max())}
-    cap = min(MAX_BUFFER_SIZE, (BUFFER_BYTES_CAP // (4 * m)) // 4 * 4)
+    hits = _hit_stats(bvh, queries, radius, sample)
     keep = bool(getattr(bvh.opts, "keep_order", 0))
     if keep:
         bvh.emit_subtrees(False)  # widths are timed with the walking traversal
-    cands = {0}
-    if cap >= 4:
-        cands |= {min(cap, _round4(hits[q])) for q in ("p50", "p99", "max")}
+    cands = buffer_candidates(bvh, queries, radius, hits)
     ms = {}
     for bs in sorted(cands):
         ms[bs] = round(_time(lambda: bvh.query_spatial(queries, radius, order=order, buffer_size=bs), reps), 4)
