@@ -1039,7 +1039,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const int32_t *__res
 constexpr int kScThreads = 256;
 constexpr int kScQ = 8;                        // queries per thread (2: 62.5 against 54.1 us at 1e6 rows)
 constexpr int kScTile = kScThreads * kScQ;     // queries per tile
-constexpr int kScUnroll = 4;                   // row-buffer loads in flight per thread
+constexpr int kScUnroll = 8;                   // row-buffer loads in flight per thread
 constexpr uint64_t kScAgg = 1ull << 62;        // tile total published
 constexpr uint64_t kScPre = 1ull << 63;        // inclusive prefix over tiles 0..t published
 constexpr uint64_t kScVal = kScAgg - 1;
