@@ -461,6 +461,25 @@ def test_async_one_pass_many_scan_tiles(bs):
     assert np.array_equal(host(idx)[:nnz], host(ig))
 
 
+@pytest.mark.parametrize("m", [1, 31, 2047, 2048, 2049, 4096, 6145])
+def test_async_one_pass_scan_tile_edges(m):
+    # query counts around the fused scan's 2048-query tiles: one partial tile, exactly full tiles,
+    # one query into the next tile; offsets and rows equal the two-pass query's
+    ab = _ab()
+    p = datagen.cube(50_000, 68)
+    q = datagen.cube(m, 69)
+    r = datagen.radius_for_mean(50_000, "cube")
+    bvh = ab.BVH(dev(p))
+    qd = dev(q)
+    og, ig = bvh.query_spatial(qd, r)
+    nnz = int(ig.numel())
+    for bs in (8, 10):
+        off, idx = bvh.query_spatial_async(qd, r, buffer_size=bs, capacity=max(nnz, 1))
+        bvh.check()
+        assert np.array_equal(host(off), host(og))
+        assert np.array_equal(host(idx)[:nnz], host(ig))
+
+
 def test_async_one_pass_spatial_capacity_and_graph():
     ab = _ab()
     import torch
