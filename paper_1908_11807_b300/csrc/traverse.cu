@@ -1033,8 +1033,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const int32_t *__res
 // scans the tile's counts, obtains the sum of all earlier tiles by decoupled look-back over one
 // 64-bit status word per tile (bounded spin, ERR_TIMEOUT on give-up), writes the tile's offsets
 // and copies the tile's rows from the buffer.  Rows longer than bs are left to the overflow
-// pass, which writes them at the same offsets.  Replaces the three scan kernels and the
-// compaction kernel of the split form.
+// pass, which writes them at the same offsets.  The one-call form runs it where the split form
+// (count call, then fill call) runs three scan kernels and k_compact.
 
 constexpr int kScThreads = 256;
 constexpr int kScQ = 8;                        // queries per thread (2: 62.5 against 54.1 us at 1e6 rows)
@@ -1043,7 +1043,7 @@ constexpr int kScUnroll = 8;                   // row-buffer loads in flight per
 constexpr uint64_t kScAgg = 1ull << 62;        // tile total published
 constexpr uint64_t kScPre = 1ull << 63;        // inclusive prefix over tiles 0..t published
 constexpr uint64_t kScVal = kScAgg - 1;
-constexpr uint32_t kScSpinCap = 1u << 20;      // look-back give-up bound (about half a second)
+constexpr uint32_t kScSpinCap = 1u << 20;      // look-back give-up bound (about a second with the sleeps)
 
 __device__ __forceinline__ uint64_t ld_relaxed_gpu_u64(const uint64_t *p) {
   uint64_t v;
