@@ -554,17 +554,22 @@ def run_gpu(args):
     prof = ab.profile_report()
     launches = int(sum(c for c, _ in prof.values()))  # every launch of the K timed steps
     prof_overlapped = prof
+    seq_phase = None
     if concurrent:
         # Per-kernel times for the kernel table and the roofline come from the same number of
         # steps run one kernel after another (the two traversals of the step above share the
         # GPU, so each one's event interval also holds the other's work)
+        seq_phase = np.zeros(3)
         for _ in range(args.steps):
             flush()
             barrier()
-            _, _, bvh = step(p, q, conc=False)
+            ev, _, bvh = step(p, q, conc=False)
             torch.cuda.synchronize()
             bvh.check()
             bvh.destroy()
+            t = [ev[0].elapsed_time(e) for e in ev[1:]]
+            seq_phase += np.array([t[0], t[1] - t[0], t[2] - t[1]])
+        seq_phase /= args.steps
         prof = ab.profile_report()
     ab.profile_enable(False)
     clocks = clk.summary()
@@ -628,7 +633,13 @@ def run_gpu(args):
                         "build_ms": round(build_ms, 4),
                         "queries_ms": round(spatial_ms, 4), "nnz": nnz,
                         "queries": "query order, then the radius and k-NN queries in one call "
-                                   "(arborx_query_spatial_nearest: the k-NN traversal on a second stream)"}
+                                   "(arborx_query_spatial_nearest: the k-NN traversal on a second stream)",
+                        "sequential_pass": {"note": "the same steps with the two queries one after the "
+                                                    "other (the pass that times the kernels)",
+                                            "build_ms": round(float(seq_phase[0]), 4),
+                                            "radius_ms": round(float(seq_phase[1]), 4),
+                                            "knn_ms": round(float(seq_phase[2]), 4),
+                                            "step_ms": round(float(seq_phase.sum()), 4)}}
                        if concurrent else
                        {"build_mpts_s": round(n / (build_ms * 1e-3) / 1e6, 2),
                         "radius_mq_s": round(m / (spatial_ms * 1e-3) / 1e6, 2),
