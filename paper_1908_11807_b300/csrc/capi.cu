@@ -1086,11 +1086,20 @@ int arborx_query_spatial_nearest(arborx_handle h, const float *d_queries, int64_
     if (d_nn_offsets) cudaMemsetAsync(d_nn_offsets, 0, (size_t)(m + 1) * sizeof(int64_t), s);
     return spatial_buffered_work(h, q, perm, d_queries, m, radius, buffer_size, s, d_offsets, d_indices, capacity);
   }
-  if (!h->side) {
-    if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess)
+  if (!h->side) {  // first such call on the handle: its second stream and the two events
+    cudaStream_t side = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&e0, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&e1, cudaEventDisableTiming) != cudaSuccess) {
+      if (e0) cudaEventDestroy(e0);
+      if (side) cudaStreamDestroy(side);
+      cudaGetLastError();
       return ARBORX_ECUDA;
+    }
+    h->side = side;
+    h->ev_fork = e0;
+    h->ev_join = e1;
   }
   // fork: the nearest traversal on the handle's second stream, the spatial query on `stream`
   if (cudaEventRecord(h->ev_fork, s) != cudaSuccess || cudaStreamWaitEvent(h->side, h->ev_fork, 0) != cudaSuccess)
