@@ -55,6 +55,14 @@ def test_paper_scale_sampled_exact(dist, n):
     # the two-pass scheme returns the same CSR arrays (same traversal order)
     og2, ig2 = bvh.query_spatial(qd, r, order=order)
     assert bool((og2 == og).all()) and bool((ig2 == ig).all())
+    # the benchmark step's form (both queries in one call, the k-NN traversal on a second
+    # stream) returns the same arrays as the two calls
+    oc, ic, kc, dc = bvh.query_spatial_nearest(qd, r, 10, buffer_size=BENCH_BUFFER, order=order,
+                                               capacity=int(ig.numel()))
+    bvh.check()
+    assert bool((oc == og).all()) and bool((ic[:ig.numel()] == ig).all())
+    assert bool((kc == kg).all()) and bool((dc == dg).all())
+    del oc, ic, kc, dc
     og, ig, kg, dg = host(og), host(ig), host(kg), host(dg)
     # every row: CSR well formed, nearest rows sorted by (d2, index), distinct
     assert og[0] == 0 and np.all(np.diff(og) >= 0) and og[-1] == ig.size
