@@ -728,7 +728,7 @@ int arborx_selftest_scan_wait(void *stream) {
   const cudaStream_t s = (cudaStream_t)stream;
   arborx_opts o;
   arborx_default_opts(&o);
-  constexpr uint32_t m = 4096;  // two tiles of the one-call scan
+  const uint32_t m = scan_compact_probe_queries();  // two tiles of the one-call scan
   const size_t ws_words = scan_compact_ws_words(m);
   const size_t bytes = align_up(m * sizeof(int32_t)) + align_up((m + 1) * sizeof(int64_t)) +
                        align_up(ws_words * sizeof(uint64_t)) + align_up(sizeof(uint32_t));

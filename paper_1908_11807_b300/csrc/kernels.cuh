@@ -91,8 +91,10 @@ void launch_compact(const int32_t *buf, int bs, const int32_t *counts, const int
 size_t scan_compact_ws_words(uint32_t m);
 void launch_scan_compact(const int32_t *counts, uint32_t m, const int32_t *buf, int bs, int64_t *offsets,
                          int32_t *indices, int64_t capacity, uint64_t *ws, uint32_t *err, cudaStream_t s);
-// the one-call scan's look-back wait on a predecessor that never publishes (self-test): counts of
-// 2 * 2048 words, offsets of 4097, ws of scan_compact_ws_words(4096) words, *err zero
+// the one-call scan's look-back wait on a predecessor that never publishes (self-test), over
+// p = scan_compact_probe_queries() queries (two tiles): counts of p words, offsets of p + 1, ws of
+// scan_compact_ws_words(p) words, *err zero
+uint32_t scan_compact_probe_queries();
 void launch_scan_compact_wait_probe(int32_t *counts, int64_t *offsets, uint64_t *ws, uint32_t *err, cudaStream_t s);
 // exclusive scan counts[m] -> offsets[m+1]; tmp holds scan_tmp_words(m) int64
 size_t scan_tmp_words(uint32_t m);

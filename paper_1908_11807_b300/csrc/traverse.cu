@@ -1312,10 +1312,12 @@ void launch_scan_compact(const int32_t *counts, uint32_t m, const int32_t *buf, 
     k_scan_compact<false><<<tiles, kScThreads, 0, s>>>(counts, m, buf, bs, offsets, indices, capacity, ws, ctr, err);
 }
 
+uint32_t scan_compact_probe_queries() { return 2 * kScTile; }
+
 void launch_scan_compact_wait_probe(int32_t *counts, int64_t *offsets, uint64_t *ws, uint32_t *err, cudaStream_t s) {
   // two tiles of empty rows; the tile counter starts at 1, so the single block takes tile 1 and
   // looks back at tile 0, whose status word nobody publishes
-  const uint32_t m = 2 * kScTile;
+  const uint32_t m = scan_compact_probe_queries();
   cudaMemsetAsync(counts, 0, (size_t)m * sizeof(int32_t), s);
   cudaMemsetAsync(ws, 0, scan_compact_ws_words(m) * sizeof(uint64_t), s);
   cudaMemsetAsync(reinterpret_cast<uint32_t *>(ws + 2), 1, 1, s);  // the tile counter (after the 2 status words): 1
